@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Benchmark: Wilson-Dirac operator on one GB300 (and N independent replicas).
+
+Headline workload: one full-lattice FP32 Wilson-Dirac application,
+D = (m+4) - H/2 with 18-real links, on a 32^4 periodic lattice (1,048,576
+sites), smoothed SU(3) links exp(0.2 i H) (seed 1001), Gaussian source
+(seed 2001), m = 0.1.  One step = one application.  The metric is achieved
+HBM bandwidth in GB/s counted with compulsory bytes (480 B per site:
+spinor in 96 B + out 96 B + four 72 B links), reported against the measured
+copy bandwidth of the GPU.
+
+Per step the inputs (503 MB) are much larger than the 129 MB L2, so no
+explicit flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle (the plain definition of D) on
+the host cores, one step = one application on an 8^4 sample lattice of the
+same recipe, in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DIMS = (32, 32, 32, 32)
+MASS = 0.1
+LINK_SEED, SRC_SEED = 1001, 2001
+BYTES_PER_SITE = {  # compulsory bytes per output site
+    ("f32", "full", 18): 480, ("f32", "full", 12): 384, ("f32", "eo", 18): 768, ("f32", "eo", 12): 576,
+    ("f64", "full", 18): 960, ("f64", "full", 12): 768, ("f64", "eo", 18): 1536, ("f64", "eo", 12): 1152,
+    ("f16", "full", 18): 248, ("f16", "full", 12): 200, ("f16", "eo", 18): 392, ("f16", "eo", 12): 296,
+    ("bf16", "full", 18): 248, ("bf16", "full", 12): 200, ("bf16", "eo", 18): 392, ("bf16", "eo", 12): 296,
+}
+FLOPS_PER_SITE = 1320
+HEADLINE_KERNEL = "hop_kernel<F32, 18, dagger=false, axpy=true>"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic_from_profile():
+    """Per-launch DRAM bytes of the headline kernel from the committed ncu summary,
+    valid only while the kernel sources are unchanged (source hash recorded there)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "hop_f32_full_r18_32x32x32x32.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    h = hashlib.sha256()
+    for name in ("dslash_impl.cuh", "wd_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1901_07294_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    if vals.get("kernel_source_sha256") != h.hexdigest()[:16]:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """Samples SM clock and throttle reasons with nvidia-smi while active."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_baseline(samples_dims=(8, 8, 8, 8), min_seconds=10.0, max_reps=400):
+    """FP64 oracle D on the host cores, in the same GB/s unit (480 B per site)."""
+    import oracle
+    import synth
+    U = synth.gauge(samples_dims, seed=LINK_SEED)
+    psi = synth.spinor(samples_dims, seed=SRC_SEED)
+    v = synth.volume(samples_dims)
+    oracle.dirac(samples_dims, U, psi, MASS)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.dirac(samples_dims, U, psi, MASS)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or reps >= max_reps:
+            break
+    gbs = BYTES_PER_SITE[("f32", "full", 18)] * v * reps / el / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle D on {'x'.join(map(str, samples_dims))} ({v} sites) x {reps} reps, "
+                      f"{el:.1f} s; GB/s = sites/s x 480 B"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    dims = (8, 8, 8, 8)
+    v = synth.volume(dims)
+    U = synth.gauge(dims, seed=LINK_SEED)
+    psi = synth.spinor(dims, seed=SRC_SEED)
+    for _ in range(args.warmup):
+        oracle.dirac(dims, U, psi, MASS)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.dirac(dims, U, psi, MASS)
+    el = time.perf_counter() - t0
+    gbs = BYTES_PER_SITE[("f32", "full", 18)] * v * args.steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": "dslash_hbm_gbs", "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "wilson_dslash_full_fp64_oracle_sample_8x8x8x8", "lattice": list(dims),
+                   "mass": MASS, "link_seed": LINK_SEED, "source_seed": SRC_SEED},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"one step = FP64 oracle D on 8^4 ({v} sites); GB/s = sites/s x 480 B"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_1901_07294_gb300 as wd
+    import synth
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    ctx = wd.Context(dev)
+    dims = DIMS
+    v = synth.volume(dims)
+    U = synth.gauge(dims, seed=LINK_SEED)
+    psi = synth.spinor(dims, seed=SRC_SEED)
+    g = wd.Gauge(ctx, dims, U)
+    psi_host = torch.from_numpy(psi.view(np.float64).reshape(-1).copy()).pin_memory()
+    aos = psi_host.cuda()
+    prec, recon = wd.F32, 18
+    g.prepare(prec, recon)
+    fin = wd.alloc_field(dims, wd.SITES_FULL, prec)
+    fout = wd.alloc_field(dims, wd.SITES_FULL, prec)
+    wd.pack(ctx, dims, wd.SITES_FULL, prec, aos, fin)
+
+    def step():
+        wd.dslash_apply(ctx, g, fout, fin, MASS, prec=prec, recon=recon, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        events[0].record(stream)
+        for k in range(args.steps):
+            step()
+            events[k + 1].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launch_ms = [events[k].elapsed_time(events[k + 1]) for k in range(args.steps)]
+    total_ms = events[0].elapsed_time(events[-1])
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    bytes_step = BYTES_PER_SITE[("f32", "full", 18)] * v
+    value = bytes_step * args.steps * ws / (total_ms * 1e-3) / 1e9
+    mean_launch = sum(launch_ms) / len(launch_ms)
+    achieved = bytes_step / (mean_launch * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+
+    # end to end through the public API with host buffers: H2D of the canonical
+    # FP64 source (pinned), pack, operator, unpack, D2H of the canonical result
+    out_host = torch.empty_like(psi_host).pin_memory()
+    aos_out = torch.empty_like(aos)
+    e2e_steps = max(3, min(args.steps, 20))
+
+    def e2e_step():
+        aos.copy_(psi_host, non_blocking=True)
+        wd.pack(ctx, dims, wd.SITES_FULL, prec, aos, fin, stream=stream)
+        wd.dslash_apply(ctx, g, fout, fin, MASS, prec=prec, recon=recon, stream=stream)
+        wd.unpack(ctx, dims, wd.SITES_FULL, prec, fout, aos_out, stream=stream)
+        out_host.copy_(aos_out, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_value = bytes_step * ws / (e2e_ms * 1e-3) / 1e9
+
+    variants = {}
+    if not args.no_variants:
+        variants = _variants(wd, torch, ctx, dims, U, psi, stream, peak)
+
+    line = {
+        "metric": "dslash_hbm_gbs", "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "wilson_dslash_full_fp32_recon18_32x32x32x32", "lattice": list(dims),
+                   "sites": v, "mass": MASS, "links": "exp(0.2 i H) smoothed SU(3), seed 1001",
+                   "source": "Gaussian N(0,1), seed 2001", "bytes_per_site": 480,
+                   "flops_per_site": FLOPS_PER_SITE, "l2": "inputs 503 MB per step > 129 MB L2, no flush",
+                   "parallelism": f"replicas{ws}"},
+        "gflops": FLOPS_PER_SITE * v * args.steps * ws / (total_ms * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "kernel": HEADLINE_KERNEL, "achieved": achieved, "peak": peak,
+                     "peak_kind": f"{peak_kind} copy bandwidth (burst)", "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": _traffic_from_profile(), "algorithmic_bytes_per_launch": bytes_step,
+                     "mean_launch_ms": mean_launch},
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": v * 24 * 8,
+                "d2h_bytes_per_step": v * 24 * 8, "ms_per_step": e2e_ms,
+                "path": "pinned H2D FP64 canonical -> wd.pack -> wd.dslash_apply -> wd.unpack -> D2H"},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "variants": variants,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, reps=50):
+    """Per-launch GB/s of every operator variant of the 32^4 / 16^3x32 configuration."""
+    import numpy as np
+
+    import synth
+    out = {}
+    for dims in ((32, 32, 32, 32), (16, 16, 16, 32)):
+        if dims == base_dims:
+            U, psi = U_base, psi_base
+        else:
+            U = synth.gauge(dims, seed=1000 + 2)
+            psi = synth.spinor(dims, seed=2002)
+        v = synth.volume(dims)
+        g = wd.Gauge(ctx, dims, U)
+        aos = torch.from_numpy(psi.view(np.float64).reshape(-1).copy()).cuda()
+        for prec in (wd.F32, wd.F64, wd.F16, wd.BF16):
+            pn = wd.PREC_NAMES[prec]
+            full_in = wd.alloc_field(dims, wd.SITES_FULL, prec)
+            wd.pack(ctx, dims, wd.SITES_FULL, prec, aos, full_in, stream=stream)
+            full_out = wd.alloc_field(dims, wd.SITES_FULL, prec)
+            half = wd.field_bytes(dims, wd.SITES_EVEN, prec)
+            eo_in = full_in[half:]             # odd half
+            eo_out = wd.alloc_field(dims, wd.SITES_EVEN, prec)
+            for recon in (18, 12):
+                g.prepare(prec, recon)
+                for kind in ("full", "eo"):
+                    if kind == "full":
+                        fn = lambda: wd.dslash_apply(ctx, g, full_out, full_in, MASS, prec=prec, recon=recon,
+                                                     stream=stream)
+                        nsite = v
+                    else:
+                        fn = lambda: wd.dslash_eo_apply(ctx, g, eo_out, eo_in, None, wd.EVEN, 0.0, 1.0,
+                                                        prec=prec, recon=recon, stream=stream)
+                        nsite = v // 2
+                    for _ in range(5):
+                        fn()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(reps):
+                        fn()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / reps
+                    b = BYTES_PER_SITE[(pn, kind, recon)] * nsite
+                    gbs = b / (ms * 1e-3) / 1e9
+                    key = f"{'x'.join(map(str, dims))}/{pn}/{kind}/r{recon}"
+                    out[key] = {"ms": round(ms, 5), "gbs": round(gbs, 1), "frac_hbm": round(gbs / peak, 4),
+                                "gflops": round(FLOPS_PER_SITE * nsite / (ms * 1e-3) / 1e9, 1)}
+        g.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="wdirac", choices=["wdirac", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

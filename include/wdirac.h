@@ -1,0 +1,149 @@
+/*
+ * wdirac -- Wilson-Dirac operator and solvers on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI.  Every function returns a wd_status (0 = success, negative = error)
+ * unless stated otherwise; no C++ exception crosses this boundary.  After an
+ * error, wd_last_error() returns a message for the calling thread.
+ *
+ * The operator (arXiv:1901.07294, Sec. II-A, Eq. (1)).  A quark field psi has
+ * 4 spin x 3 colour complex components per lattice site; the SU(3) gauge link
+ * U_mu(x) sits on the link from x to x+mu.  This library implements the
+ * hopping sum
+ *     H psi(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                       + (1 + gamma_mu) U_mu(x-mu)^dagger psi(x-mu) ]
+ * and the Wilson operator D = (m+4) - H/2, on a periodic 4D lattice, with the
+ * Hermitian chiral gamma basis (gamma5 = diag(1,1,-1,-1)).  Eq. (1) as
+ * printed (projectors swapped) equals gamma5 H gamma5.
+ *
+ * Lattice.  dims = {Lx, Ly, Lz, Lt}, every extent even and >= 2; mu = 0..3 =
+ * x,y,z,t; lexicographic site = x + Lx*(y + Ly*(z + Lz*t)); parity of a site
+ * = (x+y+z+t) mod 2, even = 0.  V = Lx*Ly*Lz*Lt, Vh = V/2 (< 2^31).
+ *
+ * Canonical (user) layout, FP64, interleaved re/im, lexicographic order:
+ *     spinor double[V][4 spin][3 colour][2]
+ *     links  double[V][4 mu][3 row][3 col][2]
+ *
+ * Device field layout (opaque to callers; size from wd_field_bytes()).  A
+ * "half field" holds the Vh sites of one parity in checkerboard order
+ * cb = site >> 1.  Its 24 reals per site are split into planes of 16-byte
+ * vectors (plane-major, site-minor) so that consecutive threads read
+ * consecutive 16-byte words:
+ *     WD_F64 : 12 planes of double2
+ *     WD_F32 :  6 planes of float4
+ *     WD_F16, WD_BF16 : 3 planes of 8 halves, then one plane of FP32
+ *               per-site scales (stored value = real / scale, scale =
+ *               max |real| over the site's 24 reals).
+ * A full field is the even half followed by the odd half.  nrhs > 1 means
+ * nrhs fields stored one after another.
+ *
+ * Memory ownership.  Field pointers are device memory owned by the caller
+ * (for example torch tensors); the library never frees them.  Context and
+ * gauge objects are owned by the library and released by their destroy call.
+ * Pointers passed as fields must be 16-byte aligned.
+ *
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ * Operator calls are asynchronous on that stream; launch errors are reported
+ * at once, asynchronous faults at the next synchronising call.
+ */
+#ifndef WDIRAC_H
+#define WDIRAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WD_OK = 0,
+    WD_EINVAL = -1,      /* bad argument (dims, precision, pointer, alignment) */
+    WD_ENOMEM = -2,      /* device or host allocation failed */
+    WD_ECUDA = -3,       /* CUDA runtime error */
+    WD_ENOCONV = -4,     /* solver reached maxiter without converging */
+    WD_ETIMEOUT = -5,    /* a bounded device-side wait gave up */
+    WD_ECANCELLED = -6,  /* request cancelled */
+    WD_EBUSY = -7        /* result not ready yet */
+} wd_status;
+
+typedef enum { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2, WD_BF16 = 3 } wd_prec;   /* storage precision */
+typedef enum { WD_RECON_18 = 18, WD_RECON_12 = 12 } wd_recon;               /* reals stored per link */
+typedef enum { WD_EVEN = 0, WD_ODD = 1 } wd_parity;
+typedef enum { WD_SITES_FULL = 0, WD_SITES_EVEN = 1, WD_SITES_ODD = 2 } wd_sites;
+
+typedef struct wd_ctx wd_ctx;
+typedef struct wd_gauge wd_gauge;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int wd_version(void);
+
+/* Message of the last error on the calling thread ("" if none).  The pointer
+ * stays valid until the next wdirac call on this thread. */
+const char *wd_last_error(void);
+
+/* Context: binds a CUDA device and holds per-device scratch (reduction
+ * partial sums, launch-shape cache).  One context may be shared by threads
+ * whose calls do not overlap; give overlapping callers one context each. */
+int wd_ctx_create(int device, wd_ctx **out);
+int wd_ctx_destroy(wd_ctx *ctx);
+
+/* Bytes of one device field of `sites` (wd_sites) in precision `prec`,
+ * times nrhs.  Errors: WD_EINVAL for bad dims, prec or nrhs < 1. */
+int wd_field_bytes(const int dims[4], int sites, int prec, int nrhs, size_t *out);
+
+/* Layout conversion (Sec. II-C lists precision conversion among the
+ * machine-specific primitives).  wd_pack reads a canonical FP64 spinor of the
+ * FULL lattice (device memory, V sites) and writes the device field holding
+ * `sites` (full, even or odd half) in precision `prec`.  wd_unpack writes the
+ * sites held by the field back into a canonical full-lattice array; sites of
+ * the other parity are left untouched.  Asynchronous on `stream`. */
+int wd_pack(wd_ctx *ctx, const int dims[4], int sites, int prec, const double *aos,
+            void *field, void *stream);
+int wd_unpack(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *field,
+              double *aos, void *stream);
+
+/* Gauge field (Sec. II-A: one SU(3) matrix per link).  `links` is canonical
+ * FP64 (device memory, or host memory if links_on_host != 0); the library
+ * keeps its own FP64 copy and builds device layouts on demand: per parity,
+ * per mu, planes of 16-byte vectors holding the first `recon` reals of the
+ * row-major matrix (12 = rows 0 and 1 only; row 2 is rebuilt in the kernel as
+ * conj(row0 x row1), valid for SU(3)).  Synchronous. */
+int wd_gauge_create(wd_ctx *ctx, const int dims[4], const double *links, int links_on_host,
+                    wd_gauge **out);
+/* Builds (if not built yet) the (prec, recon) layout.  Operator calls build
+ * missing layouts themselves; call this first when the operator call must not
+ * allocate (for example before capturing a CUDA graph).  Synchronous. */
+int wd_gauge_prepare(wd_gauge *g, int prec, int recon);
+int wd_gauge_bytes(const wd_gauge *g, int prec, int recon, size_t *out);
+int wd_gauge_destroy(wd_gauge *g);
+
+/*
+ * Full-lattice Wilson-Dirac operator:  out = D in = (m+4) in - H in / 2.
+ * `in` and `out` are full fields of precision `prec` (nrhs consecutive
+ * fields); the gauge layout (prec, recon) is used (WD_F64 fields need WD_F64
+ * links; WD_F32 / WD_F16 / WD_BF16 fields compute in FP32 on links stored in
+ * the same precision as the field).  out must not alias in.
+ * Flop count: 1320 per site for H (Eq. (1): 8 directions of spin projection,
+ * SU(3) x half-spinor and reconstruction).
+ */
+int dslash_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, double mass,
+                 int nrhs, int prec, int recon, void *stream);
+
+/*
+ * Even-odd hopping block with fused axpby:
+ *     out_p = a * x_p + b * H^(d)_{p,1-p} in_{1-p},   p = out_parity,
+ * where H_{p,1-p} is H restricted to output sites of parity p (its inputs
+ * are the sites of parity 1-p), and H^(d) = H (dagger = 0) or
+ * gamma5 H gamma5 (dagger = 1; the projectors 1 -+ gamma swap).  `in`, `x`
+ * and `out` are half fields; x may be NULL (then a is ignored).  out must not
+ * alias in; it may alias x.  With dagger = 1 the block is the adjoint of the
+ * opposite block: (H_{p,1-p})^dagger = gamma5 H_{1-p,p} gamma5.
+ */
+int dslash_eo_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, const void *x,
+                    int out_parity, double a, double b, int dagger, int nrhs, int prec, int recon,
+                    void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WDIRAC_H */

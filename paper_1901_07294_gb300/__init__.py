@@ -1,0 +1,216 @@
+"""wdirac: Wilson-Dirac operator and solvers on one NVIDIA GB300 (sm_103a).
+
+Thin Python binding of the C ABI declared in ``include/wdirac.h``.  Every
+function here only marshals arguments (tensor pointers, sizes, the current
+CUDA stream) into one call of the native library ``_build/libwdirac.so``;
+all computation runs in its CUDA kernels.  There is no CPU path: if the
+library cannot be built or loaded, every call raises.
+
+Arrays: device fields are opaque byte buffers (torch.uint8 CUDA tensors of
+``field_bytes(...)`` bytes); canonical spinors and links are FP64 complex
+arrays (torch.complex128 / float64 CUDA tensors, or numpy arrays on the host
+where stated) in lexicographic order ``site = x + Lx*(y + Ly*(z + Lz*t))``.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+from . import _build
+
+F64, F32, F16, BF16 = 0, 1, 2, 3
+PREC_NAMES = {F64: "f64", F32: "f32", F16: "f16", BF16: "bf16"}
+SITES_FULL, SITES_EVEN, SITES_ODD = 0, 1, 2
+EVEN, ODD = 0, 1
+
+WD_OK, WD_EINVAL, WD_ENOMEM, WD_ECUDA, WD_ENOCONV, WD_ETIMEOUT, WD_ECANCELLED, WD_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
+_STATUS = {WD_EINVAL: "EINVAL", WD_ENOMEM: "ENOMEM", WD_ECUDA: "ECUDA", WD_ENOCONV: "ENOCONV",
+           WD_ETIMEOUT: "ETIMEOUT", WD_ECANCELLED: "ECANCELLED", WD_EBUSY: "EBUSY"}
+
+_lock = threading.Lock()
+_lib = None
+_vp, _ip, _dp, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+_DIMS = ctypes.c_int * 4
+
+
+class WdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"wdirac {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_SIGS = {
+    "wd_version": (_ip, []),
+    "wd_last_error": (ctypes.c_char_p, []),
+    "wd_ctx_create": (_ip, [_ip, ctypes.POINTER(_vp)]),
+    "wd_ctx_destroy": (_ip, [_vp]),
+    "wd_field_bytes": (_ip, [_DIMS, _ip, _ip, _ip, ctypes.POINTER(_sz)]),
+    "wd_pack": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _vp, _vp]),
+    "wd_unpack": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _vp, _vp]),
+    "wd_gauge_create": (_ip, [_vp, _DIMS, _vp, _ip, ctypes.POINTER(_vp)]),
+    "wd_gauge_prepare": (_ip, [_vp, _ip, _ip]),
+    "wd_gauge_bytes": (_ip, [_vp, _ip, _ip, ctypes.POINTER(_sz)]),
+    "wd_gauge_destroy": (_ip, [_vp]),
+    "dslash_apply": (_ip, [_vp, _vp, _vp, _vp, _dp, _ip, _ip, _ip, _vp]),
+    "dslash_eo_apply": (_ip, [_vp, _vp, _vp, _vp, _vp, _ip, _dp, _dp, _ip, _ip, _ip, _ip, _vp]),
+}
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Load (building first if needed) the native library; raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB_PATH
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != WD_OK:
+        msg = load().wd_last_error().decode(errors="replace")
+        raise WdError(status, msg)
+
+
+def _dims(dims):
+    return _DIMS(*[int(d) for d in dims])
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+class Context:
+    """A wd_ctx bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._h = _vp()
+        _check(load().wd_ctx_create(int(device), ctypes.byref(self._h)))
+        self.device = int(device)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().wd_ctx_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def field_bytes(dims, sites: int, prec: int, nrhs: int = 1) -> int:
+    out = _sz()
+    _check(load().wd_field_bytes(_dims(dims), int(sites), int(prec), int(nrhs), ctypes.byref(out)))
+    return int(out.value)
+
+
+def alloc_field(dims, sites: int, prec: int, nrhs: int = 1, device="cuda"):
+    """Uninitialised device field (torch.uint8 tensor) of the right size."""
+    import torch
+    return torch.empty(field_bytes(dims, sites, prec, nrhs), dtype=torch.uint8, device=device)
+
+
+def pack(ctx: Context, dims, sites: int, prec: int, aos, field, stream=None) -> None:
+    """Canonical FP64 full-lattice spinor (device) -> device field holding `sites`."""
+    _check(load().wd_pack(ctx.handle, _dims(dims), int(sites), int(prec), _ptr(aos), _ptr(field), _stream(stream)))
+
+
+def unpack(ctx: Context, dims, sites: int, prec: int, field, aos, stream=None) -> None:
+    """Device field -> the sites it holds inside a canonical FP64 full-lattice array."""
+    _check(load().wd_unpack(ctx.handle, _dims(dims), int(sites), int(prec), _ptr(field), _ptr(aos), _stream(stream)))
+
+
+class Gauge:
+    """Library-owned gauge field built from canonical FP64 links (V,4,3,3).
+
+    `links` is a CUDA tensor (complex128 or float64) or a host numpy array."""
+
+    def __init__(self, ctx: Context, dims, links):
+        self._h = _vp()
+        self.ctx = ctx
+        self.dims = tuple(int(d) for d in dims)
+        on_host = 0
+        if hasattr(links, "data_ptr"):
+            if not links.is_cuda:
+                raise ValueError("torch links must be a CUDA tensor (or pass a numpy array)")
+            if not links.is_contiguous():
+                raise ValueError("links must be contiguous")
+            ptr = links.data_ptr()
+        else:
+            import numpy as np
+            arr = np.ascontiguousarray(links, dtype=np.complex128)
+            self._host_keepalive = arr
+            ptr = arr.ctypes.data
+            on_host = 1
+        _check(load().wd_gauge_create(ctx.handle, _dims(dims), ptr, on_host, ctypes.byref(self._h)))
+        self._host_keepalive = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def prepare(self, prec: int, recon: int) -> None:
+        _check(load().wd_gauge_prepare(self._h, int(prec), int(recon)))
+
+    def nbytes(self, prec: int, recon: int) -> int:
+        out = _sz()
+        _check(load().wd_gauge_bytes(self._h, int(prec), int(recon), ctypes.byref(out)))
+        return int(out.value)
+
+    def close(self):
+        if self._h:
+            load().wd_gauge_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dslash_apply(ctx: Context, gauge: Gauge, out, inp, mass: float, nrhs: int = 1, prec: int = F32,
+                 recon: int = 18, stream=None) -> None:
+    """out = D in = (m+4) in - H in / 2 on full fields (asynchronous)."""
+    _check(load().dslash_apply(ctx.handle, gauge.handle, _ptr(out), _ptr(inp), float(mass), int(nrhs),
+                               int(prec), int(recon), _stream(stream)))
+
+
+def dslash_eo_apply(ctx: Context, gauge: Gauge, out, inp, x, out_parity: int, a: float, b: float,
+                    dagger: bool = False, nrhs: int = 1, prec: int = F32, recon: int = 18, stream=None) -> None:
+    """out_p = a x_p + b H^(dagger)_{p,1-p} in_{1-p} on half fields (asynchronous)."""
+    _check(load().dslash_eo_apply(ctx.handle, gauge.handle, _ptr(out), _ptr(inp), _ptr(x), int(out_parity),
+                                  float(a), float(b), int(bool(dagger)), int(nrhs), int(prec), int(recon),
+                                  _stream(stream)))

@@ -1,0 +1,390 @@
+// Context, errors, geometry, layout conversion (pack/unpack) and gauge objects.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "wd_device.cuh"
+#include "wd_internal.h"
+
+namespace wd {
+
+static thread_local char g_err[512] = "";
+
+int set_error(int status, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+bool valid_prec(int prec) { return prec >= WD_F64 && prec <= WD_BF16; }
+bool valid_recon(int recon) { return recon == WD_RECON_18 || recon == WD_RECON_12; }
+
+static int storage_bytes(int prec) { return prec == WD_F64 ? 8 : prec == WD_F32 ? 4 : 2; }
+
+size_t half_field_bytes(int vh, int prec)
+{
+    size_t per_site = 24 * (size_t)storage_bytes(prec) + ((prec == WD_F16 || prec == WD_BF16) ? 4 : 0);
+    return per_site * (size_t)vh;
+}
+
+size_t link_block_bytes(int vh, int prec, int recon)
+{
+    return (size_t)recon * storage_bytes(prec) * (size_t)vh;
+}
+
+int make_geometry(const int dims[4], Geometry &g)
+{
+    if (!dims) return set_error(WD_EINVAL, "dims is NULL");
+    int64_t v = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (dims[mu] < 2 || (dims[mu] & 1))
+            return set_error(WD_EINVAL, "lattice extent L[%d] = %d must be even and >= 2", mu, dims[mu]);
+        g.L[mu] = dims[mu];
+        v *= dims[mu];
+    }
+    if (v / 2 >= (int64_t)1 << 31) return set_error(WD_EINVAL, "volume %lld too large (V/2 must be < 2^31)", (long long)v);
+    g.V = v;
+    g.Vh = (int)(v / 2);
+    return WD_OK;
+}
+
+// ---- spinor pack / unpack ------------------------------------------------
+struct SiteMap {
+    int Lx, Ly, Lz, vh, p0, np;
+    size_t half_bytes;
+    // (parity slot, checkerboard index) -> lexicographic site
+    __device__ __forceinline__ int64_t lex(int p, int i) const
+    {
+        const int lxh = Lx >> 1;
+        int r = i / lxh;
+        const int xh = i - r * lxh;
+        const int y = r % Ly;
+        const int r2 = r / Ly;
+        const int z = r2 % Lz;
+        const int t = r2 / Lz;
+        const int bit = (p + y + z + t) & 1;
+        return (int64_t)r * Lx + 2 * xh + bit;
+    }
+};
+
+template <int P>
+__global__ void pack_spinor_kernel(const double *__restrict__ aos, char *__restrict__ field, SiteMap m)
+{
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)m.np * m.vh) return;
+    const int slot = (int)(gid / m.vh);
+    const int i = (int)(gid - (int64_t)slot * m.vh);
+    const int64_t s = m.lex(m.p0 + slot, i);
+    typename Prec<P>::real v[24];
+    const double2 *src = reinterpret_cast<const double2 *>(aos + s * 24);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        double2 d = src[k];
+        v[2 * k] = (typename Prec<P>::real)d.x;
+        v[2 * k + 1] = (typename Prec<P>::real)d.y;
+    }
+    Spinor<P>::store(field + slot * m.half_bytes, m.vh, i, v);
+}
+
+template <int P>
+__global__ void unpack_spinor_kernel(const char *__restrict__ field, double *__restrict__ aos, SiteMap m)
+{
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)m.np * m.vh) return;
+    const int slot = (int)(gid / m.vh);
+    const int i = (int)(gid - (int64_t)slot * m.vh);
+    const int64_t s = m.lex(m.p0 + slot, i);
+    typename Prec<P>::real v[24];
+    Spinor<P>::load(field + slot * m.half_bytes, m.vh, i, v);
+    double2 *dst = reinterpret_cast<double2 *>(aos + s * 24);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) dst[k] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
+}
+
+// ---- link pack -----------------------------------------------------------
+template <int P, int RECON>
+__global__ void pack_links_kernel(const double *__restrict__ links, char *__restrict__ out, SiteMap m, size_t blk)
+{
+    using real = typename Prec<P>::real;
+    using L = Link<P, RECON>;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)2 * m.vh) return;
+    const int p = (int)(gid / m.vh);
+    const int i = (int)(gid - (int64_t)p * m.vh);
+    const int64_t s = m.lex(p, i);
+    for (int mu = 0; mu < 4; ++mu) {
+        real u[18];
+        const double *src = links + (s * 4 + mu) * 18;
+#pragma unroll
+        for (int k = 0; k < 18; ++k) u[k] = (real)src[k];
+        char *b = out + (size_t)(p * 4 + mu) * blk;
+#pragma unroll
+        for (int k = 0; k < L::nmain; ++k) stg16(b + ((size_t)k * m.vh + i) * 16, pack16<P>(u + k * L::per16, 1.0f));
+        if constexpr (L::ntail > 0) {
+            char *tp = b + (size_t)L::nmain * m.vh * 16;
+            const int o = L::nmain * L::per16;
+            if constexpr (P == PREC_F32) {
+                reinterpret_cast<float2 *>(tp)[i] = make_float2(u[o], u[o + 1]);
+            } else if constexpr (P == PREC_F16) {
+                __half2 h0 = __floats2half2_rn(u[o], u[o + 1]);
+                if constexpr (L::ntail == 2) {
+                    reinterpret_cast<__half2 *>(tp)[i] = h0;
+                } else {
+                    __half2 h1 = __floats2half2_rn(u[o + 2], u[o + 3]);
+                    uint2 w;
+                    w.x = *reinterpret_cast<unsigned *>(&h0);
+                    w.y = *reinterpret_cast<unsigned *>(&h1);
+                    reinterpret_cast<uint2 *>(tp)[i] = w;
+                }
+            } else {
+                __nv_bfloat162 h0 = __floats2bfloat162_rn(u[o], u[o + 1]);
+                if constexpr (L::ntail == 2) {
+                    reinterpret_cast<__nv_bfloat162 *>(tp)[i] = h0;
+                } else {
+                    __nv_bfloat162 h1 = __floats2bfloat162_rn(u[o + 2], u[o + 3]);
+                    uint2 w;
+                    w.x = *reinterpret_cast<unsigned *>(&h0);
+                    w.y = *reinterpret_cast<unsigned *>(&h1);
+                    reinterpret_cast<uint2 *>(tp)[i] = w;
+                }
+            }
+        }
+    }
+}
+
+static int sites_to_map(const Geometry &g, int sites, int prec, SiteMap &m)
+{
+    m.Lx = g.L[0]; m.Ly = g.L[1]; m.Lz = g.L[2]; m.vh = g.Vh;
+    m.half_bytes = half_field_bytes(g.Vh, prec);
+    switch (sites) {
+    case WD_SITES_FULL: m.p0 = 0; m.np = 2; break;
+    case WD_SITES_EVEN: m.p0 = 0; m.np = 1; break;
+    case WD_SITES_ODD: m.p0 = 1; m.np = 1; break;
+    default: return set_error(WD_EINVAL, "sites = %d is not a wd_sites value", sites);
+    }
+    return WD_OK;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+int gauge_layout(const wd_gauge *gc, int prec, int recon, const char **out)
+{
+    wd_gauge *g = const_cast<wd_gauge *>(gc);
+    if (!valid_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
+    if (!valid_recon(recon)) return set_error(WD_EINVAL, "bad reconstruction %d (use 18 or 12)", recon);
+    std::lock_guard<std::mutex> lk(g->mu);
+    auto key = std::make_pair(prec, recon);
+    auto it = g->layouts.find(key);
+    if (it != g->layouts.end()) {
+        *out = it->second;
+        return WD_OK;
+    }
+    DeviceGuard dg(g->ctx->device);
+    const size_t blk = link_block_bytes(g->geo.Vh, prec, recon);
+    char *buf = nullptr;
+    if (cudaMalloc(&buf, 8 * blk) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WD_ENOMEM, "cudaMalloc of %zu bytes for a gauge layout failed", 8 * blk);
+    }
+    SiteMap m;
+    sites_to_map(g->geo, WD_SITES_FULL, prec, m);
+    const int threads = 256;
+    const int blocks = (int)((2 * (int64_t)g->geo.Vh + threads - 1) / threads);
+#define WD_PACK_LINKS(P, R) pack_links_kernel<P, R><<<blocks, threads>>>(g->canonical, buf, m, blk)
+    switch (prec * 100 + recon) {
+    case WD_F64 * 100 + 18: WD_PACK_LINKS(PREC_F64, 18); break;
+    case WD_F64 * 100 + 12: WD_PACK_LINKS(PREC_F64, 12); break;
+    case WD_F32 * 100 + 18: WD_PACK_LINKS(PREC_F32, 18); break;
+    case WD_F32 * 100 + 12: WD_PACK_LINKS(PREC_F32, 12); break;
+    case WD_F16 * 100 + 18: WD_PACK_LINKS(PREC_F16, 18); break;
+    case WD_F16 * 100 + 12: WD_PACK_LINKS(PREC_F16, 12); break;
+    case WD_BF16 * 100 + 18: WD_PACK_LINKS(PREC_BF16, 18); break;
+    case WD_BF16 * 100 + 12: WD_PACK_LINKS(PREC_BF16, 12); break;
+    }
+#undef WD_PACK_LINKS
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(buf);
+        return set_error(WD_ECUDA, "link packing failed: %s", cudaGetErrorString(e));
+    }
+    g->layouts[key] = buf;
+    *out = buf;
+    return WD_OK;
+}
+
+} // namespace wd
+
+using namespace wd;
+
+extern "C" {
+
+int wd_version(void) { return 100; }
+
+const char *wd_last_error(void) { return wd::g_err; }
+
+int wd_ctx_create(int device, wd_ctx **out)
+{
+    clear_error();
+    if (!out) return set_error(WD_EINVAL, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    WD_CUDA_TRY(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return set_error(WD_EINVAL, "device %d out of range (%d devices)", device, n);
+    wd_ctx *c = new (std::nothrow) wd_ctx();
+    if (!c) return set_error(WD_ENOMEM, "host allocation failed");
+    c->device = device;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+        delete c;
+        return set_error(WD_ECUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+    }
+    c->num_sms = prop.multiProcessorCount;
+    c->cc_major = prop.major;
+    c->cc_minor = prop.minor;
+    *out = c;
+    return WD_OK;
+}
+
+int wd_ctx_destroy(wd_ctx *ctx)
+{
+    clear_error();
+    delete ctx;
+    return WD_OK;
+}
+
+int wd_field_bytes(const int dims[4], int sites, int prec, int nrhs, size_t *out)
+{
+    clear_error();
+    Geometry g;
+    WD_TRY(make_geometry(dims, g));
+    if (!valid_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
+    if (nrhs < 1) return set_error(WD_EINVAL, "nrhs = %d must be >= 1", nrhs);
+    if (!out) return set_error(WD_EINVAL, "out is NULL");
+    size_t half = half_field_bytes(g.Vh, prec);
+    size_t one;
+    switch (sites) {
+    case WD_SITES_FULL: one = 2 * half; break;
+    case WD_SITES_EVEN:
+    case WD_SITES_ODD: one = half; break;
+    default: return set_error(WD_EINVAL, "sites = %d is not a wd_sites value", sites);
+    }
+    *out = one * (size_t)nrhs;
+    return WD_OK;
+}
+
+static int pack_common(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *a, const void *b,
+                       Geometry &g, SiteMap &m)
+{
+    if (!ctx) return set_error(WD_EINVAL, "ctx is NULL");
+    WD_TRY(make_geometry(dims, g));
+    if (!valid_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
+    if (!a || !b) return set_error(WD_EINVAL, "NULL field pointer");
+    if (!aligned16(a) || !aligned16(b)) return set_error(WD_EINVAL, "field pointers must be 16-byte aligned");
+    return sites_to_map(g, sites, prec, m);
+}
+
+int wd_pack(wd_ctx *ctx, const int dims[4], int sites, int prec, const double *aos, void *field, void *stream)
+{
+    clear_error();
+    Geometry g;
+    SiteMap m;
+    WD_TRY(pack_common(ctx, dims, sites, prec, aos, field, g, m));
+    const int threads = 256;
+    const int blocks = (int)(((int64_t)m.np * m.vh + threads - 1) / threads);
+    cudaStream_t s = (cudaStream_t)stream;
+    char *f = (char *)field;
+    switch (prec) {
+    case WD_F64: pack_spinor_kernel<PREC_F64><<<blocks, threads, 0, s>>>(aos, f, m); break;
+    case WD_F32: pack_spinor_kernel<PREC_F32><<<blocks, threads, 0, s>>>(aos, f, m); break;
+    case WD_F16: pack_spinor_kernel<PREC_F16><<<blocks, threads, 0, s>>>(aos, f, m); break;
+    case WD_BF16: pack_spinor_kernel<PREC_BF16><<<blocks, threads, 0, s>>>(aos, f, m); break;
+    }
+    WD_CUDA_TRY(cudaGetLastError());
+    return WD_OK;
+}
+
+int wd_unpack(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *field, double *aos, void *stream)
+{
+    clear_error();
+    Geometry g;
+    SiteMap m;
+    WD_TRY(pack_common(ctx, dims, sites, prec, field, aos, g, m));
+    const int threads = 256;
+    const int blocks = (int)(((int64_t)m.np * m.vh + threads - 1) / threads);
+    cudaStream_t s = (cudaStream_t)stream;
+    const char *f = (const char *)field;
+    switch (prec) {
+    case WD_F64: unpack_spinor_kernel<PREC_F64><<<blocks, threads, 0, s>>>(f, aos, m); break;
+    case WD_F32: unpack_spinor_kernel<PREC_F32><<<blocks, threads, 0, s>>>(f, aos, m); break;
+    case WD_F16: unpack_spinor_kernel<PREC_F16><<<blocks, threads, 0, s>>>(f, aos, m); break;
+    case WD_BF16: unpack_spinor_kernel<PREC_BF16><<<blocks, threads, 0, s>>>(f, aos, m); break;
+    }
+    WD_CUDA_TRY(cudaGetLastError());
+    return WD_OK;
+}
+
+int wd_gauge_create(wd_ctx *ctx, const int dims[4], const double *links, int links_on_host, wd_gauge **out)
+{
+    clear_error();
+    if (!ctx || !links || !out) return set_error(WD_EINVAL, "NULL argument");
+    *out = nullptr;
+    Geometry geo;
+    WD_TRY(make_geometry(dims, geo));
+    DeviceGuard dg(ctx->device);
+    wd_gauge *g = new (std::nothrow) wd_gauge();
+    if (!g) return set_error(WD_ENOMEM, "host allocation failed");
+    g->ctx = ctx;
+    g->geo = geo;
+    const size_t nb = (size_t)geo.V * 4 * 18 * sizeof(double);
+    if (cudaMalloc(&g->canonical, nb) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        return set_error(WD_ENOMEM, "cudaMalloc of %zu bytes for the gauge field failed", nb);
+    }
+    cudaError_t e = cudaMemcpy(g->canonical, links, nb, links_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(g->canonical);
+        delete g;
+        return set_error(WD_ECUDA, "copying the gauge field failed: %s", cudaGetErrorString(e));
+    }
+    *out = g;
+    return WD_OK;
+}
+
+int wd_gauge_prepare(wd_gauge *g, int prec, int recon)
+{
+    clear_error();
+    if (!g) return set_error(WD_EINVAL, "gauge is NULL");
+    const char *p;
+    return gauge_layout(g, prec, recon, &p);
+}
+
+int wd_gauge_bytes(const wd_gauge *g, int prec, int recon, size_t *out)
+{
+    clear_error();
+    if (!g || !out) return set_error(WD_EINVAL, "NULL argument");
+    if (!valid_prec(prec) || !valid_recon(recon)) return set_error(WD_EINVAL, "bad precision or reconstruction");
+    *out = 8 * link_block_bytes(g->geo.Vh, prec, recon);
+    return WD_OK;
+}
+
+int wd_gauge_destroy(wd_gauge *g)
+{
+    clear_error();
+    if (!g) return WD_OK;
+    DeviceGuard dg(g->ctx->device);
+    for (auto &kv : g->layouts) cudaFree(kv.second);
+    cudaFree(g->canonical);
+    delete g;
+    return WD_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,103 @@
+// C entry points of the Wilson-Dirac operator: dslash_apply (full lattice)
+// and dslash_eo_apply (even-odd block with fused axpby).
+#include "dslash_impl.cuh"
+#include "wd_internal.h"
+
+namespace wd {
+extern template cudaError_t launch_hop<PREC_F64>(const HopArgs &, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_hop<PREC_F32>(const HopArgs &, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_hop<PREC_F16>(const HopArgs &, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_hop<PREC_BF16>(const HopArgs &, int, int, int, int, cudaStream_t);
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+int hop_launch(const HopArgs &A, int prec, int recon, int dagger, int nrhs, cudaStream_t s)
+{
+    const int threads = 256;
+    cudaError_t e = cudaSuccess;
+    switch (prec) {
+    case WD_F64: e = launch_hop<PREC_F64>(A, recon, dagger, nrhs, threads, s); break;
+    case WD_F32: e = launch_hop<PREC_F32>(A, recon, dagger, nrhs, threads, s); break;
+    case WD_F16: e = launch_hop<PREC_F16>(A, recon, dagger, nrhs, threads, s); break;
+    case WD_BF16: e = launch_hop<PREC_BF16>(A, recon, dagger, nrhs, threads, s); break;
+    }
+    if (e != cudaSuccess) return set_error(WD_ECUDA, "hop kernel launch failed: %s", cudaGetErrorString(e));
+    return WD_OK;
+}
+
+// Fills the geometry and gauge parts of HopArgs.
+int hop_setup(const wd_gauge *g, int prec, int recon, HopArgs &A)
+{
+    if (!g) return set_error(WD_EINVAL, "gauge is NULL");
+    if (!valid_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
+    if (!valid_recon(recon)) return set_error(WD_EINVAL, "bad reconstruction %d", recon);
+    const char *base = nullptr;
+    WD_TRY(gauge_layout(g, prec, recon, &base));
+    const int vh = g->geo.Vh;
+    A.link_blk = link_block_bytes(vh, prec, recon);
+    A.gauge[0] = base;
+    A.gauge[1] = base + 4 * A.link_blk;
+    for (int mu = 0; mu < 4; ++mu) A.L[mu] = g->geo.L[mu];
+    A.vh = vh;
+    return WD_OK;
+}
+
+} // namespace wd
+
+using namespace wd;
+
+extern "C" {
+
+int dslash_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, double mass, int nrhs, int prec,
+                 int recon, void *stream)
+{
+    clear_error();
+    if (!ctx) return set_error(WD_EINVAL, "ctx is NULL");
+    if (!out || !in) return set_error(WD_EINVAL, "NULL field pointer");
+    if (!aligned16(out) || !aligned16(in)) return set_error(WD_EINVAL, "field pointers must be 16-byte aligned");
+    if (out == in) return set_error(WD_EINVAL, "out must not alias in");
+    if (nrhs < 1) return set_error(WD_EINVAL, "nrhs = %d must be >= 1", nrhs);
+    HopArgs A{};
+    WD_TRY(hop_setup(g, prec, recon, A));
+    const size_t half = half_field_bytes(A.vh, prec);
+    const char *src = (const char *)in;
+    char *dst = (char *)out;
+    for (int p = 0; p < 2; ++p) {
+        A.in[p] = src + (size_t)(1 - p) * half;
+        A.x[p] = src + (size_t)p * half;
+        A.out[p] = dst + (size_t)p * half;
+    }
+    A.rhs_stride = 2 * half;
+    A.nparity = 2;
+    A.parity0 = 0;
+    A.a = mass + 4.0;
+    A.b = -0.5;
+    return hop_launch(A, prec, recon, 0, nrhs, (cudaStream_t)stream);
+}
+
+int dslash_eo_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, const void *x, int out_parity,
+                    double a, double b, int dagger, int nrhs, int prec, int recon, void *stream)
+{
+    clear_error();
+    if (!ctx) return set_error(WD_EINVAL, "ctx is NULL");
+    if (!out || !in) return set_error(WD_EINVAL, "NULL field pointer");
+    if (!aligned16(out) || !aligned16(in) || (x && !aligned16(x)))
+        return set_error(WD_EINVAL, "field pointers must be 16-byte aligned");
+    if (out == in) return set_error(WD_EINVAL, "out must not alias in");
+    if (out_parity != WD_EVEN && out_parity != WD_ODD) return set_error(WD_EINVAL, "out_parity must be 0 or 1");
+    if (nrhs < 1) return set_error(WD_EINVAL, "nrhs = %d must be >= 1", nrhs);
+    HopArgs A{};
+    WD_TRY(hop_setup(g, prec, recon, A));
+    const int p = out_parity;
+    A.in[p] = A.in[1 - p] = (const char *)in;
+    A.x[p] = A.x[1 - p] = (const char *)x;
+    A.out[p] = A.out[1 - p] = (char *)out;
+    A.rhs_stride = half_field_bytes(A.vh, prec);
+    A.nparity = 1;
+    A.parity0 = p;
+    A.a = a;
+    A.b = b;
+    return hop_launch(A, prec, recon, dagger ? 1 : 0, nrhs, (cudaStream_t)stream);
+}
+
+} // extern "C"

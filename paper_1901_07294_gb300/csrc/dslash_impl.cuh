@@ -1,0 +1,218 @@
+// Wilson hopping kernel: one thread per output site of one parity.
+//
+// For output parity p and checkerboard site i the kernel computes
+//     acc = sum_mu (1 + s_f gamma_mu) U_mu(x) psi(x+mu)
+//         +        (1 + s_b gamma_mu) U_mu(x-mu)^dagger psi(x-mu)
+// with s_f = -1, s_b = +1 (the library's H; Sec. II-A, Eq. (1) up to the
+// gamma5 similarity) or the swapped signs for gamma5 H gamma5 (DAG), and
+// stores out = a*x + b*acc.  Each direction: load the 24-real neighbour
+// spinor (16-byte plane loads), project to two spin components (12 reals),
+// load the link (reconstructing row 3 when 12 reals are stored), multiply
+// the two colour vectors by U or U^dagger, and rebuild the two lower spin
+// components from the upper ones.  1320 flops per output site.
+#pragma once
+
+#include "wd_device.cuh"
+
+namespace wd {
+
+struct HopArgs {
+    const char *in[2];    // neighbour source for output parity p (a half field of parity 1-p)
+    const char *x[2];     // axpy term of parity p (NULL if unused)
+    char *out[2];         // output half field of parity p
+    const char *gauge[2]; // links at sites of parity p: 4 mu blocks of `link_blk` bytes
+    size_t link_blk;
+    size_t rhs_stride;    // bytes between consecutive right-hand sides
+    int L[4];
+    int vh;
+    int nparity;          // 2: blocks alternate parity (full operator); 1: parity0 only
+    int parity0;
+    double a, b;
+};
+
+// h0, h1 = upper two spin components of (1 + S gamma_MU) psi, chiral basis.
+template <int MU, int S, typename T>
+__device__ __forceinline__ void project(const T (&v)[24], cpx<T> (&h0)[3], cpx<T> (&h1)[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cpx<T> p0{v[2 * c], v[2 * c + 1]}, p1{v[6 + 2 * c], v[7 + 2 * c]};
+        const cpx<T> p2{v[12 + 2 * c], v[13 + 2 * c]}, p3{v[18 + 2 * c], v[19 + 2 * c]};
+        if constexpr (MU == 0) {        // h0 = p0 + S i p3, h1 = p1 + S i p2
+            h0[c] = {p0.re - S * p3.im, p0.im + S * p3.re};
+            h1[c] = {p1.re - S * p2.im, p1.im + S * p2.re};
+        } else if constexpr (MU == 1) { // h0 = p0 - S p3, h1 = p1 + S p2
+            h0[c] = {p0.re - S * p3.re, p0.im - S * p3.im};
+            h1[c] = {p1.re + S * p2.re, p1.im + S * p2.im};
+        } else if constexpr (MU == 2) { // h0 = p0 + S i p2, h1 = p1 - S i p3
+            h0[c] = {p0.re - S * p2.im, p0.im + S * p2.re};
+            h1[c] = {p1.re + S * p3.im, p1.im - S * p3.re};
+        } else {                        // h0 = p0 + S p2, h1 = p1 + S p3
+            h0[c] = {p0.re + S * p2.re, p0.im + S * p2.im};
+            h1[c] = {p1.re + S * p3.re, p1.im + S * p3.im};
+        }
+    }
+}
+
+// acc += (1 + S gamma_MU) applied in the projected form: spins 0,1 get w0,w1
+// and spins 2,3 are the fixed multiples of w0,w1 that the projector implies.
+template <int MU, int S, typename T>
+__device__ __forceinline__ void accumulate(cpx<T> (&acc)[4][3], const cpx<T> (&w0)[3], const cpx<T> (&w1)[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[0][c].re += w0[c].re; acc[0][c].im += w0[c].im;
+        acc[1][c].re += w1[c].re; acc[1][c].im += w1[c].im;
+        if constexpr (MU == 0) {        // spin2 += -S i w1, spin3 += -S i w0
+            acc[2][c].re += S * w1[c].im; acc[2][c].im -= S * w1[c].re;
+            acc[3][c].re += S * w0[c].im; acc[3][c].im -= S * w0[c].re;
+        } else if constexpr (MU == 1) { // spin2 += S w1, spin3 += -S w0
+            acc[2][c].re += S * w1[c].re; acc[2][c].im += S * w1[c].im;
+            acc[3][c].re -= S * w0[c].re; acc[3][c].im -= S * w0[c].im;
+        } else if constexpr (MU == 2) { // spin2 += -S i w0, spin3 += S i w1
+            acc[2][c].re += S * w0[c].im; acc[2][c].im -= S * w0[c].re;
+            acc[3][c].re -= S * w1[c].im; acc[3][c].im += S * w1[c].re;
+        } else {                        // spin2 += S w0, spin3 += S w1
+            acc[2][c].re += S * w0[c].re; acc[2][c].im += S * w0[c].im;
+            acc[3][c].re += S * w1[c].re; acc[3][c].im += S * w1[c].im;
+        }
+    }
+}
+
+// w = U h (FWD) or U^dagger h.
+template <bool FWD, typename T>
+__device__ __forceinline__ void su3_mul(const cpx<T> (&U)[3][3], const cpx<T> (&h)[3], cpx<T> (&w)[3])
+{
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        if constexpr (FWD) {
+            cpx<T> s = cmul(U[r][0], h[0]);
+            s = cfma(U[r][1], h[1], s);
+            w[r] = cfma(U[r][2], h[2], s);
+        } else {
+            cpx<T> s = cmul_conj(U[0][r], h[0]);
+            s = cfma_conj(U[1][r], h[1], s);
+            w[r] = cfma_conj(U[2][r], h[2], s);
+        }
+    }
+}
+
+template <int P, int RECON, int MU, int S, bool FWD>
+__device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh, int nb, int li,
+                                        cpx<typename Prec<P>::real> (&acc)[4][3])
+{
+    using T = typename Prec<P>::real;
+    T psi[24];
+    Spinor<P>::load(in, vh, nb, psi);
+    cpx<T> h0[3], h1[3];
+    project<MU, S>(psi, h0, h1);
+    cpx<T> U[3][3];
+    Link<P, RECON>::load(lblk, vh, li, U);
+    cpx<T> w0[3], w1[3];
+    su3_mul<FWD>(U, h0, w0);
+    su3_mul<FWD>(U, h1, w1);
+    accumulate<MU, S>(acc, w0, w1);
+}
+
+template <int P, int RECON, bool DAG, bool HAS_X>
+__global__ void __launch_bounds__(256) hop_kernel(const HopArgs A)
+{
+    using T = typename Prec<P>::real;
+    int p, blk;
+    if (A.nparity == 2) { p = blockIdx.x & 1; blk = blockIdx.x >> 1; }
+    else { p = A.parity0; blk = blockIdx.x; }
+    const int i = blk * blockDim.x + threadIdx.x;
+    const int vh = A.vh;
+    if (i >= vh) return;
+    const size_t roff = (size_t)blockIdx.y * A.rhs_stride;
+    // parity-dependent pointers chosen by select: a runtime index into the
+    // parameter struct would force a copy of it into local memory
+    const char *in = (p ? A.in[1] : A.in[0]) + roff;
+    const char *gf = p ? A.gauge[1] : A.gauge[0];
+    const char *gb = p ? A.gauge[0] : A.gauge[1];
+
+    // checkerboard index -> coordinates; x-parity bit from the site parity
+    const int Lx = A.L[0], Ly = A.L[1], Lz = A.L[2], Lt = A.L[3];
+    const int lxh = Lx >> 1;
+    int r = i / lxh;
+    const int xh = i - r * lxh;
+    const int y = r % Ly;
+    r /= Ly;
+    const int z = r % Lz;
+    const int t = r / Lz;
+    const int x = 2 * xh + ((p + y + z + t) & 1);
+    const int sy = lxh, sz = lxh * Ly, st = sz * Lz;
+    const int row = i - xh;
+    const int xf = row + ((x + 1 == Lx ? 0 : x + 1) >> 1);
+    const int xb = row + ((x == 0 ? Lx - 1 : x - 1) >> 1);
+    const int yf = (y == Ly - 1) ? i - (Ly - 1) * sy : i + sy;
+    const int yb = (y == 0) ? i + (Ly - 1) * sy : i - sy;
+    const int zf = (z == Lz - 1) ? i - (Lz - 1) * sz : i + sz;
+    const int zb = (z == 0) ? i + (Lz - 1) * sz : i - sz;
+    const int tf = (t == Lt - 1) ? i - (Lt - 1) * st : i + st;
+    const int tb = (t == 0) ? i + (Lt - 1) * st : i - st;
+
+    constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF gamma
+    constexpr int SB = -SF;             // backward projector
+    const size_t lb = A.link_blk;
+
+    cpx<T> acc[4][3];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[s][c] = {T(0), T(0)};
+
+    hop_dir<P, RECON, 0, SF, true>(in, gf + 0 * lb, vh, xf, i, acc);
+    hop_dir<P, RECON, 0, SB, false>(in, gb + 0 * lb, vh, xb, xb, acc);
+    hop_dir<P, RECON, 1, SF, true>(in, gf + 1 * lb, vh, yf, i, acc);
+    hop_dir<P, RECON, 1, SB, false>(in, gb + 1 * lb, vh, yb, yb, acc);
+    hop_dir<P, RECON, 2, SF, true>(in, gf + 2 * lb, vh, zf, i, acc);
+    hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, acc);
+    hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, acc);
+    hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, acc);
+
+    const T a = (T)A.a, b = (T)A.b;
+    T o[24];
+    if constexpr (HAS_X) {
+        Spinor<P>::load((p ? A.x[1] : A.x[0]) + roff, vh, i, o);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o[6 * s + 2 * c] = a * o[6 * s + 2 * c] + b * acc[s][c].re;
+                o[6 * s + 2 * c + 1] = a * o[6 * s + 2 * c + 1] + b * acc[s][c].im;
+            }
+    } else {
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o[6 * s + 2 * c] = b * acc[s][c].re;
+                o[6 * s + 2 * c + 1] = b * acc[s][c].im;
+            }
+    }
+    Spinor<P>::store((p ? A.out[1] : A.out[0]) + roff, vh, i, o);
+}
+
+// Launches the hop kernel of precision P for the runtime (recon, dagger, has_x).
+template <int P>
+cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int threads, cudaStream_t s)
+{
+    const int per = (A.vh + threads - 1) / threads;
+    dim3 grid((unsigned)(per * A.nparity), (unsigned)nrhs);
+    const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
+    const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
+    switch (key) {
+    case 0: hop_kernel<P, 18, false, false><<<grid, threads, 0, s>>>(A); break;
+    case 1: hop_kernel<P, 18, false, true><<<grid, threads, 0, s>>>(A); break;
+    case 2: hop_kernel<P, 18, true, false><<<grid, threads, 0, s>>>(A); break;
+    case 3: hop_kernel<P, 18, true, true><<<grid, threads, 0, s>>>(A); break;
+    case 4: hop_kernel<P, 12, false, false><<<grid, threads, 0, s>>>(A); break;
+    case 5: hop_kernel<P, 12, false, true><<<grid, threads, 0, s>>>(A); break;
+    case 6: hop_kernel<P, 12, true, false><<<grid, threads, 0, s>>>(A); break;
+    case 7: hop_kernel<P, 12, true, true><<<grid, threads, 0, s>>>(A); break;
+    }
+    return cudaGetLastError();
+}
+
+} // namespace wd

@@ -1,0 +1,225 @@
+// Device-side building blocks: storage traits, 16-byte plane loads/stores,
+// complex multiply-add, link reconstruction.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace wd {
+
+enum { PREC_F64 = 0, PREC_F32 = 1, PREC_F16 = 2, PREC_BF16 = 3 };
+
+// Storage traits.  `real` is the compute type; `per16` reals fit in one 16-byte
+// vector; half types carry a per-site FP32 scale plane for spinors.
+template <int P> struct Prec;
+template <> struct Prec<PREC_F64> { using real = double; static constexpr int per16 = 2;  static constexpr int bytes = 8; static constexpr bool scaled = false; };
+template <> struct Prec<PREC_F32> { using real = float;  static constexpr int per16 = 4;  static constexpr int bytes = 4; static constexpr bool scaled = false; };
+template <> struct Prec<PREC_F16> { using real = float;  static constexpr int per16 = 8;  static constexpr int bytes = 2; static constexpr bool scaled = true; };
+template <> struct Prec<PREC_BF16>{ using real = float;  static constexpr int per16 = 8;  static constexpr int bytes = 2; static constexpr bool scaled = true; };
+
+template <typename T> struct cpx { T re, im; };
+
+// z + x*y and z + conj(x)*y with real FMAs (the two complex multiply-add
+// forms of Sec. III-D, Eq. (2), which SVE gets from a pair of FCMLA).
+template <typename T> __device__ __forceinline__ cpx<T> cfma(cpx<T> x, cpx<T> y, cpx<T> z)
+{
+    z.re = fma(x.re, y.re, z.re); z.re = fma(-x.im, y.im, z.re);
+    z.im = fma(x.re, y.im, z.im); z.im = fma(x.im, y.re, z.im);
+    return z;
+}
+template <typename T> __device__ __forceinline__ cpx<T> cfma_conj(cpx<T> x, cpx<T> y, cpx<T> z)
+{
+    z.re = fma(x.re, y.re, z.re); z.re = fma(x.im, y.im, z.re);
+    z.im = fma(x.re, y.im, z.im); z.im = fma(-x.im, y.re, z.im);
+    return z;
+}
+template <typename T> __device__ __forceinline__ cpx<T> cmul(cpx<T> x, cpx<T> y)
+{
+    cpx<T> z;
+    z.re = x.re * y.re; z.re = fma(-x.im, y.im, z.re);
+    z.im = x.re * y.im; z.im = fma(x.im, y.re, z.im);
+    return z;
+}
+template <typename T> __device__ __forceinline__ cpx<T> cmul_conj(cpx<T> x, cpx<T> y)
+{
+    cpx<T> z;
+    z.re = x.re * y.re; z.re = fma(x.im, y.im, z.re);
+    z.im = x.re * y.im; z.im = fma(-x.im, y.re, z.im);
+    return z;
+}
+
+// ---- 16-byte vector <-> reals -------------------------------------------
+__device__ __forceinline__ uint4 ldg16(const void *p)
+{
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+__device__ __forceinline__ void stg16(void *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
+
+template <int P> __device__ __forceinline__ void unpack16(uint4 w, typename Prec<P>::real *r, float scale);
+template <> __device__ __forceinline__ void unpack16<PREC_F64>(uint4 w, double *r, float)
+{
+    r[0] = __hiloint2double(w.y, w.x);
+    r[1] = __hiloint2double(w.w, w.z);
+}
+template <> __device__ __forceinline__ void unpack16<PREC_F32>(uint4 w, float *r, float)
+{
+    r[0] = __uint_as_float(w.x); r[1] = __uint_as_float(w.y);
+    r[2] = __uint_as_float(w.z); r[3] = __uint_as_float(w.w);
+}
+template <> __device__ __forceinline__ void unpack16<PREC_F16>(uint4 w, float *r, float s)
+{
+    const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        __half2 h = *reinterpret_cast<const __half2 *>(&u[k]);
+        float2 f = __half22float2(h);
+        r[2 * k] = f.x * s; r[2 * k + 1] = f.y * s;
+    }
+}
+template <> __device__ __forceinline__ void unpack16<PREC_BF16>(uint4 w, float *r, float s)
+{
+    const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&u[k]);
+        float2 f = __bfloat1622float2(h);
+        r[2 * k] = f.x * s; r[2 * k + 1] = f.y * s;
+    }
+}
+
+template <int P> __device__ __forceinline__ uint4 pack16(const typename Prec<P>::real *r, float inv_scale);
+template <> __device__ __forceinline__ uint4 pack16<PREC_F64>(const double *r, float)
+{
+    uint4 w;
+    w.x = __double2loint(r[0]); w.y = __double2hiint(r[0]);
+    w.z = __double2loint(r[1]); w.w = __double2hiint(r[1]);
+    return w;
+}
+template <> __device__ __forceinline__ uint4 pack16<PREC_F32>(const float *r, float)
+{
+    return make_uint4(__float_as_uint(r[0]), __float_as_uint(r[1]), __float_as_uint(r[2]), __float_as_uint(r[3]));
+}
+template <> __device__ __forceinline__ uint4 pack16<PREC_F16>(const float *r, float is)
+{
+    unsigned u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        __half2 h = __floats2half2_rn(r[2 * k] * is, r[2 * k + 1] * is);
+        u[k] = *reinterpret_cast<unsigned *>(&h);
+    }
+    return make_uint4(u[0], u[1], u[2], u[3]);
+}
+template <> __device__ __forceinline__ uint4 pack16<PREC_BF16>(const float *r, float is)
+{
+    unsigned u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(r[2 * k] * is, r[2 * k + 1] * is);
+        u[k] = *reinterpret_cast<unsigned *>(&h);
+    }
+    return make_uint4(u[0], u[1], u[2], u[3]);
+}
+
+// ---- spinor fields ------------------------------------------------------
+// Half field: planes of 16-byte vectors, plane k at byte offset k*Vh*16; half
+// types then hold an FP32 scale plane.
+template <int P> struct Spinor {
+    using real = typename Prec<P>::real;
+    static constexpr int nplane = 24 / Prec<P>::per16;
+    static constexpr size_t site_bytes = 24 * Prec<P>::bytes + (Prec<P>::scaled ? 4 : 0);
+
+    __device__ static __forceinline__ void load(const char *f, int vh, int i, real (&v)[24])
+    {
+        float s = 1.0f;
+        if (Prec<P>::scaled) s = __ldg(reinterpret_cast<const float *>(f + (size_t)nplane * vh * 16) + i);
+#pragma unroll
+        for (int k = 0; k < nplane; ++k) {
+            uint4 w = ldg16(f + ((size_t)k * vh + i) * 16);
+            unpack16<P>(w, v + k * Prec<P>::per16, s);
+        }
+    }
+    __device__ static __forceinline__ void store(char *f, int vh, int i, const real (&v)[24])
+    {
+        float is = 1.0f;
+        if (Prec<P>::scaled) {
+            float m = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 24; ++k) m = fmaxf(m, fabsf((float)v[k]));
+            reinterpret_cast<float *>(f + (size_t)nplane * vh * 16)[i] = m;
+            is = m > 0.0f ? 1.0f / m : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < nplane; ++k) stg16(f + ((size_t)k * vh + i) * 16, pack16<P>(v + k * Prec<P>::per16, is));
+    }
+};
+
+// ---- gauge links --------------------------------------------------------
+// Per (parity, mu): `nmain` planes of 16-byte vectors, then a tail plane with
+// the remaining reals (8 or 4 bytes per site) when RECON*bytes is not a
+// multiple of 16.  Reals are the row-major matrix entries (re, im), the first
+// RECON of the 18.
+template <int P, int RECON> struct Link {
+    using real = typename Prec<P>::real;
+    static constexpr int per16 = Prec<P>::per16;
+    static constexpr int nmain = RECON / per16;
+    static constexpr int ntail = RECON % per16;   // reals in the tail plane
+    static constexpr size_t site_bytes = (size_t)RECON * Prec<P>::bytes;
+
+    __device__ static __forceinline__ void load_raw(const char *blk, int vh, int i, real (&u)[18])
+    {
+#pragma unroll
+        for (int k = 0; k < nmain; ++k) {
+            uint4 w = ldg16(blk + ((size_t)k * vh + i) * 16);
+            unpack16<P>(w, u + k * per16, 1.0f);
+        }
+        if constexpr (ntail > 0) {
+            const char *tp = blk + (size_t)nmain * vh * 16;
+            if constexpr (P == PREC_F32) {          // 2 floats
+                float2 t = __ldg(reinterpret_cast<const float2 *>(tp) + i);
+                u[nmain * per16] = t.x; u[nmain * per16 + 1] = t.y;
+            } else if constexpr (ntail == 2) {      // 2 halves
+                unsigned t = __ldg(reinterpret_cast<const unsigned *>(tp) + i);
+                float2 f;
+                if constexpr (P == PREC_F16) f = __half22float2(*reinterpret_cast<__half2 *>(&t));
+                else f = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&t));
+                u[nmain * per16] = f.x; u[nmain * per16 + 1] = f.y;
+            } else {                                // 4 halves
+                uint2 t = __ldg(reinterpret_cast<const uint2 *>(tp) + i);
+                float2 f0, f1;
+                if constexpr (P == PREC_F16) {
+                    f0 = __half22float2(*reinterpret_cast<__half2 *>(&t.x));
+                    f1 = __half22float2(*reinterpret_cast<__half2 *>(&t.y));
+                } else {
+                    f0 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&t.x));
+                    f1 = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&t.y));
+                }
+                u[nmain * per16] = f0.x; u[nmain * per16 + 1] = f0.y;
+                u[nmain * per16 + 2] = f1.x; u[nmain * per16 + 3] = f1.y;
+            }
+        }
+    }
+
+    // Full 3x3 matrix; with RECON = 12 the third row is conj(row0 x row1).
+    __device__ static __forceinline__ void load(const char *blk, int vh, int i, cpx<real> (&U)[3][3])
+    {
+        real u[18];
+        load_raw(blk, vh, i, u);
+#pragma unroll
+        for (int r = 0; r < (RECON == 18 ? 3 : 2); ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { U[r][c].re = u[6 * r + 2 * c]; U[r][c].im = u[6 * r + 2 * c + 1]; }
+        if constexpr (RECON == 12) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int a = (c + 1) % 3, b = (c + 2) % 3;
+                cpx<real> t = cmul(U[0][a], U[1][b]);
+                cpx<real> s = cmul(U[0][b], U[1][a]);
+                U[2][c].re = t.re - s.re;
+                U[2][c].im = -(t.im - s.im);
+            }
+        }
+    }
+};
+
+} // namespace wd

@@ -1,0 +1,94 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+
+#include "../../include/wdirac.h"
+
+namespace wd {
+
+// Thread-local error message behind wd_last_error().
+int set_error(int status, const char *fmt, ...);
+void clear_error();
+
+#define WD_CUDA_TRY(expr)                                                                      \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return ::wd::set_error(WD_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                                   __FILE__, __LINE__);                                        \
+    } while (0)
+
+#define WD_TRY(expr)                \
+    do {                            \
+        int s_ = (expr);            \
+        if (s_ != WD_OK) return s_; \
+    } while (0)
+
+struct Geometry {
+    int L[4];
+    int64_t V;
+    int Vh;
+};
+
+// Validates dims (all even, >= 2, Vh < 2^31) and fills g.
+int make_geometry(const int dims[4], Geometry &g);
+bool valid_prec(int prec);
+bool valid_recon(int recon);
+
+// Bytes of one half field (one parity) in a storage precision.
+size_t half_field_bytes(int vh, int prec);
+// Bytes of the links of one (parity, mu) block.
+size_t link_block_bytes(int vh, int prec, int recon);
+
+// Restores the calling thread's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+} // namespace wd
+
+struct wd_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+    std::mutex mu;
+    // launch-shape cache: (kernel id, geometry key) -> threads per block
+    std::map<std::pair<int, int64_t>, int> tuned;
+};
+
+struct wd_gauge {
+    wd_ctx *ctx = nullptr;
+    wd::Geometry geo{};
+    double *canonical = nullptr;   // device, FP64 canonical links (V*4*18 doubles)
+    std::mutex mu;
+    std::map<std::pair<int, int>, char *> layouts;  // (prec, recon) -> device buffer
+};
+
+namespace wd {
+// Device pointer of the (prec, recon) layout, built on first use.
+int gauge_layout(const wd_gauge *g, int prec, int recon, const char **out);
+// Per-(parity, mu) block pointer inside a layout buffer.
+inline const char *link_block(const char *base, int vh, int prec, int recon, int parity, int mu)
+{
+    return base + (size_t)(parity * 4 + mu) * link_block_bytes(vh, prec, recon);
+}
+} // namespace wd

@@ -1,0 +1,164 @@
+"""GPU parity of the Wilson-Dirac kernels against the FP64 oracle (through the C ABI).
+
+Tolerances (relative max error over all reals, vs the FP64 oracle on the
+unrounded inputs): FP64 1e-13, FP32 1e-5, FP16/BF16 storage 3e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1901_07294_gb300 as wd
+import synth
+from tests._gpu import TOL, pack_field, to_dev, unpack_field
+from tests._lattice import parity, rel_max_err, volume
+
+pytestmark = pytest.mark.gpu
+
+ALL_PREC = [wd.F64, wd.F32, wd.F16, wd.BF16]
+# 8^4 (the small parity case), an uneven all-even lattice, and 16^3x32
+DIMS = [(8, 8, 8, 8), (4, 6, 8, 10), (16, 16, 16, 32)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    return wd.Context(0)
+
+
+_cache = {}
+
+
+def _inputs(dims):
+    if dims not in _cache:
+        U = synth.gauge(dims, seed=synth.LINK_SEED_BASE + volume(dims) % 997)
+        psi = synth.spinor(dims, seed=synth.SOURCE_SEED_BASE + 1)
+        _cache[dims] = (U, psi)
+    return _cache[dims]
+
+
+@pytest.mark.parametrize("prec", ALL_PREC)
+def test_pack_unpack_round_trip(ctx, prec):
+    dims = (4, 6, 8, 10)
+    psi = synth.spinor(dims, seed=2011)
+    back = unpack_field(ctx, dims, wd.SITES_FULL, prec, pack_field(ctx, dims, wd.SITES_FULL, prec, psi))
+    if prec == wd.F64:
+        assert np.array_equal(back, psi)
+        return
+    # per-site relative error bound: unit roundoff of the storage type
+    u = {wd.F32: 2.0 ** -24, wd.F16: 2.0 ** -11, wd.BF16: 2.0 ** -8}[prec]
+    site_max = np.max(np.abs(psi.view(np.float64).reshape(-1, 24)), axis=1)
+    err = np.max(np.abs((back - psi).view(np.float64).reshape(-1, 24)), axis=1) / site_max
+    assert np.max(err) <= u * 1.01
+
+
+def test_pack_half_fields_touch_only_their_parity(ctx):
+    dims = (4, 4, 4, 6)
+    psi = synth.spinor(dims, seed=2012)
+    par = parity(dims)
+    for sites, p in ((wd.SITES_EVEN, 0), (wd.SITES_ODD, 1)):
+        back = unpack_field(ctx, dims, sites, wd.F64, pack_field(ctx, dims, sites, wd.F64, psi))
+        assert np.array_equal(back[par == p], psi[par == p])
+        assert np.all(back[par != p] == 0)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("recon", [18, 12])
+@pytest.mark.parametrize("prec", ALL_PREC)
+def test_dslash_full_matches_oracle(ctx, dims, recon, prec):
+    U, psi = _inputs(dims)
+    m = 0.1
+    g = wd.Gauge(ctx, dims, U)
+    fin = pack_field(ctx, dims, wd.SITES_FULL, prec, psi)
+    fout = wd.alloc_field(dims, wd.SITES_FULL, prec)
+    wd.dslash_apply(ctx, g, fout, fin, m, prec=prec, recon=recon)
+    got = unpack_field(ctx, dims, wd.SITES_FULL, prec, fout)
+    ref = oracle.dirac(dims, U, psi, m)
+    err = rel_max_err(got, ref)
+    assert err < TOL[prec], f"err {err:.3e}"
+
+
+@pytest.mark.parametrize("prec", ALL_PREC)
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("out_parity", [0, 1])
+@pytest.mark.parametrize("with_x", [False, True])
+def test_dslash_eo_matches_oracle(ctx, prec, dagger, out_parity, with_x):
+    dims = (4, 6, 8, 10)
+    U, psi = _inputs(dims)
+    xs = synth.spinor(dims, seed=2099)
+    a, b = 1.7, -0.35
+    g = wd.Gauge(ctx, dims, U)
+    p = out_parity
+    in_sites = wd.SITES_ODD if p == 0 else wd.SITES_EVEN
+    out_sites = wd.SITES_EVEN if p == 0 else wd.SITES_ODD
+    fin = pack_field(ctx, dims, in_sites, prec, psi)
+    fx = pack_field(ctx, dims, out_sites, prec, xs) if with_x else None
+    fout = wd.alloc_field(dims, out_sites, prec)
+    wd.dslash_eo_apply(ctx, g, fout, fin, fx, p, a, b, dagger=dagger, prec=prec, recon=18)
+    got = unpack_field(ctx, dims, out_sites, prec, fout)
+    par = parity(dims)
+    src = psi.copy()
+    src[par == p] = 0            # only the 1-p half is an input
+    if dagger:
+        h = oracle.gamma_apply(4, oracle.hop(dims, U, oracle.gamma_apply(4, src), out_parity=p))
+    else:
+        h = oracle.hop(dims, U, src, out_parity=p)
+    ref = b * h + (a * xs if with_x else 0)
+    ref[par != p] = 0
+    err = rel_max_err(got[par == p], ref[par == p])
+    assert err < TOL[prec], f"err {err:.3e}"
+
+
+def test_dslash_multi_rhs_equals_single(ctx):
+    import torch
+    dims = (8, 8, 8, 8)
+    U, _ = _inputs(dims)
+    g = wd.Gauge(ctx, dims, U)
+    nrhs = 3
+    srcs = [synth.spinor(dims, seed=2100 + k) for k in range(nrhs)]
+    nb = wd.field_bytes(dims, wd.SITES_FULL, wd.F32)
+    fin = torch.cat([pack_field(ctx, dims, wd.SITES_FULL, wd.F32, s) for s in srcs])
+    fout = wd.alloc_field(dims, wd.SITES_FULL, wd.F32, nrhs)
+    wd.dslash_apply(ctx, g, fout, fin, 0.1, nrhs=nrhs, prec=wd.F32)
+    for k in range(nrhs):
+        single = wd.alloc_field(dims, wd.SITES_FULL, wd.F32)
+        wd.dslash_apply(ctx, g, single, fin[k * nb:(k + 1) * nb], 0.1, prec=wd.F32)
+        torch.cuda.synchronize()
+        assert torch.equal(single, fout[k * nb:(k + 1) * nb])
+
+
+def test_dslash_32_4_full_size(ctx):
+    """The benchmark launch (32^4, FP32 and FP64, 18 and 12 reals) against the oracle on every site."""
+    dims = (32, 32, 32, 32)
+    U = synth.gauge(dims, seed=1001)
+    psi = synth.spinor(dims, seed=2001)
+    ref = oracle.dirac(dims, U, psi, 0.1)
+    g = wd.Gauge(ctx, dims, U)
+    for prec in (wd.F32, wd.F64):
+        fin = pack_field(ctx, dims, wd.SITES_FULL, prec, psi)
+        fout = wd.alloc_field(dims, wd.SITES_FULL, prec)
+        for recon in (18, 12):
+            wd.dslash_apply(ctx, g, fout, fin, 0.1, prec=prec, recon=recon)
+            err = rel_max_err(unpack_field(ctx, dims, wd.SITES_FULL, prec, fout), ref)
+            assert err < TOL[prec], (prec, recon, err)
+
+
+def test_argument_errors(ctx):
+    import torch
+    dims = (4, 4, 4, 4)
+    U = synth.gauge(dims, seed=1)
+    g = wd.Gauge(ctx, dims, U)
+    f = wd.alloc_field(dims, wd.SITES_FULL, wd.F32)
+    with pytest.raises(wd.WdError) as e:
+        wd.dslash_apply(ctx, g, f, f, 0.1)           # aliasing
+    assert e.value.status == wd.WD_EINVAL
+    big = torch.empty(f.numel() + 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(wd.WdError) as e:
+        wd.dslash_apply(ctx, g, big[4:].data_ptr(), f, 0.1)   # misaligned
+    assert e.value.status == wd.WD_EINVAL
+    with pytest.raises(wd.WdError) as e:
+        wd.dslash_apply(ctx, g, big, f, 0.1, recon=9)
+    assert e.value.status == wd.WD_EINVAL
+    with pytest.raises(wd.WdError) as e:
+        wd.dslash_eo_apply(ctx, g, big, f, None, 2, 1.0, 1.0)
+    assert e.value.status == wd.WD_EINVAL
