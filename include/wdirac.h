@@ -120,9 +120,10 @@ int wd_gauge_destroy(wd_gauge *g);
 /*
  * Full-lattice Wilson-Dirac operator:  out = D in = (m+4) in - H in / 2.
  * `in` and `out` are full fields of precision `prec` (nrhs consecutive
- * fields); the gauge layout (prec, recon) is used (WD_F64 fields need WD_F64
- * links; WD_F32 / WD_F16 / WD_BF16 fields compute in FP32 on links stored in
- * the same precision as the field).  out must not alias in.
+ * fields).  WD_F64 computes in FP64 on FP64 links; WD_F32, WD_F16 and
+ * WD_BF16 compute in FP32 on links stored in the field's precision, except
+ * that WD_BF16 fields use FP16 links (link entries are bounded by 1, so FP16's
+ * 3 extra mantissa bits cost no range).  out must not alias in.
  * Flop count: 1320 per site for H (Eq. (1): 8 directions of spin projection,
  * SU(3) x half-spinor and reconstruction).
  */
@@ -142,6 +143,57 @@ int dslash_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, doub
 int dslash_eo_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, const void *x,
                     int out_parity, double a, double b, int dagger, int nrhs, int prec, int recon,
                     void *stream);
+
+/* ---- BLAS-1 on device fields (sites = wd_sites of the field) ----------------
+ * Reductions accumulate each site's 24 reals in the field's compute type,
+ * then sum sites in FP64 (warp shuffles, per-block partials in the context's
+ * scratch, fixed-order final sum), so repeated calls are bitwise identical.
+ * `result` is device memory.  Calls on one context must not overlap on the
+ * GPU (they share the context's scratch). */
+int wd_norm2(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *x, double *result,
+             void *stream);                                    /* result[0] = |x|^2 */
+int wd_dot(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *a, const void *b,
+           double *result, void *stream);                      /* result = <a,b> = sum conj(a) b (re, im) */
+int wd_axpby(wd_ctx *ctx, const int dims[4], int sites, int prec, double a, const void *x, double b,
+             void *y, void *stream);                           /* y = a x + b y */
+int wd_convert(wd_ctx *ctx, const int dims[4], int sites, int prec_out, void *out, int prec_in,
+               const void *in, void *stream);                  /* out = in, new storage precision */
+
+/* ---- Conjugate gradient (Sec. II-A: CG solves the Dirac system) ------------
+ * Solves  Mhat^dagger Mhat x = b  on the even sites, where
+ *     Mhat = (m+4) - H_eo H_oe / (4(m+4))
+ * is the Schur complement of D = (m+4) - H/2 and Mhat^dagger = gamma5 Mhat
+ * gamma5.  x_e and b_e are even half fields in WD_F64 (device).  x_0 = 0.
+ * Converged when the true residual |b - A x| / |b| <= tol, computed in FP64.
+ * inner_prec = WD_F64: plain FP64 CG.  Otherwise mixed precision: the
+ * iterated residual, search direction and operator use inner_prec storage
+ * (FP32 arithmetic), while the solution, true residual and all inner products
+ * are FP64.  reliable = 1: reliable updates (Sleijpen-van der Vorst) when the
+ * iterated residual has dropped by `delta` since the last update;
+ * reliable = 0: iterative refinement with restarted inner solves to relative
+ * residual `delta`.  Synchronous; uses a workspace owned by the context
+ * (allocated on first use, grown when a larger lattice needs more).
+ * Returns WD_ENOCONV (stats still filled) if maxiter inner iterations pass
+ * without convergence or the iteration breaks down. */
+typedef struct {
+    int inner_prec;    /* wd_prec of the inner operator and vectors */
+    int inner_recon;   /* 18 or 12: links of the inner operator */
+    int outer_recon;   /* 18 or 12: links of the FP64 operator */
+    int reliable;      /* 1 reliable updates, 0 iterative refinement */
+    double delta;      /* see above; ignored for inner_prec = WD_F64 */
+    int maxiter;       /* limit on inner iterations */
+} wd_cg_opts;
+
+typedef struct {
+    int iters;             /* inner iterations */
+    int reliable_updates;  /* FP64 true-residual recomputations */
+    int status;            /* wd_status of the solve */
+    double true_rel_resid; /* final |b - A x| / |b|, FP64 */
+    double seconds;        /* host wall time of the call */
+} wd_cg_stats;
+
+int cg_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x_e, const void *b_e, double tol,
+             const wd_cg_opts *opts, wd_cg_stats *stats, void *stream);
 
 #ifdef __cplusplus
 }

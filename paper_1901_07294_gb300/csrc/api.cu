@@ -4,6 +4,7 @@
 #include <cstring>
 #include <new>
 
+#include "blas.cuh"
 #include "wd_device.cuh"
 #include "wd_internal.h"
 
@@ -173,11 +174,32 @@ static int sites_to_map(const Geometry &g, int sites, int prec, SiteMap &m)
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+int ctx_workspace(wd_ctx *ctx, size_t bytes, char **out)
+{
+    if (ctx->work_bytes < bytes) {
+        DeviceGuard dg(ctx->device);
+        if (ctx->d_work) {
+            cudaDeviceSynchronize();
+            cudaFree(ctx->d_work);
+            ctx->d_work = nullptr;
+            ctx->work_bytes = 0;
+        }
+        if (cudaMalloc(&ctx->d_work, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(WD_ENOMEM, "cudaMalloc of %zu bytes of solver workspace failed", bytes);
+        }
+        ctx->work_bytes = bytes;
+    }
+    *out = ctx->d_work;
+    return WD_OK;
+}
+
 int gauge_layout(const wd_gauge *gc, int prec, int recon, const char **out)
 {
     wd_gauge *g = const_cast<wd_gauge *>(gc);
     if (!valid_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
     if (!valid_recon(recon)) return set_error(WD_EINVAL, "bad reconstruction %d (use 18 or 12)", recon);
+    prec = link_prec(prec);   // BF16 fields use FP16 links
     std::lock_guard<std::mutex> lk(g->mu);
     auto key = std::make_pair(prec, recon);
     auto it = g->layouts.find(key);
@@ -204,8 +226,6 @@ int gauge_layout(const wd_gauge *gc, int prec, int recon, const char **out)
     case WD_F32 * 100 + 12: WD_PACK_LINKS(PREC_F32, 12); break;
     case WD_F16 * 100 + 18: WD_PACK_LINKS(PREC_F16, 18); break;
     case WD_F16 * 100 + 12: WD_PACK_LINKS(PREC_F16, 12); break;
-    case WD_BF16 * 100 + 18: WD_PACK_LINKS(PREC_BF16, 18); break;
-    case WD_BF16 * 100 + 12: WD_PACK_LINKS(PREC_BF16, 12); break;
     }
 #undef WD_PACK_LINKS
     cudaError_t e = cudaGetLastError();
@@ -249,6 +269,19 @@ int wd_ctx_create(int device, wd_ctx **out)
     c->num_sms = prop.multiProcessorCount;
     c->cc_major = prop.major;
     c->cc_minor = prop.minor;
+    {
+        DeviceGuard dg(device);
+        const size_t pbytes = (size_t)MAX_RED_BLOCKS * MAX_NR * sizeof(double);
+        if (cudaMalloc(&c->d_partials, pbytes) != cudaSuccess || cudaMalloc(&c->d_ticket, 256) != cudaSuccess ||
+            cudaMalloc(&c->d_scal, NSCAL * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&c->h_scal, NSCAL * sizeof(double)) != cudaSuccess ||
+            cudaMemset(c->d_ticket, 0, 256) != cudaSuccess || cudaMemset(c->d_scal, 0, NSCAL * sizeof(double)) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess) {
+            cudaGetLastError();
+            wd_ctx_destroy(c);
+            return set_error(WD_ENOMEM, "allocating the context scratch failed");
+        }
+    }
     *out = c;
     return WD_OK;
 }
@@ -256,6 +289,15 @@ int wd_ctx_create(int device, wd_ctx **out)
 int wd_ctx_destroy(wd_ctx *ctx)
 {
     clear_error();
+    if (!ctx) return WD_OK;
+    {
+        DeviceGuard dg(ctx->device);
+        cudaFree(ctx->d_partials);
+        cudaFree(ctx->d_ticket);
+        cudaFree(ctx->d_scal);
+        cudaFree(ctx->d_work);
+        if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+    }
     delete ctx;
     return WD_OK;
 }
@@ -372,7 +414,7 @@ int wd_gauge_bytes(const wd_gauge *g, int prec, int recon, size_t *out)
     clear_error();
     if (!g || !out) return set_error(WD_EINVAL, "NULL argument");
     if (!valid_prec(prec) || !valid_recon(recon)) return set_error(WD_EINVAL, "bad precision or reconstruction");
-    *out = 8 * link_block_bytes(g->geo.Vh, prec, recon);
+    *out = 8 * link_block_bytes(g->geo.Vh, link_prec(prec), recon);
     return WD_OK;
 }
 

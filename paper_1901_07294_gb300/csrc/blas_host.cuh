@@ -1,0 +1,31 @@
+// Host-side launcher of the BLAS-1 kernels (shared by the BLAS entry points and the solvers).
+#pragma once
+
+#include "blas.cuh"
+#include "wd_internal.h"
+
+namespace wd {
+
+template <int P> inline FieldRef<P> field_ref(const void *p, int vh)
+{
+    return FieldRef<P>{(char *)p, half_field_bytes(vh, P), vh};
+}
+
+inline int blas_grid(const wd_ctx *ctx, int nsite)
+{
+    int want = (nsite + BLAS_THREADS - 1) / BLAS_THREADS;
+    int cap = 4 * (ctx->num_sms > 0 ? ctx->num_sms : 132);
+    if (cap > MAX_RED_BLOCKS) cap = MAX_RED_BLOCKS;
+    return want < cap ? (want > 0 ? want : 1) : cap;
+}
+
+template <typename Op> int run_blas(const wd_ctx *ctx, const Op &op, int nsite, cudaStream_t s)
+{
+    RedScratch rs{ctx->d_partials, ctx->d_ticket};
+    blas_kernel<Op><<<blas_grid(ctx, nsite), BLAS_THREADS, 0, s>>>(op, nsite, rs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(WD_ECUDA, "BLAS kernel launch failed: %s", cudaGetErrorString(e));
+    return WD_OK;
+}
+
+} // namespace wd

@@ -34,12 +34,28 @@ int hop_setup(const wd_gauge *g, int prec, int recon, HopArgs &A)
     const char *base = nullptr;
     WD_TRY(gauge_layout(g, prec, recon, &base));
     const int vh = g->geo.Vh;
-    A.link_blk = link_block_bytes(vh, prec, recon);
+    A.link_blk = link_block_bytes(vh, link_prec(prec), recon);
     A.gauge[0] = base;
     A.gauge[1] = base + 4 * A.link_blk;
     for (int mu = 0; mu < 4; ++mu) A.L[mu] = g->geo.L[mu];
     A.vh = vh;
     return WD_OK;
+}
+
+int eo_hop(const wd_gauge *g, int prec, int recon, void *out, const void *in, const void *x, int p, double a,
+           double b, int dagger, cudaStream_t s)
+{
+    HopArgs A{};
+    WD_TRY(hop_setup(g, prec, recon, A));
+    A.in[0] = A.in[1] = (const char *)in;
+    A.x[0] = A.x[1] = (const char *)x;
+    A.out[0] = A.out[1] = (char *)out;
+    A.rhs_stride = half_field_bytes(A.vh, prec);
+    A.nparity = 1;
+    A.parity0 = p;
+    A.a = a;
+    A.b = b;
+    return hop_launch(A, prec, recon, dagger ? 1 : 0, 1, s);
 }
 
 } // namespace wd

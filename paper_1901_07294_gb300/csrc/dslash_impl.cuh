@@ -107,7 +107,7 @@ __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh
     cpx<T> h0[3], h1[3];
     project<MU, S>(psi, h0, h1);
     cpx<T> U[3][3];
-    Link<P, RECON>::load(lblk, vh, li, U);
+    Link<link_prec(P), RECON>::load(lblk, vh, li, U);
     cpx<T> w0[3], w1[3];
     su3_mul<FWD>(U, h0, w0);
     su3_mul<FWD>(U, h1, w1);

@@ -20,6 +20,11 @@ template <> struct Prec<PREC_BF16>{ using real = float;  static constexpr int pe
 
 template <typename T> struct cpx { T re, im; };
 
+// Storage precision of the links that go with fields of precision P.  Link
+// entries are bounded by 1 in magnitude, so they need no exponent range; for
+// BF16 fields they are kept in FP16, which has 3 more mantissa bits.
+__host__ __device__ constexpr int link_prec(int p) { return p == PREC_BF16 ? PREC_F16 : p; }
+
 // z + x*y and z + conj(x)*y with real FMAs (the two complex multiply-add
 // forms of Sec. III-D, Eq. (2), which SVE gets from a pair of FCMLA).
 template <typename T> __device__ __forceinline__ cpx<T> cfma(cpx<T> x, cpx<T> y, cpx<T> z)

@@ -71,6 +71,14 @@ struct wd_ctx {
     int num_sms = 0;
     int cc_major = 0, cc_minor = 0;
     std::mutex mu;
+    // reduction scratch (device): partial sums, a ticket counter and result slots
+    double *d_partials = nullptr;
+    unsigned *d_ticket = nullptr;
+    double *d_scal = nullptr;      // wd::NSCAL result slots
+    double *h_scal = nullptr;      // pinned host mirror of d_scal
+    // solver workspace (device), grown on demand
+    char *d_work = nullptr;
+    size_t work_bytes = 0;
     // launch-shape cache: (kernel id, geometry key) -> threads per block
     std::map<std::pair<int, int64_t>, int> tuned;
 };
@@ -84,6 +92,12 @@ struct wd_gauge {
 };
 
 namespace wd {
+constexpr int NSCAL = 64;
+// Even-odd hop on half fields: out_p = a x_p + b H^(d)_{p,1-p} in (see dslash_eo_apply).
+int eo_hop(const wd_gauge *g, int prec, int recon, void *out, const void *in, const void *x, int p, double a,
+           double b, int dagger, cudaStream_t s);
+// Solver workspace of at least `bytes` bytes (device), owned by the context.
+int ctx_workspace(wd_ctx *ctx, size_t bytes, char **out);
 // Device pointer of the (prec, recon) layout, built on first use.
 int gauge_layout(const wd_gauge *g, int prec, int recon, const char **out);
 // Per-(parity, mu) block pointer inside a layout buffer.
