@@ -282,6 +282,9 @@ def run_gpu(args):
     variants = {}
     if not args.no_variants:
         variants = _variants(wd, torch, ctx, dims, U, psi, stream, peak)
+    cg = None
+    if not args.no_cg:
+        cg = _cg_section(wd, torch, ctx, with_cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline))
 
     line = {
         "metric": "dslash_hbm_gbs", "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
@@ -303,6 +306,7 @@ def run_gpu(args):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "variants": variants,
+        "cg": cg,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline()
@@ -365,6 +369,61 @@ def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, reps=50
     return out
 
 
+def _cg_section(wd, torch, ctx, with_cpu: bool):
+    """Mixed-precision vs FP64 CG on the even-odd normal equations, 24^3x48, tol 1e-10."""
+    import numpy as np
+
+    import synth
+    dims = (24, 24, 24, 48)
+    U = synth.gauge(dims, seed=1000 + 3)
+    b = synth.even_spinor(dims, seed=3001)
+    g = wd.Gauge(ctx, dims, U)
+    fb = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+    wd.pack(ctx, dims, wd.SITES_EVEN, wd.F64, torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
+    fx = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+    runs = [("fp64", dict(inner_prec=wd.F64)),
+            ("fp32", dict(inner_prec=wd.F32, reliable=True, delta=0.1)),
+            ("fp16", dict(inner_prec=wd.F16, reliable=True, delta=0.1)),
+            ("bf16", dict(inner_prec=wd.BF16, reliable=True, delta=0.1)),
+            ("fp16_r12", dict(inner_prec=wd.F16, inner_recon=12, reliable=True, delta=0.1)),
+            ("fp16_refine", dict(inner_prec=wd.F16, reliable=False, delta=1e-3))]
+    out = {"lattice": list(dims), "tol": 1e-10, "source": "Gaussian on even sites, seed 3001", "runs": {}}
+    for mass in (0.1, 0.05):
+        for name, kw in runs:
+            wd.cg_solve(ctx, g, mass, fx, fb, tol=1e-10, maxiter=20000, **kw)   # warm (layouts, workspace)
+            best = None
+            for _ in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st = wd.cg_solve(ctx, g, mass, fx, fb, tol=1e-10, maxiter=20000, **kw)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                if best is None or ms < best[0]:
+                    best = (ms, st)
+            ms, st = best
+            out["runs"][f"m{mass}/{name}"] = {"seconds": round(ms / 1e3, 5), "iters": st["iters"],
+                                              "reliable_updates": st["reliable_updates"],
+                                              "true_rel_resid": st["true_rel_resid"]}
+    for mass in (0.1, 0.05):
+        t64 = out["runs"][f"m{mass}/fp64"]["seconds"]
+        out[f"speedup_fp16_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/fp16"]["seconds"], 2)
+        out[f"speedup_bf16_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/bf16"]["seconds"], 2)
+    if with_cpu:
+        import oracle
+        oracle.mdagm(dims, U, 0.1, b)
+        t0 = time.perf_counter()
+        for _ in range(2):
+            oracle.mdagm(dims, U, 0.1, b)
+        per_it = (time.perf_counter() - t0) / 2
+        it64 = out["runs"]["m0.1/fp64"]["iters"]
+        out["cpu_oracle_cg_estimate"] = {
+            "seconds": round(per_it * it64, 2), "cores": oracle.max_threads(),
+            "how": f"oracle Mhat^dagger Mhat time per application ({per_it:.3f} s, 2 reps) x {it64} FP64 GPU iterations"}
+    g.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,6 +432,7 @@ def main():
     ap.add_argument("--impl", default="wdirac", choices=["wdirac", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cg", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -53,7 +53,27 @@ _SIGS = {
     "wd_gauge_destroy": (_ip, [_vp]),
     "dslash_apply": (_ip, [_vp, _vp, _vp, _vp, _dp, _ip, _ip, _ip, _vp]),
     "dslash_eo_apply": (_ip, [_vp, _vp, _vp, _vp, _vp, _ip, _dp, _dp, _ip, _ip, _ip, _ip, _vp]),
+    "wd_norm2": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _vp, _vp]),
+    "wd_dot": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _vp, _vp, _vp]),
+    "wd_axpby": (_ip, [_vp, _DIMS, _ip, _ip, _dp, _vp, _dp, _vp, _vp]),
+    "wd_convert": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _ip, _vp, _vp]),
+    "cg_solve": (_ip, [_vp, _vp, _dp, _vp, _vp, _dp, _vp, _vp, _vp]),
 }
+
+
+class CgOpts(ctypes.Structure):
+    """wd_cg_opts"""
+    _fields_ = [("inner_prec", _ip), ("inner_recon", _ip), ("outer_recon", _ip), ("reliable", _ip),
+                ("delta", _dp), ("maxiter", _ip)]
+
+
+class CgStats(ctypes.Structure):
+    """wd_cg_stats"""
+    _fields_ = [("iters", _ip), ("reliable_updates", _ip), ("status", _ip), ("true_rel_resid", _dp),
+                ("seconds", _dp)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def exported_symbols() -> list[str]:
@@ -214,3 +234,43 @@ def dslash_eo_apply(ctx: Context, gauge: Gauge, out, inp, x, out_parity: int, a:
     _check(load().dslash_eo_apply(ctx.handle, gauge.handle, _ptr(out), _ptr(inp), _ptr(x), int(out_parity),
                                   float(a), float(b), int(bool(dagger)), int(nrhs), int(prec), int(recon),
                                   _stream(stream)))
+
+
+def norm2(ctx: Context, dims, sites: int, prec: int, x, result, stream=None) -> None:
+    """result[0] = |x|^2 (FP64, device tensor of >= 1 float64)."""
+    _check(load().wd_norm2(ctx.handle, _dims(dims), int(sites), int(prec), _ptr(x), _ptr(result), _stream(stream)))
+
+
+def dot(ctx: Context, dims, sites: int, prec: int, a, b, result, stream=None) -> None:
+    """result[0:2] = <a, b> = sum conj(a) b (FP64 re, im; device tensor)."""
+    _check(load().wd_dot(ctx.handle, _dims(dims), int(sites), int(prec), _ptr(a), _ptr(b), _ptr(result),
+                         _stream(stream)))
+
+
+def axpby(ctx: Context, dims, sites: int, prec: int, a: float, x, b: float, y, stream=None) -> None:
+    """y = a x + b y."""
+    _check(load().wd_axpby(ctx.handle, _dims(dims), int(sites), int(prec), float(a), _ptr(x), float(b), _ptr(y),
+                           _stream(stream)))
+
+
+def convert(ctx: Context, dims, sites: int, prec_out: int, out, prec_in: int, inp, stream=None) -> None:
+    """out = in with a change of storage precision."""
+    _check(load().wd_convert(ctx.handle, _dims(dims), int(sites), int(prec_out), _ptr(out), int(prec_in), _ptr(inp),
+                             _stream(stream)))
+
+
+def cg_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-10, inner_prec: int = F64,
+             inner_recon: int = 18, outer_recon: int = 18, reliable: bool = True, delta: float = 0.1,
+             maxiter: int = 20000, stream=None, check: bool = True) -> dict:
+    """Solve Mhat^dagger Mhat x = b on even half fields (FP64).  Returns the solve statistics;
+    raises WdError on failure unless check=False (then 'status' carries the code)."""
+    opts = CgOpts(int(inner_prec), int(inner_recon), int(outer_recon), int(bool(reliable)), float(delta),
+                  int(maxiter))
+    st = CgStats()
+    rc = load().cg_solve(ctx.handle, gauge.handle, float(mass), _ptr(x), _ptr(b), float(tol), ctypes.byref(opts),
+                         ctypes.byref(st), _stream(stream))
+    if check:
+        _check(rc)
+    out = st.as_dict()
+    out["status"] = rc
+    return out

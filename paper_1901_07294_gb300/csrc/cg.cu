@@ -91,8 +91,10 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
     WD_CUDA_TRY(cudaMemsetAsync(xs, 0, hx, s));
 
     const double stop2 = tol * tol * b2;
-    const bool reliable = o.reliable != 0;
-    const double delta = o.delta;
+    // plain FP64 CG: the iterated residual is already FP64, so the true
+    // residual is recomputed only to confirm convergence
+    const bool reliable = PS == PREC_F64 ? true : o.reliable != 0;
+    const double delta = PS == PREC_F64 ? 0.0 : o.delta;
     double r2 = b2, maxr = std::sqrt(b2), r2_restart = b2, r2_true = b2;
     bool converged = false;
     int status = WD_OK;

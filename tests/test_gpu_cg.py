@@ -1,0 +1,127 @@
+"""CG solves on the GPU against the FP64 oracle.
+
+A solve is judged by its true residual |b - A x| / |b| computed by the oracle's
+own operator on the GPU solution (the bar: the tolerance asked for, 1e-10 here),
+and by the distance to the oracle CG solution, which agrees to about
+cond(A) * tol.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1901_07294_gb300 as wd
+import synth
+from tests._gpu import pack_field, unpack_field
+from tests._lattice import parity, rel_max_err, volume
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return wd.Context(0)
+
+
+_cache = {}
+
+
+def _problem(dims, mass):
+    key = (dims, mass)
+    if key not in _cache:
+        U = synth.gauge(dims, seed=1000 + volume(dims) % 991)
+        b = synth.even_spinor(dims, seed=3001)
+        xo, it, rel = oracle.cg(dims, U, mass, b, tol=1e-11)
+        assert it > 0 and rel <= 1e-11
+        _cache[key] = (U, b, xo)
+    return _cache[key]
+
+
+def _solve(ctx, dims, mass, tol, **kw):
+    U, b, xo = _problem(dims, mass)
+    g = wd.Gauge(ctx, dims, U)
+    fb = pack_field(ctx, dims, wd.SITES_EVEN, wd.F64, b)
+    fx = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+    st = wd.cg_solve(ctx, g, mass, fx, fb, tol=tol, **kw)
+    x = unpack_field(ctx, dims, wd.SITES_EVEN, wd.F64, fx)
+    r = b - oracle.mdagm(dims, U, mass, x)
+    true_rel = float(np.linalg.norm(r) / np.linalg.norm(b))
+    return st, x, xo, true_rel
+
+
+CASES = [
+    dict(inner_prec=wd.F64),
+    dict(inner_prec=wd.F32, reliable=True, delta=0.1),
+    dict(inner_prec=wd.F16, reliable=True, delta=0.1),
+    dict(inner_prec=wd.BF16, reliable=True, delta=0.1),
+    dict(inner_prec=wd.F16, inner_recon=12, reliable=True, delta=0.1),
+    dict(inner_prec=wd.F32, reliable=False, delta=1e-4),
+    dict(inner_prec=wd.F16, reliable=False, delta=1e-3),
+]
+
+
+@pytest.mark.parametrize("kw", CASES, ids=lambda k: "-".join(f"{a}{b}" for a, b in k.items()))
+@pytest.mark.parametrize("dims,mass", [((8, 8, 8, 8), 0.1), ((4, 6, 8, 10), 0.05)])
+def test_cg_reaches_true_residual(ctx, dims, mass, kw):
+    tol = 1e-10
+    st, x, xo, true_rel = _solve(ctx, dims, mass, tol, **kw)
+    assert st["status"] == 0
+    assert st["true_rel_resid"] <= tol
+    assert true_rel <= 1.05 * tol, true_rel          # checked with the oracle operator
+    par = parity(dims)
+    assert np.all(x[par == 1] == 0)
+    assert rel_max_err(x, xo) < 1e-6
+
+
+def test_mixed_iterations_close_to_fp64(ctx):
+    dims, mass = (8, 8, 8, 8), 0.1
+    st64 = _solve(ctx, dims, mass, 1e-10, inner_prec=wd.F64)[0]
+    st16 = _solve(ctx, dims, mass, 1e-10, inner_prec=wd.F16, reliable=True, delta=0.1)[0]
+    assert st16["reliable_updates"] >= 2
+    assert st16["iters"] < 2 * st64["iters"]
+
+
+def test_cg_not_converged_reports_enoconv(ctx):
+    dims, mass = (8, 8, 8, 8), 0.1
+    U, b, _ = _problem(dims, mass)
+    g = wd.Gauge(ctx, dims, U)
+    fb = pack_field(ctx, dims, wd.SITES_EVEN, wd.F64, b)
+    fx = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+    st = wd.cg_solve(ctx, g, mass, fx, fb, tol=1e-10, inner_prec=wd.F64, maxiter=3, check=False)
+    assert st["status"] == wd.WD_ENOCONV and st["iters"] == 3
+    assert 1e-10 < st["true_rel_resid"] < 1.0
+
+
+def test_cg_zero_source(ctx):
+    dims = (4, 4, 4, 4)
+    U = synth.gauge(dims, seed=3)
+    g = wd.Gauge(ctx, dims, U)
+    fb = pack_field(ctx, dims, wd.SITES_EVEN, wd.F64, np.zeros((volume(dims), 4, 3), np.complex128))
+    fx = pack_field(ctx, dims, wd.SITES_EVEN, wd.F64, synth.spinor(dims, seed=4))
+    st = wd.cg_solve(ctx, g, 0.1, fx, fb, tol=1e-10, inner_prec=wd.F16)
+    assert st["iters"] == 0 and st["true_rel_resid"] == 0.0
+    assert np.all(unpack_field(ctx, dims, wd.SITES_EVEN, wd.F64, fx) == 0)
+
+
+def test_cg_free_field_closed_form(ctx):
+    """Unit links: the solution is the momentum-space inverse on even-restricted plane waves."""
+    from tests._lattice import golden_gammas, plane_wave
+    G = golden_gammas()
+    dims, m = (8, 4, 4, 8), 0.2
+    U = synth.unit_gauge(dims)
+    par = parity(dims)
+    n = (3, 1, 2, 5)
+    p = 2 * np.pi * np.asarray(n) / np.asarray(dims)
+    I4 = np.eye(4)
+    Hp = 2 * np.sum(np.cos(p)) * I4 - 2j * sum(G[mu] * np.sin(p[mu]) for mu in range(4))
+    Mp = (m + 4) * I4 - Hp @ Hp / (4 * (m + 4))
+    u = np.random.default_rng(5).standard_normal((4, 3)) + 1j * np.random.default_rng(6).standard_normal((4, 3))
+    b = plane_wave(dims, n, u)
+    b[par == 1] = 0
+    xs = plane_wave(dims, n, np.linalg.solve(Mp.conj().T @ Mp, u))
+    xs[par == 1] = 0
+    g = wd.Gauge(ctx, dims, U)
+    fb = pack_field(ctx, dims, wd.SITES_EVEN, wd.F64, b)
+    fx = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+    wd.cg_solve(ctx, g, m, fx, fb, tol=1e-12, inner_prec=wd.F32, reliable=True, delta=0.1)
+    x = unpack_field(ctx, dims, wd.SITES_EVEN, wd.F64, fx)
+    assert rel_max_err(x, xs) < 1e-10
