@@ -58,6 +58,7 @@ _SIGS = {
     "wd_axpby": (_ip, [_vp, _DIMS, _ip, _ip, _dp, _vp, _dp, _vp, _vp]),
     "wd_convert": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _ip, _vp, _vp]),
     "cg_solve": (_ip, [_vp, _vp, _dp, _vp, _vp, _dp, _vp, _vp, _vp]),
+    "wd_norm2_noalloc": (_ip, [_DIMS, _ip, _ip, _vp, _vp, _vp]),
 }
 
 
@@ -274,3 +275,14 @@ def cg_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-10, 
     out = st.as_dict()
     out["status"] = rc
     return out
+
+
+def norm2_noalloc(dims, sites: int, prec: int, x, result, stream=None) -> None:
+    """result[0] = |x|^2 without any device allocation and without a context.
+
+    For callers that must not allocate (inside a global-mode graph capture of
+    another component, under a host framework that owns all device memory, or in
+    latency-critical loops).  Uses a fixed scratch array in the library; fields
+    larger than 2,097,152 sites are rejected; concurrent calls race.  The first
+    call on a device does a one-time address lookup: make it before any capture."""
+    _check(load().wd_norm2_noalloc(_dims(dims), int(sites), int(prec), _ptr(x), _ptr(result), _stream(stream)))
