@@ -142,7 +142,7 @@ def _dist():
     return ws, rank, local
 
 
-def _cpu_baseline(samples_dims=(8, 8, 8, 8), min_seconds=10.0, max_reps=400):
+def _cpu_baseline(samples_dims=(8, 8, 8, 8), min_seconds=10.0, max_reps=1_000_000):
     """FP64 oracle D on the host cores, in the same GB/s unit (480 B per site)."""
     import oracle
     import synth
@@ -184,8 +184,10 @@ def run_reference(args):
         "impl": "reference", "metric": "dslash_hbm_gbs", "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "wilson_dslash_full_fp64_oracle_sample_8x8x8x8", "lattice": list(dims),
-                   "mass": MASS, "link_seed": LINK_SEED, "source_seed": SRC_SEED},
+        "config": {"workload": "wilson_dslash_full_fp32_recon18_32x32x32x32", "lattice": list(DIMS),
+                   "sample_lattice": list(dims), "mass": MASS, "link_seed": LINK_SEED, "source_seed": SRC_SEED,
+                   "note": "each step is a bounded sample of the workload: one D on an 8^4 lattice of the "
+                           "same recipe, timed per site in the same unit"},
         "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": oracle.max_threads(), "kind": "oracle",
                          "sample": f"one step = FP64 oracle D on 8^4 ({v} sites); GB/s = sites/s x 480 B"},
         "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -218,6 +220,8 @@ def run_gpu(args):
     aos = psi_host.cuda()
     prec, recon = wd.F32, 18
     g.prepare(prec, recon)
+    tune_table = wd.tune_dslash(ctx, g, prec, recon, full=True)   # the autotuner picks the launch shape
+    best = min(tune_table, key=lambda t: t["ms"])
     fin = wd.alloc_field(dims, wd.SITES_FULL, prec)
     fout = wd.alloc_field(dims, wd.SITES_FULL, prec)
     wd.pack(ctx, dims, wd.SITES_FULL, prec, aos, fin)
@@ -303,6 +307,9 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": v * 24 * 8,
                 "d2h_bytes_per_step": v * 24 * 8, "ms_per_step": e2e_ms,
                 "path": "pinned H2D FP64 canonical -> wd.pack -> wd.dslash_apply -> wd.unpack -> D2H"},
+        "autotune": {"chosen": {"threads": best["threads"], "variant": best["variant"]},
+                     "candidates_us": {f"{t['threads']}/v{t['variant']}": round(t["ms"] * 1e3, 1)
+                                       for t in tune_table}},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "variants": variants,
@@ -342,6 +349,8 @@ def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, reps=50
             eo_out = wd.alloc_field(dims, wd.SITES_EVEN, prec)
             for recon in (18, 12):
                 g.prepare(prec, recon)
+                wd.tune_dslash(ctx, g, prec, recon, full=True)
+                wd.tune_dslash(ctx, g, prec, recon, full=False, with_x=False)
                 for kind in ("full", "eo"):
                     if kind == "full":
                         fn = lambda: wd.dslash_apply(ctx, g, full_out, full_in, MASS, prec=prec, recon=recon,
@@ -390,7 +399,7 @@ def _cg_section(wd, torch, ctx, with_cpu: bool):
     out = {"lattice": list(dims), "tol": 1e-10, "source": "Gaussian on even sites, seed 3001", "runs": {}}
     for mass in (0.1, 0.05):
         for name, kw in runs:
-            wd.cg_solve(ctx, g, mass, fx, fb, tol=1e-10, maxiter=20000, **kw)   # warm (layouts, workspace)
+            wd.cg_solve(ctx, g, mass, fx, fb, tol=1e-10, maxiter=20000, autotune=True, **kw)   # warm: layouts, workspace, tuning
             best = None
             for _ in range(2):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -144,6 +144,32 @@ int dslash_eo_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, c
                     int out_parity, double a, double b, int dagger, int nrhs, int prec, int recon,
                     void *stream);
 
+/* ---- Autotuning of the operator launches ------------------------------------
+ * The hop kernel has tunable launch parameters: threads per block (32..256,
+ * multiple of 32) and a memory-schedule variant (0: directions x+,x-,..,t-
+ * with no prefetch; 1: backward directions first with the forward links and
+ * t-forward neighbour prefetched into L2; 2: as 1 plus the backward links).
+ * wd_tune_dslash times every candidate for one problem shape (full = 1: the
+ * dslash_apply shape; full = 0: dslash_eo_apply with (with_x = 1) or without
+ * the x term) on private scratch fields (allocated and freed by the call),
+ * stores the fastest in the context and, if WD_TUNE_CACHE names a file,
+ * appends it there (new contexts read that file).  Up to table_len timings
+ * are written to `table`.  Synchronous.  Results of tuned and untuned
+ * launches can differ in the last bits (the summation order of the eight
+ * directions depends on the variant).  wd_tune_set_dslash pins a
+ * configuration; wd_tune_clear forgets all of them. */
+typedef struct {
+    int threads;
+    int variant;
+    double ms;   /* mean time per launch */
+} wd_tune_entry;
+
+int wd_tune_dslash(wd_ctx *ctx, const wd_gauge *g, int prec, int recon, int full, int with_x, int nrhs,
+                   wd_tune_entry *table, int table_len, int *n_out);
+int wd_tune_set_dslash(wd_ctx *ctx, const wd_gauge *g, int prec, int recon, int full, int with_x, int nrhs,
+                       int threads, int variant);
+int wd_tune_clear(wd_ctx *ctx);
+
 /* ---- BLAS-1 on device fields (sites = wd_sites of the field) ----------------
  * Reductions accumulate each site's 24 reals in the field's compute type,
  * then sum sites in FP64 (warp shuffles, per-block partials in the context's
@@ -200,6 +226,7 @@ typedef struct {
     int reliable;      /* 1 reliable updates, 0 iterative refinement */
     double delta;      /* see above; ignored for inner_prec = WD_F64 */
     int maxiter;       /* limit on inner iterations */
+    int autotune;      /* 1: tune the hop launches the solve uses (once per context) */
 } wd_cg_opts;
 
 typedef struct {

@@ -59,13 +59,21 @@ _SIGS = {
     "wd_convert": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _ip, _vp, _vp]),
     "cg_solve": (_ip, [_vp, _vp, _dp, _vp, _vp, _dp, _vp, _vp, _vp]),
     "wd_norm2_noalloc": (_ip, [_DIMS, _ip, _ip, _vp, _vp, _vp]),
+    "wd_tune_dslash": (_ip, [_vp, _vp, _ip, _ip, _ip, _ip, _ip, _vp, _ip, ctypes.POINTER(_ip)]),
+    "wd_tune_set_dslash": (_ip, [_vp, _vp, _ip, _ip, _ip, _ip, _ip, _ip, _ip]),
+    "wd_tune_clear": (_ip, [_vp]),
 }
+
+
+class TuneEntry(ctypes.Structure):
+    """wd_tune_entry"""
+    _fields_ = [("threads", _ip), ("variant", _ip), ("ms", _dp)]
 
 
 class CgOpts(ctypes.Structure):
     """wd_cg_opts"""
     _fields_ = [("inner_prec", _ip), ("inner_recon", _ip), ("outer_recon", _ip), ("reliable", _ip),
-                ("delta", _dp), ("maxiter", _ip)]
+                ("delta", _dp), ("maxiter", _ip), ("autotune", _ip)]
 
 
 class CgStats(ctypes.Structure):
@@ -262,11 +270,11 @@ def convert(ctx: Context, dims, sites: int, prec_out: int, out, prec_in: int, in
 
 def cg_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-10, inner_prec: int = F64,
              inner_recon: int = 18, outer_recon: int = 18, reliable: bool = True, delta: float = 0.1,
-             maxiter: int = 20000, stream=None, check: bool = True) -> dict:
+             maxiter: int = 20000, autotune: bool = False, stream=None, check: bool = True) -> dict:
     """Solve Mhat^dagger Mhat x = b on even half fields (FP64).  Returns the solve statistics;
     raises WdError on failure unless check=False (then 'status' carries the code)."""
     opts = CgOpts(int(inner_prec), int(inner_recon), int(outer_recon), int(bool(reliable)), float(delta),
-                  int(maxiter))
+                  int(maxiter), int(bool(autotune)))
     st = CgStats()
     rc = load().cg_solve(ctx.handle, gauge.handle, float(mass), _ptr(x), _ptr(b), float(tol), ctypes.byref(opts),
                          ctypes.byref(st), _stream(stream))
@@ -286,3 +294,23 @@ def norm2_noalloc(dims, sites: int, prec: int, x, result, stream=None) -> None:
     larger than 2,097,152 sites are rejected; concurrent calls race.  The first
     call on a device does a one-time address lookup: make it before any capture."""
     _check(load().wd_norm2_noalloc(_dims(dims), int(sites), int(prec), _ptr(x), _ptr(result), _stream(stream)))
+
+
+def tune_dslash(ctx: Context, gauge: Gauge, prec: int, recon: int, full: bool, with_x: bool = False,
+                nrhs: int = 1) -> list[dict]:
+    """Time every launch candidate of one operator shape; the fastest is kept in ctx."""
+    table = (TuneEntry * 32)()
+    n = _ip(0)
+    _check(load().wd_tune_dslash(ctx.handle, gauge.handle, int(prec), int(recon), int(bool(full)),
+                                 int(bool(with_x)), int(nrhs), table, 32, ctypes.byref(n)))
+    return [{"threads": table[k].threads, "variant": table[k].variant, "ms": table[k].ms} for k in range(n.value)]
+
+
+def tune_set_dslash(ctx: Context, gauge: Gauge, prec: int, recon: int, full: bool, with_x: bool, nrhs: int,
+                    threads: int, variant: int) -> None:
+    _check(load().wd_tune_set_dslash(ctx.handle, gauge.handle, int(prec), int(recon), int(bool(full)),
+                                     int(bool(with_x)), int(nrhs), int(threads), int(variant)))
+
+
+def tune_clear(ctx: Context) -> None:
+    _check(load().wd_tune_clear(ctx.handle))

@@ -282,6 +282,7 @@ int wd_ctx_create(int device, wd_ctx **out)
             return set_error(WD_ENOMEM, "allocating the context scratch failed");
         }
     }
+    load_tune_file(c);
     *out = c;
     return WD_OK;
 }

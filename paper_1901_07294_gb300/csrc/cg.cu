@@ -189,6 +189,12 @@ int cg_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x_e, const void 
     // build the gauge layouts up front so that no allocation happens mid-solve
     WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), WD_F64, opts->outer_recon));
     WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), opts->inner_prec, opts->inner_recon));
+    if (opts->autotune) {
+        for (int with_x = 0; with_x < 2; ++with_x) {
+            WD_TRY(hop_ensure_tuned(ctx, g, WD_F64, opts->outer_recon, 0, with_x));
+            WD_TRY(hop_ensure_tuned(ctx, g, opts->inner_prec, opts->inner_recon, 0, with_x));
+        }
+    }
     clear_error();
     wd_cg_stats st{};
     const auto t0 = std::chrono::steady_clock::now();

@@ -1,28 +1,54 @@
 // C entry points of the Wilson-Dirac operator: dslash_apply (full lattice)
 // and dslash_eo_apply (even-odd block with fused axpby).
+#include <cstdio>
+#include <string>
+
 #include "dslash_impl.cuh"
 #include "wd_internal.h"
 
 namespace wd {
-extern template cudaError_t launch_hop<PREC_F64>(const HopArgs &, int, int, int, int, cudaStream_t);
-extern template cudaError_t launch_hop<PREC_F32>(const HopArgs &, int, int, int, int, cudaStream_t);
-extern template cudaError_t launch_hop<PREC_F16>(const HopArgs &, int, int, int, int, cudaStream_t);
-extern template cudaError_t launch_hop<PREC_BF16>(const HopArgs &, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_hop<PREC_F64>(const HopArgs &, int, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_hop<PREC_F32>(const HopArgs &, int, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_hop<PREC_F16>(const HopArgs &, int, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_hop<PREC_BF16>(const HopArgs &, int, int, int, int, int, cudaStream_t);
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-int hop_launch(const HopArgs &A, int prec, int recon, int dagger, int nrhs, cudaStream_t s)
+// Key of a hop launch in the tuning cache (dagger shares its configuration).
+std::string hop_key(const wd_ctx *ctx, const HopArgs &A, int prec, int recon, int nrhs)
 {
-    const int threads = 256;
+    const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
+    char buf[160];
+    snprintf(buf, sizeof(buf), "hop sm%d p%d r%d np%d x%d n%d L%dx%dx%dx%d", ctx->num_sms, prec, recon, A.nparity,
+             hx ? 1 : 0, nrhs, A.L[0], A.L[1], A.L[2], A.L[3]);
+    return buf;
+}
+
+// Untuned defaults, from tuning runs on GB300 (32^4, 24^3x48, 16^3x32): the
+// FP32/FP16/BF16 kernels are fastest with 64-thread blocks and memory
+// schedule 1; the FP64 kernel (FP64-ALU bound) with 128 threads, schedule 0.
+static std::pair<int, int> hop_default(int prec) { return prec == WD_F64 ? std::make_pair(128, 0) : std::make_pair(64, 1); }
+
+int hop_launch_cfg(const HopArgs &A, int prec, int recon, int dagger, int nrhs, int threads, int variant,
+                   cudaStream_t s)
+{
+    if (threads < 32 || threads > 256 || (threads & 31) || variant < 0 || variant >= HOP_VARIANTS)
+        return set_error(WD_EINVAL, "bad hop launch configuration (%d threads, variant %d)", threads, variant);
     cudaError_t e = cudaSuccess;
     switch (prec) {
-    case WD_F64: e = launch_hop<PREC_F64>(A, recon, dagger, nrhs, threads, s); break;
-    case WD_F32: e = launch_hop<PREC_F32>(A, recon, dagger, nrhs, threads, s); break;
-    case WD_F16: e = launch_hop<PREC_F16>(A, recon, dagger, nrhs, threads, s); break;
-    case WD_BF16: e = launch_hop<PREC_BF16>(A, recon, dagger, nrhs, threads, s); break;
+    case WD_F64: e = launch_hop<PREC_F64>(A, recon, dagger, nrhs, threads, variant, s); break;
+    case WD_F32: e = launch_hop<PREC_F32>(A, recon, dagger, nrhs, threads, variant, s); break;
+    case WD_F16: e = launch_hop<PREC_F16>(A, recon, dagger, nrhs, threads, variant, s); break;
+    case WD_BF16: e = launch_hop<PREC_BF16>(A, recon, dagger, nrhs, threads, variant, s); break;
     }
     if (e != cudaSuccess) return set_error(WD_ECUDA, "hop kernel launch failed: %s", cudaGetErrorString(e));
     return WD_OK;
+}
+
+int hop_launch(wd_ctx *ctx, const HopArgs &A, int prec, int recon, int dagger, int nrhs, cudaStream_t s)
+{
+    auto cfg = tuned_config(ctx, hop_key(ctx, A, prec, recon, nrhs), hop_default(prec));
+    return hop_launch_cfg(A, prec, recon, dagger, nrhs, cfg.first, cfg.second, s);
 }
 
 // Fills the geometry and gauge parts of HopArgs.
@@ -55,7 +81,7 @@ int eo_hop(const wd_gauge *g, int prec, int recon, void *out, const void *in, co
     A.parity0 = p;
     A.a = a;
     A.b = b;
-    return hop_launch(A, prec, recon, dagger ? 1 : 0, 1, s);
+    return hop_launch(g->ctx, A, prec, recon, dagger ? 1 : 0, 1, s);
 }
 
 } // namespace wd
@@ -88,7 +114,7 @@ int dslash_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, doub
     A.parity0 = 0;
     A.a = mass + 4.0;
     A.b = -0.5;
-    return hop_launch(A, prec, recon, 0, nrhs, (cudaStream_t)stream);
+    return hop_launch(ctx, A, prec, recon, 0, nrhs, (cudaStream_t)stream);
 }
 
 int dslash_eo_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, const void *x, int out_parity,
@@ -113,7 +139,7 @@ int dslash_eo_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, c
     A.parity0 = p;
     A.a = a;
     A.b = b;
-    return hop_launch(A, prec, recon, dagger ? 1 : 0, nrhs, (cudaStream_t)stream);
+    return hop_launch(ctx, A, prec, recon, dagger ? 1 : 0, nrhs, (cudaStream_t)stream);
 }
 
 } // extern "C"

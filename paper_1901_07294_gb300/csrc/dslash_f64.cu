@@ -3,5 +3,5 @@
 #include "dslash_impl.cuh"
 
 namespace wd {
-template cudaError_t launch_hop<PREC_F64>(const HopArgs &, int, int, int, int, cudaStream_t);
+template cudaError_t launch_hop<PREC_F64>(const HopArgs &, int, int, int, int, int, cudaStream_t);
 } // namespace wd

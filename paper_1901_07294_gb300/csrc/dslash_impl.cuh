@@ -114,8 +114,15 @@ __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh
     accumulate<MU, S>(acc, w0, w1);
 }
 
-template <int P, int RECON, bool DAG, bool HAS_X>
-__global__ void __launch_bounds__(256) hop_kernel(const HopArgs A)
+// PF selects the memory schedule (chosen per problem by the autotuner):
+//   0: directions in the order x+, x-, y+, y-, ..., no prefetch;
+//   1: backward directions first (their data is mostly already in L2), the
+//      forward links and the t-forward neighbour (the first touches of new
+//      data) prefetched into L2 at thread start;
+//   2: as 1, and the backward links prefetched too (even-odd blocks touch
+//      every link once, so all of them come from DRAM).
+template <int P, int RECON, bool DAG, bool HAS_X, int PF>
+__global__ void __launch_bounds__(256, 2) hop_kernel(const HopArgs A)
 {
     using T = typename Prec<P>::real;
     int p, blk;
@@ -162,14 +169,35 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs A)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[s][c] = {T(0), T(0)};
 
-    hop_dir<P, RECON, 0, SF, true>(in, gf + 0 * lb, vh, xf, i, acc);
-    hop_dir<P, RECON, 0, SB, false>(in, gb + 0 * lb, vh, xb, xb, acc);
-    hop_dir<P, RECON, 1, SF, true>(in, gf + 1 * lb, vh, yf, i, acc);
-    hop_dir<P, RECON, 1, SB, false>(in, gb + 1 * lb, vh, yb, yb, acc);
-    hop_dir<P, RECON, 2, SF, true>(in, gf + 2 * lb, vh, zf, i, acc);
-    hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, acc);
-    hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, acc);
-    hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, acc);
+    using LK = Link<link_prec(P), RECON>;
+    if constexpr (PF == 0) {
+        hop_dir<P, RECON, 0, SF, true>(in, gf + 0 * lb, vh, xf, i, acc);
+        hop_dir<P, RECON, 0, SB, false>(in, gb + 0 * lb, vh, xb, xb, acc);
+        hop_dir<P, RECON, 1, SF, true>(in, gf + 1 * lb, vh, yf, i, acc);
+        hop_dir<P, RECON, 1, SB, false>(in, gb + 1 * lb, vh, yb, yb, acc);
+        hop_dir<P, RECON, 2, SF, true>(in, gf + 2 * lb, vh, zf, i, acc);
+        hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, acc);
+        hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, acc);
+        hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, acc);
+    } else {
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) LK::prefetch(gf + mu * lb, vh, i);
+        Spinor<P>::prefetch(in, vh, tf);
+        if constexpr (PF >= 2) {
+            LK::prefetch(gb + 0 * lb, vh, xb);
+            LK::prefetch(gb + 1 * lb, vh, yb);
+            LK::prefetch(gb + 2 * lb, vh, zb);
+            LK::prefetch(gb + 3 * lb, vh, tb);
+        }
+        hop_dir<P, RECON, 0, SB, false>(in, gb + 0 * lb, vh, xb, xb, acc);
+        hop_dir<P, RECON, 1, SB, false>(in, gb + 1 * lb, vh, yb, yb, acc);
+        hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, acc);
+        hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, acc);
+        hop_dir<P, RECON, 0, SF, true>(in, gf + 0 * lb, vh, xf, i, acc);
+        hop_dir<P, RECON, 1, SF, true>(in, gf + 1 * lb, vh, yf, i, acc);
+        hop_dir<P, RECON, 2, SF, true>(in, gf + 2 * lb, vh, zf, i, acc);
+        hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, acc);
+    }
 
     const T a = (T)A.a, b = (T)A.b;
     T o[24];
@@ -194,23 +222,36 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs A)
     Spinor<P>::store((p ? A.out[1] : A.out[0]) + roff, vh, i, o);
 }
 
-// Launches the hop kernel of precision P for the runtime (recon, dagger, has_x).
+constexpr int HOP_VARIANTS = 3;   // values of PF
+
+template <int P, int RECON, bool DAG, bool HX>
+void launch_hop_pf(const HopArgs &A, dim3 grid, int threads, int pf, cudaStream_t s)
+{
+    switch (pf) {
+    case 0: hop_kernel<P, RECON, DAG, HX, 0><<<grid, threads, 0, s>>>(A); break;
+    case 1: hop_kernel<P, RECON, DAG, HX, 1><<<grid, threads, 0, s>>>(A); break;
+    default: hop_kernel<P, RECON, DAG, HX, 2><<<grid, threads, 0, s>>>(A); break;
+    }
+}
+
+// Launches the hop kernel of precision P for the runtime (recon, dagger,
+// has_x) with `threads` per block (at most 256) and memory schedule `pf`.
 template <int P>
-cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int threads, cudaStream_t s)
+cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int threads, int pf, cudaStream_t s)
 {
     const int per = (A.vh + threads - 1) / threads;
     dim3 grid((unsigned)(per * A.nparity), (unsigned)nrhs);
     const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
     const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
     switch (key) {
-    case 0: hop_kernel<P, 18, false, false><<<grid, threads, 0, s>>>(A); break;
-    case 1: hop_kernel<P, 18, false, true><<<grid, threads, 0, s>>>(A); break;
-    case 2: hop_kernel<P, 18, true, false><<<grid, threads, 0, s>>>(A); break;
-    case 3: hop_kernel<P, 18, true, true><<<grid, threads, 0, s>>>(A); break;
-    case 4: hop_kernel<P, 12, false, false><<<grid, threads, 0, s>>>(A); break;
-    case 5: hop_kernel<P, 12, false, true><<<grid, threads, 0, s>>>(A); break;
-    case 6: hop_kernel<P, 12, true, false><<<grid, threads, 0, s>>>(A); break;
-    case 7: hop_kernel<P, 12, true, true><<<grid, threads, 0, s>>>(A); break;
+    case 0: launch_hop_pf<P, 18, false, false>(A, grid, threads, pf, s); break;
+    case 1: launch_hop_pf<P, 18, false, true>(A, grid, threads, pf, s); break;
+    case 2: launch_hop_pf<P, 18, true, false>(A, grid, threads, pf, s); break;
+    case 3: launch_hop_pf<P, 18, true, true>(A, grid, threads, pf, s); break;
+    case 4: launch_hop_pf<P, 12, false, false>(A, grid, threads, pf, s); break;
+    case 5: launch_hop_pf<P, 12, false, true>(A, grid, threads, pf, s); break;
+    case 6: launch_hop_pf<P, 12, true, false>(A, grid, threads, pf, s); break;
+    case 7: launch_hop_pf<P, 12, true, true>(A, grid, threads, pf, s); break;
     }
     return cudaGetLastError();
 }

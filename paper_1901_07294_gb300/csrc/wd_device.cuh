@@ -61,6 +61,12 @@ __device__ __forceinline__ uint4 ldg16(const void *p)
 }
 __device__ __forceinline__ void stg16(void *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
 
+// Hint: bring the 128-byte line holding p into L2 (no register result).
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <int P> __device__ __forceinline__ void unpack16(uint4 w, typename Prec<P>::real *r, float scale);
 template <> __device__ __forceinline__ void unpack16<PREC_F64>(uint4 w, double *r, float)
 {
@@ -134,6 +140,13 @@ template <int P> struct Spinor {
     static constexpr int nplane = 24 / Prec<P>::per16;
     static constexpr size_t site_bytes = 24 * Prec<P>::bytes + (Prec<P>::scaled ? 4 : 0);
 
+    __device__ static __forceinline__ void prefetch(const char *f, int vh, int i)
+    {
+#pragma unroll
+        for (int k = 0; k < nplane; ++k) prefetch_l2(f + ((size_t)k * vh + i) * 16);
+        if (Prec<P>::scaled) prefetch_l2(reinterpret_cast<const float *>(f + (size_t)nplane * vh * 16) + i);
+    }
+
     __device__ static __forceinline__ void load(const char *f, int vh, int i, real (&v)[24])
     {
         float s = 1.0f;
@@ -170,6 +183,13 @@ template <int P, int RECON> struct Link {
     static constexpr int nmain = RECON / per16;
     static constexpr int ntail = RECON % per16;   // reals in the tail plane
     static constexpr size_t site_bytes = (size_t)RECON * Prec<P>::bytes;
+
+    __device__ static __forceinline__ void prefetch(const char *blk, int vh, int i)
+    {
+#pragma unroll
+        for (int k = 0; k < nmain; ++k) prefetch_l2(blk + ((size_t)k * vh + i) * 16);
+        if constexpr (ntail > 0) prefetch_l2(blk + (size_t)nmain * vh * 16 + (size_t)i * ntail * Prec<P>::bytes);
+    }
 
     __device__ static __forceinline__ void load_raw(const char *blk, int vh, int i, real (&u)[18])
     {

@@ -79,8 +79,10 @@ struct wd_ctx {
     // solver workspace (device), grown on demand
     char *d_work = nullptr;
     size_t work_bytes = 0;
-    // launch-shape cache: (kernel id, geometry key) -> threads per block
-    std::map<std::pair<int, int64_t>, int> tuned;
+    // launch-shape cache filled by the autotuner: problem key -> (threads, variant)
+    std::mutex tune_mu;
+    std::map<std::string, std::pair<int, int>> tuned;
+    std::string tune_file;   // on-disk cache (WD_TUNE_CACHE), empty if none
 };
 
 struct wd_gauge {
@@ -96,6 +98,12 @@ constexpr int NSCAL = 64;
 // Even-odd hop on half fields: out_p = a x_p + b H^(d)_{p,1-p} in (see dslash_eo_apply).
 int eo_hop(const wd_gauge *g, int prec, int recon, void *out, const void *in, const void *x, int p, double a,
            double b, int dagger, cudaStream_t s);
+// Launch configuration of a tunable kernel: the tuned one if the context has
+// it, else `def`.
+std::pair<int, int> tuned_config(wd_ctx *ctx, const std::string &key, std::pair<int, int> def);
+void load_tune_file(wd_ctx *ctx);
+// Runs the autotuner for one hop shape unless the context already has it.
+int hop_ensure_tuned(wd_ctx *ctx, const wd_gauge *g, int prec, int recon, int full, int with_x);
 // Solver workspace of at least `bytes` bytes (device), owned by the context.
 int ctx_workspace(wd_ctx *ctx, size_t bytes, char **out);
 // Device pointer of the (prec, recon) layout, built on first use.

@@ -162,3 +162,42 @@ def test_argument_errors(ctx):
     with pytest.raises(wd.WdError) as e:
         wd.dslash_eo_apply(ctx, g, big, f, None, 2, 1.0, 1.0)
     assert e.value.status == wd.WD_EINVAL
+
+
+@pytest.mark.parametrize("prec", ALL_PREC)
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("threads", [64, 192, 256])
+def test_every_launch_variant_matches_oracle(prec, variant, threads):
+    """Each memory schedule and block size the autotuner may pick computes the same operator."""
+    dims = (4, 6, 8, 10)
+    ctx = wd.Context(0)
+    U, psi = _inputs(dims)
+    g = wd.Gauge(ctx, dims, U)
+    for recon in (18, 12):
+        wd.tune_set_dslash(ctx, g, prec, recon, True, True, 1, threads, variant)
+        wd.tune_set_dslash(ctx, g, prec, recon, False, False, 1, threads, variant)
+        fin = pack_field(ctx, dims, wd.SITES_FULL, prec, psi)
+        fout = wd.alloc_field(dims, wd.SITES_FULL, prec)
+        wd.dslash_apply(ctx, g, fout, fin, 0.1, prec=prec, recon=recon)
+        err = rel_max_err(unpack_field(ctx, dims, wd.SITES_FULL, prec, fout), oracle.dirac(dims, U, psi, 0.1))
+        assert err < TOL[prec], ("full", recon, err)
+        fo = pack_field(ctx, dims, wd.SITES_ODD, prec, psi)
+        fe = wd.alloc_field(dims, wd.SITES_EVEN, prec)
+        wd.dslash_eo_apply(ctx, g, fe, fo, None, 0, 0.0, 1.0, dagger=True, prec=prec, recon=recon)
+        par = parity(dims)
+        src = psi.copy()
+        src[par == 0] = 0
+        ref = oracle.gamma_apply(4, oracle.hop(dims, U, oracle.gamma_apply(4, src), out_parity=0))
+        got = unpack_field(ctx, dims, wd.SITES_EVEN, prec, fe)
+        assert rel_max_err(got[par == 0], ref[par == 0]) < TOL[prec], ("eo", recon)
+
+
+def test_autotuner_table_and_choice():
+    dims = (8, 8, 8, 8)
+    ctx = wd.Context(0)
+    U, _ = _inputs(dims)
+    g = wd.Gauge(ctx, dims, U)
+    table = wd.tune_dslash(ctx, g, wd.F32, 18, full=True)
+    assert len(table) == 12
+    assert {t["variant"] for t in table} == {0, 1, 2}
+    assert all(t["ms"] > 0 for t in table)
