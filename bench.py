@@ -220,8 +220,14 @@ def run_gpu(args):
     aos = psi_host.cuda()
     prec, recon = wd.F32, 18
     g.prepare(prec, recon)
-    tune_table = wd.tune_dslash(ctx, g, prec, recon, full=True)   # the autotuner picks the launch shape
-    best = min(tune_table, key=lambda t: t["ms"])
+    if args.launch:
+        # pinned launch shape (profiling: the tuner's timings are not meaningful under a profiler)
+        th, var = (int(t) for t in args.launch.split(","))
+        wd.tune_set_dslash(ctx, g, prec, recon, True, True, 1, th, var)
+        tune_table = [{"threads": th, "variant": var, "ms": float("nan")}]
+    else:
+        tune_table = wd.tune_dslash(ctx, g, prec, recon, full=True)   # the autotuner picks the launch shape
+    best = min(tune_table, key=lambda t: t["ms"] if t["ms"] == t["ms"] else 0.0)
     fin = wd.alloc_field(dims, wd.SITES_FULL, prec)
     fout = wd.alloc_field(dims, wd.SITES_FULL, prec)
     wd.pack(ctx, dims, wd.SITES_FULL, prec, aos, fin)
@@ -286,6 +292,9 @@ def run_gpu(args):
     variants = {}
     if not args.no_variants:
         variants = _variants(wd, torch, ctx, dims, U, psi, stream, peak)
+    mrhs = None
+    if not args.no_variants:
+        mrhs = _mrhs_section(wd, torch, ctx, U, psi, peak)
     cg = None
     if not args.no_cg:
         cg = _cg_section(wd, torch, ctx, with_cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline))
@@ -308,11 +317,13 @@ def run_gpu(args):
                 "d2h_bytes_per_step": v * 24 * 8, "ms_per_step": e2e_ms,
                 "path": "pinned H2D FP64 canonical -> wd.pack -> wd.dslash_apply -> wd.unpack -> D2H"},
         "autotune": {"chosen": {"threads": best["threads"], "variant": best["variant"]},
-                     "candidates_us": {f"{t['threads']}/v{t['variant']}": round(t["ms"] * 1e3, 1)
+                     "candidates_us": {f"{t['threads']}/v{t['variant']}":
+                                       (round(t["ms"] * 1e3, 1) if t["ms"] == t["ms"] else None)
                                        for t in tune_table}},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "variants": variants,
+        "multi_rhs": mrhs,
         "cg": cg,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -375,6 +386,66 @@ def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, reps=50
                     out[key] = {"ms": round(ms, 5), "gbs": round(gbs, 1), "frac_hbm": round(gbs / peak, 4),
                                 "gflops": round(FLOPS_PER_SITE * nsite / (ms * 1e-3) / 1e9, 1)}
         g.close()
+    return out
+
+
+def _mrhs_section(wd, torch, ctx, U, psi, peak, reps=20):
+    """12 right-hand sides sharing each link load vs 12 single-field launches, FP32, 32^4."""
+    import numpy as np
+
+    import synth
+    dims = DIMS
+    v = synth.volume(dims)
+    nrhs = 12
+    g = wd.Gauge(ctx, dims, U)
+    aos = torch.from_numpy(psi.view(np.float64).reshape(-1).copy()).cuda()
+    one = wd.alloc_field(dims, wd.SITES_FULL, wd.F32)
+    wd.pack(ctx, dims, wd.SITES_FULL, wd.F32, aos, one)
+    out = {"nrhs": nrhs, "lattice": list(dims)}
+    for kind, sites_in, sites_out, nsite, bps in (("eo", wd.SITES_ODD, wd.SITES_EVEN, v // 2, (192, 576)),
+                                                  ("full", wd.SITES_FULL, wd.SITES_FULL, v, (192, 288))):
+        nb_in = wd.field_bytes(dims, sites_in, wd.F32)
+        src = one[nb_in:] if kind == "eo" else one
+        fin = src.repeat(nrhs)
+        fout = wd.alloc_field(dims, sites_out, wd.F32, nrhs)
+        full = kind == "full"
+        wd.tune_dslash(ctx, g, wd.F32, 18, full=full, with_x=False, nrhs=nrhs)
+        wd.tune_dslash(ctx, g, wd.F32, 18, full=full, with_x=False, nrhs=1)
+        nb_out = wd.field_bytes(dims, sites_out, wd.F32)
+
+        def multi():
+            if full:
+                wd.dslash_apply(ctx, g, fout, fin, MASS, nrhs=nrhs, prec=wd.F32)
+            else:
+                wd.dslash_eo_apply(ctx, g, fout, fin, None, wd.EVEN, 0.0, 1.0, nrhs=nrhs, prec=wd.F32)
+
+        def singles():
+            for k in range(nrhs):
+                if full:
+                    wd.dslash_apply(ctx, g, fout[k * nb_out:(k + 1) * nb_out], fin[k * nb_in:(k + 1) * nb_in],
+                                    MASS, prec=wd.F32)
+                else:
+                    wd.dslash_eo_apply(ctx, g, fout[k * nb_out:(k + 1) * nb_out], fin[k * nb_in:(k + 1) * nb_in],
+                                       None, wd.EVEN, 0.0, 1.0, prec=wd.F32)
+
+        res = {}
+        for name, fn in (("multi", multi), ("singles", singles)):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1) / reps
+        b_multi = (nrhs * bps[0] + bps[1]) * nsite
+        out[kind] = {"multi_ms": round(res["multi"], 4), "singles_ms": round(res["singles"], 4),
+                     "speedup": round(res["singles"] / res["multi"], 2),
+                     "multi_gbs": round(b_multi / (res["multi"] * 1e-3) / 1e9, 1),
+                     "multi_frac_hbm": round(b_multi / (res["multi"] * 1e-3) / 1e9 / peak, 4),
+                     "bytes_per_site_rhs": round(b_multi / (nsite * nrhs), 1)}
+    g.close()
     return out
 
 
@@ -442,6 +513,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--launch", default="", help="THREADS,VARIANT: pin the headline launch shape instead of tuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

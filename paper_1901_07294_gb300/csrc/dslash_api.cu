@@ -27,12 +27,16 @@ std::string hop_key(const wd_ctx *ctx, const HopArgs &A, int prec, int recon, in
 // Untuned defaults, from tuning runs on GB300 (32^4, 24^3x48, 16^3x32): the
 // FP32/FP16/BF16 kernels are fastest with 64-thread blocks and memory
 // schedule 1; the FP64 kernel (FP64-ALU bound) with 128 threads, schedule 0.
-static std::pair<int, int> hop_default(int prec) { return prec == WD_F64 ? std::make_pair(128, 0) : std::make_pair(64, 1); }
+static std::pair<int, int> hop_default(int prec, int nrhs)
+{
+    if (nrhs > 1) return {128, HOP_MRHS_VARIANT};   // shared-link kernel, 4 fields at a time
+    return prec == WD_F64 ? std::make_pair(128, 0) : std::make_pair(64, 1);
+}
 
 int hop_launch_cfg(const HopArgs &A, int prec, int recon, int dagger, int nrhs, int threads, int variant,
                    cudaStream_t s)
 {
-    if (threads < 32 || threads > 256 || (threads & 31) || variant < 0 || variant >= HOP_VARIANTS)
+    if (threads < 32 || threads > 256 || (threads & 31) || variant < 0 || variant > HOP_MRHS_VARIANT)
         return set_error(WD_EINVAL, "bad hop launch configuration (%d threads, variant %d)", threads, variant);
     cudaError_t e = cudaSuccess;
     switch (prec) {
@@ -47,7 +51,7 @@ int hop_launch_cfg(const HopArgs &A, int prec, int recon, int dagger, int nrhs, 
 
 int hop_launch(wd_ctx *ctx, const HopArgs &A, int prec, int recon, int dagger, int nrhs, cudaStream_t s)
 {
-    auto cfg = tuned_config(ctx, hop_key(ctx, A, prec, recon, nrhs), hop_default(prec));
+    auto cfg = tuned_config(ctx, hop_key(ctx, A, prec, recon, nrhs), hop_default(prec, nrhs));
     return hop_launch_cfg(A, prec, recon, dagger, nrhs, cfg.first, cfg.second, s);
 }
 
