@@ -107,7 +107,9 @@ int wd_unpack(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *f
  * keeps its own FP64 copy and builds device layouts on demand: per parity,
  * per mu, planes of 16-byte vectors holding the first `recon` reals of the
  * row-major matrix (12 = rows 0 and 1 only; row 2 is rebuilt in the kernel as
- * conj(row0 x row1), valid for SU(3)).  Synchronous. */
+ * conj(row0 x row1), valid for SU(3)).  Synchronous.  Operator calls with a
+ * gauge use its context's tuning cache, so the context must outlive those
+ * calls; destroying a gauge after its context is allowed. */
 int wd_gauge_create(wd_ctx *ctx, const int dims[4], const double *links, int links_on_host,
                     wd_gauge **out);
 /* Builds (if not built yet) the (prec, recon) layout.  Operator calls build
@@ -239,6 +241,39 @@ typedef struct {
 
 int cg_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x_e, const void *b_e, double tol,
              const wd_cg_opts *opts, wd_cg_stats *stats, void *stream);
+
+/* ---- Batches of solves (different lattices, masses, tolerances) --------------
+ * Each descriptor is one cg_solve problem; its lattice comes from its gauge.
+ * Modes:
+ *   WD_BATCH_SEQUENTIAL  cg_solve on each descriptor in turn (any options);
+ *   WD_BATCH_GRAPH       mixed-precision reliable-update solves (inner_prec
+ *                        WD_F32/WD_F16/WD_BF16, the same for all), 8
+ *                        iterations of each solve captured into a CUDA graph
+ *                        and replayed on a stream per solve; residual checks
+ *                        and FP64 reliable updates on the host between replays;
+ *   WD_BATCH_PERSISTENT  one cooperative kernel: each solve runs on its own
+ *                        group of thread blocks (sized by volume), steps
+ *                        separated by group barriers whose waits are bounded
+ *                        (1 s of clock cycles; WD_BARRIER_TIMEOUT_S overrides);
+ *                        options must be inner_prec WD_F32, 18-real links,
+ *                        reliable = 1.  Batches larger than one co-resident
+ *                        grid run as several launches.
+ * stats[k] receives solve k's statistics; `seconds` is the wall time of the
+ * whole call.  Returns the first failure (WD_ENOCONV, WD_ETIMEOUT, ...).
+ * Synchronous; allocates its workspace for the duration of the call. */
+typedef enum { WD_BATCH_SEQUENTIAL = 0, WD_BATCH_GRAPH = 1, WD_BATCH_PERSISTENT = 2 } wd_batch_mode;
+
+typedef struct {
+    const wd_gauge *gauge;
+    double mass;
+    double tol;
+    void *x_e;          /* even half field, WD_F64, device (output) */
+    const void *b_e;    /* even half field, WD_F64, device */
+    wd_cg_opts opts;
+} wd_solve_desc;
+
+int cg_solve_batch(wd_ctx *ctx, int n, const wd_solve_desc *descs, int mode, wd_cg_stats *stats,
+                   void *stream);
 
 #ifdef __cplusplus
 }

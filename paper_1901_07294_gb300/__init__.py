@@ -62,6 +62,7 @@ _SIGS = {
     "wd_tune_dslash": (_ip, [_vp, _vp, _ip, _ip, _ip, _ip, _ip, _vp, _ip, ctypes.POINTER(_ip)]),
     "wd_tune_set_dslash": (_ip, [_vp, _vp, _ip, _ip, _ip, _ip, _ip, _ip, _ip]),
     "wd_tune_clear": (_ip, [_vp]),
+    "cg_solve_batch": (_ip, [_vp, _ip, _vp, _ip, _vp, _vp]),
 }
 
 
@@ -314,3 +315,32 @@ def tune_set_dslash(ctx: Context, gauge: Gauge, prec: int, recon: int, full: boo
 
 def tune_clear(ctx: Context) -> None:
     _check(load().wd_tune_clear(ctx.handle))
+
+
+BATCH_SEQUENTIAL, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
+
+
+class SolveDesc(ctypes.Structure):
+    """wd_solve_desc"""
+    _fields_ = [("gauge", _vp), ("mass", _dp), ("tol", _dp), ("x_e", _vp), ("b_e", _vp), ("opts", CgOpts)]
+
+
+def cg_solve_batch(ctx: Context, problems: list[dict], mode: int = BATCH_SEQUENTIAL, stream=None,
+                   check: bool = True) -> list[dict]:
+    """Run many solves.  Each problem: dict(gauge, mass, tol, x, b, and optional cg_solve options
+    inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune)."""
+    n = len(problems)
+    descs = (SolveDesc * max(n, 1))()
+    for k, p in enumerate(problems):
+        o = CgOpts(int(p.get("inner_prec", F32)), int(p.get("inner_recon", 18)), int(p.get("outer_recon", 18)),
+                   int(bool(p.get("reliable", True))), float(p.get("delta", 0.1)), int(p.get("maxiter", 20000)),
+                   int(bool(p.get("autotune", False))))
+        descs[k] = SolveDesc(p["gauge"].handle, float(p["mass"]), float(p["tol"]), _ptr(p["x"]), _ptr(p["b"]), o)
+    stats = (CgStats * max(n, 1))()
+    rc = load().cg_solve_batch(ctx.handle, n, descs, int(mode), stats, _stream(stream))
+    if check:
+        _check(rc)
+    out = [stats[k].as_dict() for k in range(n)]
+    for d in out:
+        d["batch_status"] = rc
+    return out

@@ -21,7 +21,11 @@ int set_error(int status, const char *fmt, ...)
     return status;
 }
 
-void clear_error() { g_err[0] = 0; }
+void clear_error()
+{
+    g_err[0] = 0;
+    cudaGetLastError();   // drop a runtime error left by an unrelated earlier call
+}
 
 bool valid_prec(int prec) { return prec >= WD_F64 && prec <= WD_BF16; }
 bool valid_recon(int recon) { return recon == WD_RECON_18 || recon == WD_RECON_12; }
@@ -207,7 +211,7 @@ int gauge_layout(const wd_gauge *gc, int prec, int recon, const char **out)
         *out = it->second;
         return WD_OK;
     }
-    DeviceGuard dg(g->ctx->device);
+    DeviceGuard dg(g->device);
     const size_t blk = link_block_bytes(g->geo.Vh, prec, recon);
     char *buf = nullptr;
     if (cudaMalloc(&buf, 8 * blk) != cudaSuccess) {
@@ -385,6 +389,7 @@ int wd_gauge_create(wd_ctx *ctx, const int dims[4], const double *links, int lin
     wd_gauge *g = new (std::nothrow) wd_gauge();
     if (!g) return set_error(WD_ENOMEM, "host allocation failed");
     g->ctx = ctx;
+    g->device = ctx->device;
     g->geo = geo;
     const size_t nb = (size_t)geo.V * 4 * 18 * sizeof(double);
     if (cudaMalloc(&g->canonical, nb) != cudaSuccess) {
@@ -423,7 +428,7 @@ int wd_gauge_destroy(wd_gauge *g)
 {
     clear_error();
     if (!g) return WD_OK;
-    DeviceGuard dg(g->ctx->device);
+    DeviceGuard dg(g->device);
     for (auto &kv : g->layouts) cudaFree(kv.second);
     cudaFree(g->canonical);
     delete g;

@@ -1,0 +1,723 @@
+// Many CG solves at once (different lattices, masses, tolerances).
+//
+// Three ways to run a batch of Mhat^dagger Mhat x = b solves, all with the
+// reliable-update scheme of cg.cu (low-precision iterated residual, FP64
+// solution, true residual and inner products):
+//   WD_BATCH_SEQUENTIAL  one cg_solve after another;
+//   WD_BATCH_GRAPH       each solve's iteration (4 hop launches and 3 BLAS
+//                        kernels whose scalars stay in device memory)
+//                        captured K times into a CUDA graph per solve; the
+//                        graphs of all active solves are replayed on their own
+//                        streams, and the host checks residuals and does the
+//                        FP64 reliable updates between replays;
+//   WD_BATCH_PERSISTENT  one cooperative launch: each solve owns a group of
+//                        thread blocks (sized in proportion to its volume)
+//                        that runs the whole solve, separated by group-local
+//                        barriers and deterministic group reductions.  Every
+//                        barrier wait is bounded (about a second of clock
+//                        cycles); on timeout the kernel sets an error word and
+//                        returns, and the call reports WD_ETIMEOUT.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "blas_host.cuh"
+#include "dslash_impl.cuh"
+
+namespace wd {
+
+int hop_setup(const wd_gauge *g, int prec, int recon, HopArgs &A);
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// persistent kernel
+// ---------------------------------------------------------------------------
+struct PSolve {
+    HopArgs hs;            // FP32 geometry and links
+    HopArgs hd;            // FP64 geometry and links
+    const char *b;         // FP64 even half fields
+    char *x, *r, *ax, *to64, *te64;
+    char *rs, *ps, *aps, *tso, *tse, *xs;   // FP32 even/odd half fields
+    double mass, tol, delta;
+    int maxiter;
+    int block0, nblocks;
+    int barrier_target;    // blocks that must arrive at each barrier
+    unsigned *bar;         // [0] arrivals, [32] generation (separate lines)
+    double *part;          // 2 buffers x nblocks x 2 partial sums
+    int *out_int;          // [0] status, [1] iterations, [2] reliable updates
+    double *out_rel;       // true relative residual
+};
+
+struct GroupCtx {
+    const PSolve *S;
+    int gb, G;             // block index in the group, group size
+    unsigned gen;          // barrier generation seen by this block
+    int red;               // reduction counter (selects the partial-sum buffer)
+    long long limit;       // clock cycles a barrier may wait
+    int *err;              // grid-wide error word
+};
+
+// Group barrier: all blocks of the group (S->barrier_target of them) arrive
+// before any leaves.  Returns false if the wait ran out or another block
+// reported an error; the caller then returns.
+__device__ bool group_sync(GroupCtx &g)
+{
+    __shared__ int s_fail;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int fail = 0;
+        unsigned *cnt = g.S->bar;
+        unsigned *gen = g.S->bar + 32;
+        __threadfence();
+        if (atomicAdd(cnt, 1u) == (unsigned)g.S->barrier_target - 1u) {
+            atomicExch(cnt, 0u);
+            __threadfence();
+            atomicExch(gen, g.gen + 1u);
+        } else {
+            const long long t0 = clock64();
+            while (atomicAdd(gen, 0u) == g.gen) {
+                if (*(volatile int *)g.err != 0) { fail = 1; break; }
+                if (clock64() - t0 > g.limit) {
+                    atomicExch(g.err, WD_ETIMEOUT);
+                    fail = 1;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_fail = fail;
+    }
+    __syncthreads();
+    g.gen += 1u;
+    return s_fail == 0;
+}
+
+// Deterministic group sum of NR values: block sums to partials, barrier, then
+// every thread adds the partials in block order (same result in all blocks).
+template <int NR> __device__ bool group_sum(GroupCtx &g, double (&v)[NR])
+{
+    __shared__ double sm[8][NR];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NR; ++k) sm[warp][k] = v[k];
+    __syncthreads();
+    double *buf = g.S->part + (size_t)(g.red & 1) * g.G * 2;
+    g.red++;
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w][k];
+            buf[g.gb * 2 + k] = s;
+        }
+    if (!group_sync(g)) return false;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        double s = 0.0;
+        for (int b = 0; b < g.G; ++b) s += __ldcg(buf + b * 2 + k);
+        v[k] = s;
+    }
+    return true;
+}
+
+template <int P, bool DAG, bool HX>
+__device__ void group_hop(const GroupCtx &g, HopArgs A, const char *in, const char *x, char *out, int p, double a,
+                          double b)
+{
+    A.in[0] = A.in[1] = in;
+    A.x[0] = A.x[1] = x;
+    A.out[0] = A.out[1] = out;
+    A.a = a;
+    A.b = b;
+    for (int i = g.gb * blockDim.x + threadIdx.x; i < A.vh; i += g.G * blockDim.x)
+        hop_site<P, 18, DAG, HX, 1>(A, p, i, 0);
+}
+
+// out = Mhat^dagger Mhat in (4 hops, a barrier after each).
+template <int P>
+__device__ bool group_mdagm(GroupCtx &g, const HopArgs &A, double mass, const char *in, char *out, char *t_o,
+                            char *t_e)
+{
+    const double a = mass + 4.0, c = 1.0 / (4.0 * (mass + 4.0));
+    group_hop<P, false, false>(g, A, in, nullptr, t_o, 1, 0.0, 1.0);
+    if (!group_sync(g)) return false;
+    group_hop<P, false, true>(g, A, t_o, in, t_e, 0, a, -c);
+    if (!group_sync(g)) return false;
+    group_hop<P, true, false>(g, A, t_e, nullptr, t_o, 1, 0.0, 1.0);
+    if (!group_sync(g)) return false;
+    group_hop<P, true, true>(g, A, t_o, t_e, out, 0, a, -c);
+    return true;   // the caller's next step reads only its own sites of `out`
+}
+
+// One 256-thread block per SM: the FP32 and FP64 hop bodies inlined together
+// need up to 255 registers per thread.
+__global__ void __launch_bounds__(256, 1) cg_persistent_kernel(const PSolve *__restrict__ solves,
+                                                                const int *__restrict__ block_solve, int *err,
+                                                                long long limit)
+{
+    const PSolve *S = solves + block_solve[blockIdx.x];
+    GroupCtx g{S, (int)blockIdx.x - S->block0, S->nblocks, 0u, 0, limit, err};
+    const int vh = S->hs.vh;
+    const size_t h64 = (size_t)vh * 192, h32 = (size_t)vh * 96;
+    const FieldRef<PREC_F64> fb{(char *)S->b, h64, vh}, fx{S->x, h64, vh}, fr{S->r, h64, vh}, fax{S->ax, h64, vh};
+    const FieldRef<PREC_F32> frs{S->rs, h32, vh}, fps{S->ps, h32, vh}, faps{S->aps, h32, vh}, fxs{S->xs, h32, vh};
+    const int i0 = g.gb * blockDim.x + threadIdx.x, stride = g.G * blockDim.x;
+
+    // |b|^2, then x = 0, r = b, rs = ps = (FP32) b, xs = 0 on this block's sites
+    double v[2] = {0.0, 0.0};
+    for (int i = i0; i < vh; i += stride) {
+        double bv[24];
+        fb.load(i, bv);
+        double s = 0.0;
+        for (int k = 0; k < 24; ++k) s = fma(bv[k], bv[k], s);
+        v[0] += s;
+        fr.store(i, bv);
+        float f[24];
+        for (int k = 0; k < 24; ++k) f[k] = (float)bv[k];
+        frs.store(i, f);
+        fps.store(i, f);
+        for (int k = 0; k < 24; ++k) { bv[k] = 0.0; f[k] = 0.0f; }
+        fx.store(i, bv);
+        fxs.store(i, f);
+    }
+    double one[1] = {v[0]};
+    if (!group_sum(g, one)) return;
+    const double b2 = one[0];
+    int status = WD_OK, it = 0, nupd = 0;
+    double r2t = b2;
+    if (b2 > 0.0) {
+        const double stop2 = S->tol * S->tol * b2;
+        double r2 = b2, maxr = sqrt(b2);
+        bool converged = false;
+        while (it < S->maxiter) {
+            if (!group_mdagm<PREC_F32>(g, S->hs, S->mass, S->ps, S->aps, S->tso, S->tse)) return;
+            double pap[1] = {0.0};
+            for (int i = i0; i < vh; i += stride) {
+                float pv[24], av[24];
+                fps.load(i, pv);
+                faps.load(i, av);
+                float t = 0.0f;
+                for (int k = 0; k < 24; ++k) t = fmaf(pv[k], av[k], t);
+                pap[0] += (double)t;
+            }
+            if (!group_sum(g, pap)) return;
+            if (!(pap[0] > 0.0)) { status = WD_ENOCONV; break; }
+            const double alpha = r2 / pap[0];
+            double rr[1] = {0.0};
+            for (int i = i0; i < vh; i += stride) {
+                float rv[24], av[24], pv[24], xv[24];
+                frs.load(i, rv);
+                faps.load(i, av);
+                fps.load(i, pv);
+                fxs.load(i, xv);
+                const float af = (float)alpha;
+                float t = 0.0f;
+                for (int k = 0; k < 24; ++k) {
+                    rv[k] = fmaf(-af, av[k], rv[k]);
+                    t = fmaf(rv[k], rv[k], t);
+                    xv[k] = fmaf(af, pv[k], xv[k]);
+                }
+                frs.store(i, rv);
+                fxs.store(i, xv);
+                rr[0] += (double)t;
+            }
+            if (!group_sum(g, rr)) return;
+            ++it;
+            double r2new = rr[0];
+            const double rn = sqrt(r2new);
+            if (rn > maxr) maxr = rn;
+            if (rn < S->delta * maxr || r2new <= stop2) {
+                // reliable update: x += xs (FP64), true residual with the FP64 operator
+                for (int i = i0; i < vh; i += stride) {
+                    double xv[24];
+                    float sv[24];
+                    fx.load(i, xv);
+                    fxs.load(i, sv);
+                    for (int k = 0; k < 24; ++k) { xv[k] += (double)sv[k]; sv[k] = 0.0f; }
+                    fx.store(i, xv);
+                    fxs.store(i, sv);
+                }
+                if (!group_sync(g)) return;
+                if (!group_mdagm<PREC_F64>(g, S->hd, S->mass, S->x, S->ax, S->to64, S->te64)) return;
+                double t2[1] = {0.0};
+                for (int i = i0; i < vh; i += stride) {
+                    double bv[24], av[24];
+                    fb.load(i, bv);
+                    fax.load(i, av);
+                    double s = 0.0;
+                    float f[24];
+                    for (int k = 0; k < 24; ++k) {
+                        bv[k] -= av[k];
+                        s = fma(bv[k], bv[k], s);
+                        f[k] = (float)bv[k];
+                    }
+                    fr.store(i, bv);
+                    frs.store(i, f);
+                    t2[0] += s;
+                }
+                if (!group_sum(g, t2)) return;
+                ++nupd;
+                r2t = t2[0];
+                if (r2t <= stop2) { converged = true; break; }
+                if (!(r2t < 1e300)) { status = WD_ENOCONV; break; }
+                r2new = r2t;
+                maxr = sqrt(r2t);
+            }
+            const float beta = (float)(r2new / r2);
+            for (int i = i0; i < vh; i += stride) {
+                float rv[24], pv[24];
+                frs.load(i, rv);
+                fps.load(i, pv);
+                for (int k = 0; k < 24; ++k) pv[k] = fmaf(beta, pv[k], rv[k]);
+                fps.store(i, pv);
+            }
+            if (!group_sync(g)) return;
+            r2 = r2new;
+        }
+        if (!converged && status == WD_OK) status = WD_ENOCONV;
+    }
+    if (g.gb == 0 && threadIdx.x == 0) {
+        S->out_int[0] = status;
+        S->out_int[1] = it;
+        S->out_int[2] = nupd;
+        S->out_rel[0] = b2 > 0.0 ? sqrt(r2t / b2) : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+int check_desc(const wd_solve_desc &d, int mode)
+{
+    if (!d.gauge || !d.x_e || !d.b_e) return set_error(WD_EINVAL, "NULL gauge or field in a solve descriptor");
+    if (((uintptr_t)d.x_e & 15u) || ((uintptr_t)d.b_e & 15u)) return set_error(WD_EINVAL, "misaligned field");
+    if (!(d.tol > 0.0)) return set_error(WD_EINVAL, "tol must be > 0");
+    if (d.opts.maxiter < 1) return set_error(WD_EINVAL, "maxiter must be >= 1");
+    if (!valid_prec(d.opts.inner_prec)) return set_error(WD_EINVAL, "bad inner precision");
+    if (!valid_recon(d.opts.inner_recon) || !valid_recon(d.opts.outer_recon))
+        return set_error(WD_EINVAL, "bad link reconstruction");
+    if (mode == WD_BATCH_PERSISTENT) {
+        if (d.opts.inner_prec != WD_F32 || d.opts.inner_recon != 18 || d.opts.outer_recon != 18 || !d.opts.reliable)
+            return set_error(WD_EINVAL,
+                             "the persistent batch runs FP32 reliable-update CG with 18-real links only");
+        if (!(d.opts.delta > 0.0 && d.opts.delta < 1.0)) return set_error(WD_EINVAL, "delta must be in (0, 1)");
+    }
+    if (mode == WD_BATCH_GRAPH && (d.opts.inner_prec == WD_F64 || !d.opts.reliable))
+        return set_error(WD_EINVAL, "the graph batch runs mixed-precision reliable-update CG");
+    return WD_OK;
+}
+
+int run_persistent(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stats, cudaStream_t s)
+{
+    int per_sm = 0;
+    WD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_persistent_kernel, 256, 0));
+    const int capacity = per_sm * ctx->num_sms;
+    if (capacity < 1) return set_error(WD_ECUDA, "persistent kernel cannot be resident");
+    // host-side fault injection for tests: WD_FAULT=barrier_missing makes each
+    // group wait for one block more than it has, so its first barrier times out
+    const char *fault = std::getenv("WD_FAULT");
+    const int extra = (fault && std::strstr(fault, "barrier_missing")) ? 1 : 0;
+    double limit_s = 1.0;
+    if (const char *ls = std::getenv("WD_BARRIER_TIMEOUT_S")) limit_s = std::atof(ls);
+    int clock_khz = 0;
+    cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, ctx->device);
+    const long long limit = (long long)(limit_s * (clock_khz > 0 ? clock_khz : 2000000) * 1e3);
+
+    int done = 0;
+    while (done < n) {
+        // next wave: as many solves as fit one block each, groups sized by volume
+        int m = std::min(n - done, capacity);
+        double vtot = 0.0;
+        for (int k = 0; k < m; ++k) vtot += d[done + k].gauge->geo.Vh;
+        std::vector<int> nb(m);
+        int used = 0;
+        for (int k = 0; k < m; ++k) {
+            const int vh = d[done + k].gauge->geo.Vh;
+            const int maxb = (vh + 255) / 256;
+            int want = (int)std::floor((double)(capacity - m) * vh / vtot) + 1;
+            nb[k] = std::max(1, std::min(want, maxb));
+            used += nb[k];
+        }
+        // hand out what rounding left to the largest groups that can take it
+        for (int k = 0; used < capacity && k < m; ++k) {
+            const int maxb = (d[done + k].gauge->geo.Vh + 255) / 256;
+            while (used < capacity && nb[k] < maxb && nb[k] < 4 * (int)std::ceil((double)capacity * d[done + k].gauge->geo.Vh / vtot)) {
+                ++nb[k];
+                ++used;
+            }
+        }
+        // device memory: workspace fields + per-solve sync/partials/outputs
+        std::vector<PSolve> ps(m);
+        std::vector<int> bmap(used);
+        size_t bytes = 0;
+        std::vector<size_t> off(m);
+        for (int k = 0; k < m; ++k) {
+            const int vh = d[done + k].gauge->geo.Vh;
+            off[k] = bytes;
+            bytes += 4 * ((size_t)vh * 192 + 256) + 6 * ((size_t)vh * 96 + 256) + 256 + 4096 +
+                     (size_t)nb[k] * 32 + 256;
+        }
+        DevBuf work, meta;
+        if (cudaMalloc(&work.p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(WD_ENOMEM, "cudaMalloc of %zu bytes for the persistent batch failed", bytes);
+        }
+        WD_CUDA_TRY(cudaMemsetAsync(work.p, 0, bytes, s));
+        int b0 = 0;
+        for (int k = 0; k < m; ++k) {
+            const wd_solve_desc &dk = d[done + k];
+            PSolve &P = ps[k];
+            std::memset(&P, 0, sizeof(P));
+            WD_TRY(hop_setup(dk.gauge, WD_F32, 18, P.hs));
+            WD_TRY(hop_setup(dk.gauge, WD_F64, 18, P.hd));
+            P.hs.nparity = P.hd.nparity = 1;
+            const int vh = dk.gauge->geo.Vh;
+            char *q = (char *)work.p + off[k];
+            auto take = [&q](size_t nbytes) {
+                char *r = q;
+                q += (nbytes + 255) & ~size_t(255);
+                return r;
+            };
+            P.b = (const char *)dk.b_e;
+            P.x = (char *)dk.x_e;
+            P.r = take((size_t)vh * 192);
+            P.ax = take((size_t)vh * 192);
+            P.to64 = take((size_t)vh * 192);
+            P.te64 = take((size_t)vh * 192);
+            P.rs = take((size_t)vh * 96);
+            P.ps = take((size_t)vh * 96);
+            P.aps = take((size_t)vh * 96);
+            P.tso = take((size_t)vh * 96);
+            P.tse = take((size_t)vh * 96);
+            P.xs = take((size_t)vh * 96);
+            P.bar = (unsigned *)take(256);
+            P.out_int = (int *)take(64);
+            P.out_rel = (double *)take(64);
+            P.part = (double *)take((size_t)nb[k] * 32);
+            P.mass = dk.mass;
+            P.tol = dk.tol;
+            P.delta = dk.opts.delta;
+            P.maxiter = dk.opts.maxiter;
+            P.block0 = b0;
+            P.nblocks = nb[k];
+            P.barrier_target = nb[k] + extra;
+            for (int b = 0; b < nb[k]; ++b) bmap[b0 + b] = k;
+            b0 += nb[k];
+        }
+        const size_t mbytes = sizeof(PSolve) * m + sizeof(int) * used + 64;
+        if (cudaMalloc(&meta.p, mbytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(WD_ENOMEM, "cudaMalloc of the batch descriptors failed");
+        }
+        PSolve *d_ps = (PSolve *)meta.p;
+        int *d_map = (int *)((char *)meta.p + sizeof(PSolve) * m);
+        int *d_err = d_map + used;
+        WD_CUDA_TRY(cudaMemcpyAsync(d_ps, ps.data(), sizeof(PSolve) * m, cudaMemcpyHostToDevice, s));
+        WD_CUDA_TRY(cudaMemcpyAsync(d_map, bmap.data(), sizeof(int) * used, cudaMemcpyHostToDevice, s));
+        WD_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+        void *args[] = {(void *)&d_ps, (void *)&d_map, (void *)&d_err, (void *)&limit};
+        WD_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)cg_persistent_kernel, dim3(used), dim3(256), args, 0, s));
+        WD_CUDA_TRY(cudaStreamSynchronize(s));
+        int herr = 0;
+        WD_CUDA_TRY(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        for (int k = 0; k < m; ++k) {
+            int oi[3];
+            double rel = 0.0;
+            WD_CUDA_TRY(cudaMemcpy(oi, ps[k].out_int, sizeof(oi), cudaMemcpyDeviceToHost));
+            WD_CUDA_TRY(cudaMemcpy(&rel, ps[k].out_rel, sizeof(double), cudaMemcpyDeviceToHost));
+            if (stats) {
+                wd_cg_stats &st = stats[done + k];
+                st.status = herr ? WD_ETIMEOUT : oi[0];
+                st.iters = oi[1];
+                st.reliable_updates = oi[2];
+                st.true_rel_resid = rel;
+            }
+        }
+        if (herr) return set_error(WD_ETIMEOUT, "a group barrier of the persistent batch timed out");
+        done += m;
+    }
+    return WD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// graph mode
+// ---------------------------------------------------------------------------
+int apply_mdagm_h(const wd_gauge *g, int prec, int recon, double mass, const char *in, char *out, char *t_o,
+                  char *t_e, cudaStream_t s)
+{
+    const double a = mass + 4.0, c = 1.0 / (4.0 * (mass + 4.0));
+    WD_TRY(eo_hop(g, prec, recon, t_o, in, nullptr, WD_ODD, 0.0, 1.0, 0, s));
+    WD_TRY(eo_hop(g, prec, recon, t_e, t_o, in, WD_EVEN, a, -c, 0, s));
+    WD_TRY(eo_hop(g, prec, recon, t_o, t_e, nullptr, WD_ODD, 0.0, 1.0, 1, s));
+    WD_TRY(eo_hop(g, prec, recon, out, t_o, t_e, WD_EVEN, a, -c, 1, s));
+    return WD_OK;
+}
+
+template <typename Op> int launch_op(const wd_ctx *ctx, const Op &op, int nsite, RedScratch rs, cudaStream_t s)
+{
+    blas_kernel<Op><<<blas_grid(ctx, nsite), BLAS_THREADS, 0, s>>>(op, nsite, rs);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? WD_OK : set_error(WD_ECUDA, "BLAS launch failed: %s", cudaGetErrorString(e));
+}
+
+struct GSolve {
+    const wd_solve_desc *d;
+    int vh;
+    cudaStream_t s = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    char *r, *ax, *t_o, *t_e, *rs, *ps, *aps, *tso, *tse, *xs;
+    double *scal;          // device: 8 slots (see OpDotAlphaDev)
+    RedScratch red;
+    double b2 = 0, stop2 = 0, maxr = 0, r2 = 0;
+    int iters = 0, updates = 0, status = WD_OK;
+    bool active = true;
+    double rel = 0;
+};
+
+template <int PS>
+int graph_iteration(const wd_ctx *ctx, GSolve &q)
+{
+    const wd_solve_desc &d = *q.d;
+    const int vh = q.vh;
+    auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
+    auto FX = [&](const void *p) { return field_ref<PREC_F32>(p, vh); };
+    WD_TRY(apply_mdagm_h(d.gauge, PS, d.opts.inner_recon, d.mass, q.ps, q.aps, q.tso, q.tse, q.s));
+    WD_TRY(launch_op(ctx, OpDotAlphaDev<PS>{FS(q.ps), FS(q.aps), q.scal}, vh, q.red, q.s));
+    OpCgUpdateDev<PREC_F32, PS> up{OpCgUpdate<PREC_F32, PS>{FX(q.xs), FS(q.rs), FS(q.ps), FS(q.aps), q.scal + 2, nullptr},
+                                   q.scal};
+    WD_TRY(launch_op(ctx, up, vh, q.red, q.s));
+    WD_TRY(launch_op(ctx, OpXpayDev<PS>{FS(q.rs), FS(q.ps), q.scal}, vh, q.red, q.s));
+    return WD_OK;
+}
+
+template <int PS>
+int graph_reliable_update(const wd_ctx *ctx, GSolve &q, double *hs)
+{
+    const wd_solve_desc &d = *q.d;
+    const int vh = q.vh;
+    auto F64 = [&](const void *p) { return field_ref<PREC_F64>(p, vh); };
+    auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
+    auto FX = [&](const void *p) { return field_ref<PREC_F32>(p, vh); };
+    WD_TRY(launch_op(ctx, OpAxpby<PREC_F32, PREC_F64>{FX(q.xs), F64(d.x_e), 1.0, 1.0}, vh, q.red, q.s));
+    WD_CUDA_TRY(cudaMemsetAsync(q.xs, 0, half_field_bytes(vh, WD_F32), q.s));
+    WD_TRY(apply_mdagm_h(d.gauge, WD_F64, d.opts.outer_recon, d.mass, (const char *)d.x_e, q.ax, q.t_o, q.t_e, q.s));
+    WD_TRY(launch_op(ctx, OpXmyNorm<PREC_F64>{F64(d.b_e), F64(q.ax), F64(q.r), q.scal + 3}, vh, q.red, q.s));
+    WD_TRY(launch_op(ctx, OpConvert<PS, PREC_F64>{FS(q.rs), F64(q.r)}, vh, q.red, q.s));
+    WD_CUDA_TRY(cudaMemcpyAsync(hs, q.scal + 3, sizeof(double), cudaMemcpyDeviceToHost, q.s));
+    return WD_OK;
+}
+
+template <int PS>
+int run_graph(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stats, cudaStream_t origin)
+{
+    constexpr int K = 8;   // iterations per graph replay
+    std::vector<GSolve> q(n);
+    size_t bytes = 0;
+    std::vector<size_t> off(n);
+    for (int k = 0; k < n; ++k) {
+        const int vh = d[k].gauge->geo.Vh;
+        off[k] = bytes;
+        bytes += 4 * ((size_t)vh * 192 + 256) + 5 * (half_field_bytes(vh, PS) + 256) + (size_t)vh * 96 + 256 + 256 +
+                 (size_t)MAX_RED_BLOCKS * MAX_NR * 8 + 512;
+    }
+    DevBuf work;
+    if (cudaMalloc(&work.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(WD_ENOMEM, "cudaMalloc of %zu bytes for the graph batch failed", bytes);
+    }
+    double *hs = nullptr;
+    WD_CUDA_TRY(cudaMallocHost(&hs, sizeof(double) * 8 * n));
+    struct HostFree { double *p; ~HostFree() { cudaFreeHost(p); } } hf{hs};
+    WD_CUDA_TRY(cudaMemset(work.p, 0, bytes));
+    int rc = WD_OK;
+    for (int k = 0; k < n && rc == WD_OK; ++k) {
+        GSolve &g = q[k];
+        g.d = &d[k];
+        g.vh = d[k].gauge->geo.Vh;
+        char *p = (char *)work.p + off[k];
+        auto take = [&p](size_t nbytes) {
+            char *r = p;
+            p += (nbytes + 255) & ~size_t(255);
+            return r;
+        };
+        const size_t h64 = (size_t)g.vh * 192, hs_b = half_field_bytes(g.vh, PS);
+        g.r = take(h64); g.ax = take(h64); g.t_o = take(h64); g.t_e = take(h64);
+        g.rs = take(hs_b); g.ps = take(hs_b); g.aps = take(hs_b); g.tso = take(hs_b); g.tse = take(hs_b);
+        g.xs = take((size_t)g.vh * 96);
+        g.scal = (double *)take(256);
+        g.red.ticket = (unsigned *)take(256);
+        g.red.partials = (double *)take((size_t)MAX_RED_BLOCKS * MAX_NR * 8);
+        if (cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking) != cudaSuccess) {
+            rc = set_error(WD_ECUDA, "stream creation failed");
+            break;
+        }
+    }
+    // initial state on each solve's stream: b2, x = 0, r = b, rs = ps = b (low precision), xs = 0
+    for (int k = 0; k < n && rc == WD_OK; ++k) {
+        GSolve &g = q[k];
+        const int vh = g.vh;
+        auto F64 = [&](const void *p) { return field_ref<PREC_F64>(p, vh); };
+        auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
+        rc = launch_op(ctx, OpNorm2<PREC_F64>{F64(d[k].b_e), g.scal + 0}, vh, g.red, g.s);
+        if (rc) break;
+        cudaMemsetAsync(d[k].x_e, 0, (size_t)vh * 192, g.s);
+        cudaMemcpyAsync(g.r, d[k].b_e, (size_t)vh * 192, cudaMemcpyDeviceToDevice, g.s);
+        rc = launch_op(ctx, OpConvert<PS, PREC_F64>{FS(g.rs), F64(g.r)}, vh, g.red, g.s);
+        if (rc) break;
+        cudaMemcpyAsync(g.ps, g.rs, half_field_bytes(vh, PS), cudaMemcpyDeviceToDevice, g.s);
+        cudaMemcpyAsync(hs + 8 * k, g.scal, sizeof(double), cudaMemcpyDeviceToHost, g.s);
+    }
+    for (int k = 0; k < n && rc == WD_OK; ++k) {
+        GSolve &g = q[k];
+        if (cudaStreamSynchronize(g.s) != cudaSuccess) { rc = set_error(WD_ECUDA, "batch init failed"); break; }
+        g.b2 = hs[8 * k];
+        g.r2 = g.b2;
+        g.maxr = std::sqrt(g.b2);
+        g.stop2 = d[k].tol * d[k].tol * g.b2;
+        if (!(g.b2 > 0.0)) { g.active = false; g.rel = 0.0; }
+        // capture K iterations
+        cudaGraph_t graph;
+        if (cudaStreamBeginCapture(g.s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            rc = set_error(WD_ECUDA, "stream capture failed");
+            break;
+        }
+        int crc = WD_OK;
+        for (int it = 0; it < K && crc == WD_OK; ++it) crc = graph_iteration<PS>(ctx, g);
+        cudaError_t ce = cudaStreamEndCapture(g.s, &graph);
+        if (crc != WD_OK) { rc = crc; break; }
+        if (ce != cudaSuccess) { rc = set_error(WD_ECUDA, "capture failed: %s", cudaGetErrorString(ce)); break; }
+        ce = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) { rc = set_error(WD_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce)); break; }
+    }
+    // replay until every solve has converged or failed
+    while (rc == WD_OK) {
+        bool any = false;
+        for (int k = 0; k < n; ++k) {
+            GSolve &g = q[k];
+            if (!g.active) continue;
+            any = true;
+            if (cudaGraphLaunch(g.exec, g.s) != cudaSuccess) { rc = set_error(WD_ECUDA, "graph launch failed"); break; }
+            cudaMemcpyAsync(hs + 8 * k, g.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, g.s);
+        }
+        if (!any || rc) break;
+        for (int k = 0; k < n; ++k) {
+            GSolve &g = q[k];
+            if (!g.active) continue;
+            if (cudaStreamSynchronize(g.s) != cudaSuccess) { rc = set_error(WD_ECUDA, "graph replay failed"); break; }
+            g.iters += K;
+            const double r2 = hs[8 * k + 0];
+            const bool broke = hs[8 * k + 6] != 0.0 || !std::isfinite(r2);
+            const double rn = std::sqrt(r2);
+            if (rn > g.maxr) g.maxr = rn;
+            if (broke || rn < d[k].opts.delta * g.maxr || r2 <= g.stop2 || g.iters >= d[k].opts.maxiter) {
+                int urc = graph_reliable_update<PS>(ctx, g, hs + 8 * k + 7);
+                if (urc == WD_OK && cudaStreamSynchronize(g.s) != cudaSuccess) urc = set_error(WD_ECUDA, "update failed");
+                if (urc) { rc = urc; break; }
+                const double r2t = hs[8 * k + 7];
+                g.updates++;
+                g.rel = std::sqrt(r2t / g.b2);
+                if (r2t <= g.stop2) { g.active = false; continue; }
+                if (g.iters >= d[k].opts.maxiter || !std::isfinite(r2t)) {
+                    g.active = false;
+                    g.status = WD_ENOCONV;
+                    continue;
+                }
+                // restart the direction if the iteration broke down; keep it otherwise
+                double sc[8] = {r2t, 0, 0, 0, r2t, 0, 0, 0};
+                cudaMemcpyAsync(g.scal, sc, sizeof(sc), cudaMemcpyHostToDevice, g.s);
+                if (broke) cudaMemcpyAsync(g.ps, g.rs, half_field_bytes(g.vh, PS), cudaMemcpyDeviceToDevice, g.s);
+                cudaStreamSynchronize(g.s);
+                g.maxr = std::sqrt(r2t);
+            }
+        }
+    }
+    for (int k = 0; k < n; ++k) {
+        if (q[k].exec) cudaGraphExecDestroy(q[k].exec);
+        if (q[k].s) cudaStreamDestroy(q[k].s);
+        if (stats) {
+            stats[k].status = rc ? rc : q[k].status;
+            stats[k].iters = q[k].iters;
+            stats[k].reliable_updates = q[k].updates;
+            stats[k].true_rel_resid = q[k].rel;
+        }
+    }
+    (void)origin;
+    if (rc) return rc;
+    for (int k = 0; k < n; ++k)
+        if (q[k].status != WD_OK) return set_error(WD_ENOCONV, "solve %d of the batch did not converge", k);
+    return WD_OK;
+}
+
+} // namespace
+} // namespace wd
+
+using namespace wd;
+
+extern "C" int cg_solve_batch(wd_ctx *ctx, int n, const wd_solve_desc *descs, int mode, wd_cg_stats *stats,
+                              void *stream)
+{
+    clear_error();
+    if (!ctx || n < 0 || (n > 0 && !descs)) return set_error(WD_EINVAL, "bad arguments");
+    if (mode != WD_BATCH_SEQUENTIAL && mode != WD_BATCH_GRAPH && mode != WD_BATCH_PERSISTENT)
+        return set_error(WD_EINVAL, "bad batch mode %d", mode);
+    for (int k = 0; k < n; ++k) WD_TRY(check_desc(descs[k], mode));
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = WD_OK;
+    if (mode == WD_BATCH_SEQUENTIAL) {
+        for (int k = 0; k < n; ++k) {
+            wd_cg_stats st{};
+            int r = cg_solve(ctx, descs[k].gauge, descs[k].mass, descs[k].x_e, descs[k].b_e, descs[k].tol,
+                             &descs[k].opts, &st, stream);
+            if (stats) stats[k] = st;
+            if (r != WD_OK && rc == WD_OK) rc = r;
+        }
+        return rc;
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    for (int k = 0; k < n; ++k) {
+        const wd_solve_desc &d = descs[k];
+        WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(d.gauge), WD_F64, d.opts.outer_recon));
+        WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(d.gauge), d.opts.inner_prec, d.opts.inner_recon));
+        if (d.opts.autotune && mode == WD_BATCH_GRAPH)
+            for (int with_x = 0; with_x < 2; ++with_x) {
+                WD_TRY(hop_ensure_tuned(ctx, d.gauge, WD_F64, d.opts.outer_recon, 0, with_x));
+                WD_TRY(hop_ensure_tuned(ctx, d.gauge, d.opts.inner_prec, d.opts.inner_recon, 0, with_x));
+            }
+    }
+    clear_error();
+    if (mode == WD_BATCH_PERSISTENT) {
+        rc = run_persistent(ctx, n, descs, stats, s);
+    } else {
+        // one inner precision per graph batch (the first descriptor's)
+        const int ps = n > 0 ? descs[0].opts.inner_prec : WD_F32;
+        for (int k = 1; k < n; ++k)
+            if (descs[k].opts.inner_prec != ps) return set_error(WD_EINVAL, "graph batch needs one inner precision");
+        switch (ps) {
+        case WD_F16: rc = run_graph<PREC_F16>(ctx, n, descs, stats, s); break;
+        case WD_BF16: rc = run_graph<PREC_BF16>(ctx, n, descs, stats, s); break;
+        default: rc = run_graph<PREC_F32>(ctx, n, descs, stats, s); break;
+        }
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats)
+        for (int k = 0; k < n; ++k) stats[k].seconds = secs;
+    return rc;
+}

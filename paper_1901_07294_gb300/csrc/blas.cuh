@@ -218,6 +218,67 @@ template <int P> struct OpXmyNorm {
     __device__ __forceinline__ void finish(const double (&s)[1]) const { out[0] = s[0]; }
 };
 
+// ---- CG steps whose scalars live in device memory (replayable in a graph) ----
+// Scalar slots: s[0] = |r|^2 now, s[1] = pAp, s[2] = alpha, s[4] = |r|^2 of
+// the previous step, s[6] = breakdown flag.
+
+// pAp = Re<p, Ap>;  alpha = s[0] / pAp  (alpha = 0 and the flag set on breakdown)
+template <int P> struct OpDotAlphaDev {
+    static constexpr int NR = 1;
+    FieldRef<P> p, q;
+    double *s;
+    __device__ __forceinline__ void site(int j, double (&acc)[1]) const
+    {
+        typename Prec<P>::real u[24], w[24];
+        p.load(j, u);
+        q.load(j, w);
+        typename Prec<P>::real t = 0;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) t = fma(u[k], w[k], t);
+        acc[0] += (double)t;
+    }
+    __device__ __forceinline__ void finish(const double (&r)[1]) const
+    {
+        s[1] = r[0];
+        const bool ok = r[0] > 0.0 && r[0] < 1e300;
+        s[2] = ok ? s[0] / r[0] : 0.0;
+        if (!ok) s[6] = 1.0;
+    }
+};
+
+// r -= alpha Ap; x += alpha p (alpha = s[2]); then s[4] = s[0], s[0] = |r|^2.
+template <int PX, int PR> struct OpCgUpdateDev {
+    static constexpr int NR = 1;
+    OpCgUpdate<PX, PR> u;
+    double *s;
+    __device__ __forceinline__ void site(int j, double (&acc)[1]) const { u.site(j, acc); }
+    __device__ __forceinline__ void finish(const double (&r)[1]) const
+    {
+        s[4] = s[0];
+        s[0] = r[0];
+    }
+};
+
+// p = r + beta p with beta = s[0] / s[4]
+template <int P> struct OpXpayDev {
+    static constexpr int NR = 0;
+    FieldRef<P> r, p;
+    const double *s;
+    __device__ __forceinline__ void site(int j, double (&)[1]) const
+    {
+        using T = typename Prec<P>::real;
+        const double d = s[4];
+        const T beta = (T)(d > 0.0 ? s[0] / d : 0.0);
+        T rv[24], pv[24];
+        r.load(j, rv);
+        p.load(j, pv);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) pv[k] = fma(beta, pv[k], rv[k]);
+        p.store(j, pv);
+    }
+    __device__ __forceinline__ void finish(const double (&)[1]) const {}
+};
+
 // y = a x + b y   (no reduction)
 template <int PX, int PY> struct OpAxpby {
     static constexpr int NR = 0;

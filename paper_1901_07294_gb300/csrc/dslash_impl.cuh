@@ -121,17 +121,13 @@ __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh
 //      data) prefetched into L2 at thread start;
 //   2: as 1, and the backward links prefetched too (even-odd blocks touch
 //      every link once, so all of them come from DRAM).
+// One output site: checkerboard index i < A.vh of parity p, right-hand side
+// at byte offset roff.  Shared by hop_kernel and the persistent solver.
 template <int P, int RECON, bool DAG, bool HAS_X, int PF>
-__global__ void __launch_bounds__(256, 2) hop_kernel(const HopArgs A)
+__device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const int i, const size_t roff)
 {
     using T = typename Prec<P>::real;
-    int p, blk;
-    if (A.nparity == 2) { p = blockIdx.x & 1; blk = blockIdx.x >> 1; }
-    else { p = A.parity0; blk = blockIdx.x; }
-    const int i = blk * blockDim.x + threadIdx.x;
     const int vh = A.vh;
-    if (i >= vh) return;
-    const size_t roff = (size_t)blockIdx.y * A.rhs_stride;
     // parity-dependent pointers chosen by select: a runtime index into the
     // parameter struct would force a copy of it into local memory
     const char *in = (p ? A.in[1] : A.in[0]) + roff;
@@ -220,6 +216,17 @@ __global__ void __launch_bounds__(256, 2) hop_kernel(const HopArgs A)
             }
     }
     Spinor<P>::store((p ? A.out[1] : A.out[0]) + roff, vh, i, o);
+}
+
+template <int P, int RECON, bool DAG, bool HAS_X, int PF>
+__global__ void __launch_bounds__(256, 2) hop_kernel(const HopArgs A)
+{
+    int p, blk;
+    if (A.nparity == 2) { p = blockIdx.x & 1; blk = blockIdx.x >> 1; }
+    else { p = A.parity0; blk = blockIdx.x; }
+    const int i = blk * blockDim.x + threadIdx.x;
+    if (i >= A.vh) return;
+    hop_site<P, RECON, DAG, HAS_X, PF>(A, p, i, (size_t)blockIdx.y * A.rhs_stride);
 }
 
 // Neighbour checkerboard indices of site i of parity p, order

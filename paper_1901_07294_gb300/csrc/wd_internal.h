@@ -86,7 +86,8 @@ struct wd_ctx {
 };
 
 struct wd_gauge {
-    wd_ctx *ctx = nullptr;
+    wd_ctx *ctx = nullptr;         // for tuning lookups; must outlive the gauge's use
+    int device = 0;                // kept here so destruction does not need ctx
     wd::Geometry geo{};
     double *canonical = nullptr;   // device, FP64 canonical links (V*4*18 doubles)
     std::mutex mu;
