@@ -295,6 +295,12 @@ def run_gpu(args):
     mrhs = None
     if not args.no_variants:
         mrhs = _mrhs_section(wd, torch, ctx, U, psi, peak)
+    batch = None
+    if not args.no_cg:
+        batch = _batch_section(wd, torch, ctx)
+    serving = None
+    if not args.no_cg and not args.no_serving:
+        serving = _serving_section(wd, torch, ctx)
     cg = None
     if not args.no_cg:
         cg = _cg_section(wd, torch, ctx, with_cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline))
@@ -325,6 +331,8 @@ def run_gpu(args):
         "variants": variants,
         "multi_rhs": mrhs,
         "cg": cg,
+        "batch": batch,
+        "serving": serving,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline()
@@ -449,6 +457,146 @@ def _mrhs_section(wd, torch, ctx, U, psi, peak, reps=20):
     return out
 
 
+def _batch_section(wd, torch, ctx):
+    """24 solves of uneven volumes (8 each of 8^4, 16^4, 24^3x48), masses U[0.05, 0.5] (seed 4001),
+    tol 1e-10, mixed FP32 reliable-update CG: one persistent launch vs per-solve CUDA graphs vs
+    24 sequential cg_solve calls."""
+    import numpy as np
+
+    import synth
+    rng = np.random.default_rng(4001)
+    lattices = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48)]
+    gauges = {}
+    probs = []
+    for k in range(24):
+        dims = lattices[k // 8]
+        if dims not in gauges:
+            gauges[dims] = wd.Gauge(ctx, dims, synth.gauge(dims, seed=1000 + 10 + k // 8))
+        b = synth.even_spinor(dims, seed=3200 + k)
+        fb = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+        wd.pack(ctx, dims, wd.SITES_EVEN, wd.F64, torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
+        probs.append(dict(gauge=gauges[dims], mass=float(rng.uniform(0.05, 0.5)), tol=1e-10, b=fb,
+                          x=wd.alloc_field(dims, wd.SITES_EVEN, wd.F64), inner_prec=wd.F32, delta=0.1))
+    t0 = time.perf_counter()
+    for p in probs[:1] + probs[8:9] + probs[16:17]:
+        for with_x in (False, True):
+            wd.tune_dslash(ctx, p["gauge"], wd.F32, 18, full=False, with_x=with_x)
+            wd.tune_dslash(ctx, p["gauge"], wd.F64, 18, full=False, with_x=with_x)
+    tune_s = time.perf_counter() - t0
+    out = {"solves": 24, "lattices": [list(d) for d in lattices], "tol": 1e-10, "inner": "fp32 reliable-update",
+           "autotune_seconds": round(tune_s, 3)}
+    for name, mode in (("sequential", wd.BATCH_SEQUENTIAL), ("graph", wd.BATCH_GRAPH),
+                       ("persistent", wd.BATCH_PERSISTENT)):
+        wd.cg_solve_batch(ctx, probs, mode=mode)   # warm
+        best = None
+        for _ in range(2):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = wd.cg_solve_batch(ctx, probs, mode=mode)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if best is None or ms < best[0]:
+                best = (ms, st)
+        ms, st = best
+        out[name] = {"seconds": round(ms / 1e3, 4), "solves_per_s": round(24 / (ms / 1e3), 1),
+                     "iters_total": int(sum(s["iters"] for s in st)),
+                     "max_true_rel_resid": max(s["true_rel_resid"] for s in st),
+                     "all_converged": all(s["status"] == 0 for s in st)}
+    for g in gauges.values():
+        g.close()
+    return out
+
+
+def _serving_section(wd, torch, ctx, n_main=600, n_sweep=150, warm=60):
+    """Serving: Poisson arrivals of CG solve requests (volumes uniform over 8^4, 16^4, 24^3x48,
+    32^3x64; masses log-uniform in [0.02, 0.5]; tolerances in {1e-8, 1e-10, 1e-12}) on resident
+    smoothed-SU(3) configurations, continuous batching with HBM admission.  Headline at 200 req/s
+    plus a rate sweep; p50/p99 of submit->result latency."""
+    import queue as pyqueue
+    import threading as th
+
+    import numpy as np
+
+    import synth
+    vols = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48), (32, 32, 32, 64)]
+    gauges, srcs = {}, {}
+    for k, dims in enumerate(vols):
+        gauges[dims] = wd.Gauge(ctx, dims, synth.gauge(dims, seed=1000 + 20 + k))
+        srcs[dims] = []
+        for j in range(2):   # a small pool of Gaussian sources per volume
+            b = synth.even_spinor(dims, seed=5100 + 10 * k + j)
+            fb = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+            wd.pack(ctx, dims, wd.SITES_EVEN, wd.F64, torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
+            srcs[dims].append(fb)
+        for with_x in (False, True):
+            wd.tune_dslash(ctx, gauges[dims], wd.F16, 18, full=False, with_x=with_x)
+            wd.tune_dslash(ctx, gauges[dims], wd.F64, 18, full=False, with_x=with_x)
+    torch.cuda.synchronize()
+    pools = {d: [] for d in vols}   # free output buffers per volume
+
+    def run(rate, n, seed):
+        rng = np.random.default_rng(seed)
+        q = wd.Queue(ctx, hbm_budget_bytes=48 << 30, max_slots=32)
+        waits = pyqueue.Queue()
+        results = []
+
+        def waiter():
+            while True:
+                item = waits.get()
+                if item is None:
+                    return
+                t, dims, x, tol = item
+                r = q.wait(t)
+                pools[dims].append(x)
+                results.append((tol, r))
+
+        wt = th.Thread(target=waiter)
+        wt.start()
+        t_next = time.perf_counter()
+        for i in range(n):
+            dims = vols[rng.integers(0, 4)]
+            mass = float(np.exp(rng.uniform(np.log(0.02), np.log(0.5))))
+            tol = float([1e-8, 1e-10, 1e-12][rng.integers(0, 3)])
+            t_next += rng.exponential(1.0 / rate)
+            while time.perf_counter() < t_next:
+                time.sleep(max(0.0, min(0.0005, t_next - time.perf_counter())))
+            x = pools[dims].pop() if pools[dims] else wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+            t = q.submit(dict(gauge=gauges[dims], mass=mass, tol=tol, b=srcs[dims][i % 2], x=x,
+                              inner_prec=wd.F16, delta=0.1))
+            waits.put((t, dims, x, tol))
+        waits.put(None)
+        wt.join()
+        st = q.stats()
+        q.close()
+        return results, st
+
+    def summarise(results, st, rate, skip):
+        tols = [t for t, _ in results][skip:]
+        res = [r for _, r in results][skip:]
+        lat = np.array([r["t_finish"] - r["t_submit"] for r in res])
+        span = max(r["t_finish"] for r in res) - min(r["t_submit"] for r in res)
+        ok = sum(1 for r in res if r["status"] == 0)
+        return {"offered_per_s": rate, "requests": len(res), "converged": ok,
+                "achieved_per_s": round(len(res) / span, 2), "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 2),
+                "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 2), "mean_running": round(st["mean_running"], 2),
+                "admission_stalls": int(st["admission_stalls"]),
+                "max_true_resid_over_tol": round(max(r["cg_true_rel_resid"] / t for t, r in zip(tols, res)), 4)}
+
+    out = {"volumes": [list(v) for v in vols], "inner": "fp16 storage, fp32 compute, fp64 reliable updates",
+           "queue": {"hbm_budget_gb": 48, "max_slots": 32, "iterations_per_step": 8}}
+    results, st = run(200.0, n_main + warm, 5001)
+    out["rate_200"] = summarise(results, st, 200.0, warm)
+    out["sweep"] = []
+    for rate in (10.0, 25.0, 50.0, 100.0):
+        results, st = run(rate, n_sweep, 5002 + int(rate))
+        out["sweep"].append(summarise(results, st, rate, 10))
+    for g in gauges.values():
+        g.close()
+    return out
+
+
 def _cg_section(wd, torch, ctx, with_cpu: bool):
     """Mixed-precision vs FP64 CG on the even-odd normal equations, 24^3x48, tol 1e-10."""
     import numpy as np
@@ -513,6 +661,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--launch", default="", help="THREADS,VARIANT: pin the headline launch shape instead of tuning")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -275,6 +275,55 @@ typedef struct {
 int cg_solve_batch(wd_ctx *ctx, int n, const wd_solve_desc *descs, int mode, wd_cg_stats *stats,
                    void *stream);
 
+/* ---- Request queue with continuous batching (serving) ------------------------
+ * rq_create starts a scheduler thread for the context's device.  Requests are
+ * wd_solve_desc problems (mixed-precision reliable-update CG: inner_prec
+ * WD_F32, WD_F16 or WD_BF16) whose gauge and fields stay resident; x_e and b_e
+ * are the caller's device buffers and must stay valid until the request's
+ * result has been taken.  Each scheduler step admits waiting requests while
+ * fewer than max_slots run and their workspace fits hbm_budget_bytes (first
+ * come first served, a request that fits may pass one that does not), runs 8
+ * CG iterations of every running request (each on its own stream, so they
+ * overlap), then checks residuals, does FP64 reliable updates and retires
+ * finished requests.  Requests join and leave between steps.
+ *   rq_submit: non-blocking, thread-safe; copies the descriptor; WD_ENOMEM if
+ *              the request alone exceeds the budget.
+ *   rq_poll:   WD_EBUSY while running; otherwise fills the result and forgets
+ *              the ticket.
+ *   rq_wait:   blocks up to timeout_ms (< 0: forever); WD_ETIMEOUT if still
+ *              running (the request keeps running).
+ *   rq_cancel: a waiting request ends at once with WD_ECANCELLED; a running one
+ *              at the end of the current step.
+ *   rq_destroy: finishes every submitted request, then stops and frees.
+ * Times in wd_solve_result are seconds since rq_create.  A request whose
+ * source is not finite ends with WD_EINVAL without affecting the others. */
+typedef struct rq_queue rq_queue;
+
+typedef struct {
+    int status;          /* wd_status of the solve */
+    wd_cg_stats stats;   /* stats.seconds = t_finish - t_submit */
+    double t_submit, t_admit, t_start, t_finish;
+} wd_solve_result;
+
+typedef struct {
+    uint64_t submitted, completed, admission_stalls, steps;
+    double mean_running;     /* running requests per scheduler step, averaged */
+    int waiting, running;
+    size_t hbm_in_use;
+} rq_counters;
+
+/* Device workspace bytes one queued (or graph-batched) solve on this lattice
+ * allocates while it runs: what the queue counts against its budget. */
+int wd_solve_workspace_bytes(const int dims[4], int inner_prec, size_t *out);
+
+int rq_create(wd_ctx *ctx, size_t hbm_budget_bytes, int max_slots, rq_queue **out);
+int rq_submit(rq_queue *q, const wd_solve_desc *desc, uint64_t *ticket);
+int rq_poll(rq_queue *q, uint64_t ticket, wd_solve_result *out);
+int rq_wait(rq_queue *q, uint64_t ticket, int timeout_ms, wd_solve_result *out);
+int rq_cancel(rq_queue *q, uint64_t ticket);
+int rq_stats(rq_queue *q, rq_counters *out);
+int rq_destroy(rq_queue *q);
+
 #ifdef __cplusplus
 }
 #endif

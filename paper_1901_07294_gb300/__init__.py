@@ -63,6 +63,14 @@ _SIGS = {
     "wd_tune_set_dslash": (_ip, [_vp, _vp, _ip, _ip, _ip, _ip, _ip, _ip, _ip]),
     "wd_tune_clear": (_ip, [_vp]),
     "cg_solve_batch": (_ip, [_vp, _ip, _vp, _ip, _vp, _vp]),
+    "rq_create": (_ip, [_vp, _sz, _ip, ctypes.POINTER(_vp)]),
+    "rq_submit": (_ip, [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "rq_poll": (_ip, [_vp, ctypes.c_uint64, _vp]),
+    "rq_wait": (_ip, [_vp, ctypes.c_uint64, _ip, _vp]),
+    "rq_cancel": (_ip, [_vp, ctypes.c_uint64]),
+    "rq_stats": (_ip, [_vp, _vp]),
+    "rq_destroy": (_ip, [_vp]),
+    "wd_solve_workspace_bytes": (_ip, [_DIMS, _ip, ctypes.POINTER(_sz)]),
 }
 
 
@@ -344,3 +352,82 @@ def cg_solve_batch(ctx: Context, problems: list[dict], mode: int = BATCH_SEQUENT
     for d in out:
         d["batch_status"] = rc
     return out
+
+
+class SolveResult(ctypes.Structure):
+    """wd_solve_result"""
+    _fields_ = [("status", _ip), ("stats", CgStats), ("t_submit", _dp), ("t_admit", _dp), ("t_start", _dp),
+                ("t_finish", _dp)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "stats"}
+        d.update({f"cg_{k}": v for k, v in self.stats.as_dict().items()})
+        return d
+
+
+class RqCounters(ctypes.Structure):
+    """rq_counters"""
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("admission_stalls", ctypes.c_uint64),
+                ("steps", ctypes.c_uint64), ("mean_running", _dp), ("waiting", _ip), ("running", _ip),
+                ("hbm_in_use", _sz)]
+
+
+def _desc(p: dict) -> SolveDesc:
+    o = CgOpts(int(p.get("inner_prec", F16)), int(p.get("inner_recon", 18)), int(p.get("outer_recon", 18)),
+               int(bool(p.get("reliable", True))), float(p.get("delta", 0.1)), int(p.get("maxiter", 20000)),
+               int(bool(p.get("autotune", False))))
+    return SolveDesc(p["gauge"].handle, float(p["mass"]), float(p["tol"]), _ptr(p["x"]), _ptr(p["b"]), o)
+
+
+class Queue:
+    """Solve-request queue with continuous batching (rq_* of the C ABI)."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int, max_slots: int):
+        self._h = _vp()
+        self.ctx = ctx
+        _check(load().rq_create(ctx.handle, _sz(int(hbm_budget_bytes)), int(max_slots), ctypes.byref(self._h)))
+
+    def submit(self, problem: dict) -> int:
+        t = ctypes.c_uint64(0)
+        d = _desc(problem)
+        _check(load().rq_submit(self._h, ctypes.byref(d), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        r = SolveResult()
+        rc = load().rq_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if rc == WD_EBUSY:
+            return None
+        _check(rc)
+        return r.as_dict()
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        r = SolveResult()
+        _check(load().rq_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(r)))
+        return r.as_dict()
+
+    def cancel(self, ticket: int) -> None:
+        _check(load().rq_cancel(self._h, ctypes.c_uint64(ticket)))
+
+    def stats(self) -> dict:
+        c = RqCounters()
+        _check(load().rq_stats(self._h, ctypes.byref(c)))
+        return {k: getattr(c, k) for k, _ in c._fields_}
+
+    def close(self) -> None:
+        if self._h:
+            load().rq_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_workspace_bytes(dims, inner_prec: int) -> int:
+    """Device workspace one queued (or graph-batched) solve allocates while it runs."""
+    out = _sz()
+    _check(load().wd_solve_workspace_bytes(_dims(dims), int(inner_prec), ctypes.byref(out)))
+    return int(out.value)

@@ -26,6 +26,7 @@
 
 #include "blas_host.cuh"
 #include "dslash_impl.cuh"
+#include "gsolve.cuh"
 
 namespace wd {
 
@@ -455,212 +456,52 @@ int run_persistent(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stat
 }
 
 // ---------------------------------------------------------------------------
-// graph mode
+// graph mode (per-solve graphs, see gsolve.cuh)
 // ---------------------------------------------------------------------------
-int apply_mdagm_h(const wd_gauge *g, int prec, int recon, double mass, const char *in, char *out, char *t_o,
-                  char *t_e, cudaStream_t s)
+int run_graph(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stats)
 {
-    const double a = mass + 4.0, c = 1.0 / (4.0 * (mass + 4.0));
-    WD_TRY(eo_hop(g, prec, recon, t_o, in, nullptr, WD_ODD, 0.0, 1.0, 0, s));
-    WD_TRY(eo_hop(g, prec, recon, t_e, t_o, in, WD_EVEN, a, -c, 0, s));
-    WD_TRY(eo_hop(g, prec, recon, t_o, t_e, nullptr, WD_ODD, 0.0, 1.0, 1, s));
-    WD_TRY(eo_hop(g, prec, recon, out, t_o, t_e, WD_EVEN, a, -c, 1, s));
-    return WD_OK;
-}
-
-template <typename Op> int launch_op(const wd_ctx *ctx, const Op &op, int nsite, RedScratch rs, cudaStream_t s)
-{
-    blas_kernel<Op><<<blas_grid(ctx, nsite), BLAS_THREADS, 0, s>>>(op, nsite, rs);
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? WD_OK : set_error(WD_ECUDA, "BLAS launch failed: %s", cudaGetErrorString(e));
-}
-
-struct GSolve {
-    const wd_solve_desc *d;
-    int vh;
-    cudaStream_t s = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    char *r, *ax, *t_o, *t_e, *rs, *ps, *aps, *tso, *tse, *xs;
-    double *scal;          // device: 8 slots (see OpDotAlphaDev)
-    RedScratch red;
-    double b2 = 0, stop2 = 0, maxr = 0, r2 = 0;
-    int iters = 0, updates = 0, status = WD_OK;
-    bool active = true;
-    double rel = 0;
-};
-
-template <int PS>
-int graph_iteration(const wd_ctx *ctx, GSolve &q)
-{
-    const wd_solve_desc &d = *q.d;
-    const int vh = q.vh;
-    auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
-    auto FX = [&](const void *p) { return field_ref<PREC_F32>(p, vh); };
-    WD_TRY(apply_mdagm_h(d.gauge, PS, d.opts.inner_recon, d.mass, q.ps, q.aps, q.tso, q.tse, q.s));
-    WD_TRY(launch_op(ctx, OpDotAlphaDev<PS>{FS(q.ps), FS(q.aps), q.scal}, vh, q.red, q.s));
-    OpCgUpdateDev<PREC_F32, PS> up{OpCgUpdate<PREC_F32, PS>{FX(q.xs), FS(q.rs), FS(q.ps), FS(q.aps), q.scal + 2, nullptr},
-                                   q.scal};
-    WD_TRY(launch_op(ctx, up, vh, q.red, q.s));
-    WD_TRY(launch_op(ctx, OpXpayDev<PS>{FS(q.rs), FS(q.ps), q.scal}, vh, q.red, q.s));
-    return WD_OK;
-}
-
-template <int PS>
-int graph_reliable_update(const wd_ctx *ctx, GSolve &q, double *hs)
-{
-    const wd_solve_desc &d = *q.d;
-    const int vh = q.vh;
-    auto F64 = [&](const void *p) { return field_ref<PREC_F64>(p, vh); };
-    auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
-    auto FX = [&](const void *p) { return field_ref<PREC_F32>(p, vh); };
-    WD_TRY(launch_op(ctx, OpAxpby<PREC_F32, PREC_F64>{FX(q.xs), F64(d.x_e), 1.0, 1.0}, vh, q.red, q.s));
-    WD_CUDA_TRY(cudaMemsetAsync(q.xs, 0, half_field_bytes(vh, WD_F32), q.s));
-    WD_TRY(apply_mdagm_h(d.gauge, WD_F64, d.opts.outer_recon, d.mass, (const char *)d.x_e, q.ax, q.t_o, q.t_e, q.s));
-    WD_TRY(launch_op(ctx, OpXmyNorm<PREC_F64>{F64(d.b_e), F64(q.ax), F64(q.r), q.scal + 3}, vh, q.red, q.s));
-    WD_TRY(launch_op(ctx, OpConvert<PS, PREC_F64>{FS(q.rs), F64(q.r)}, vh, q.red, q.s));
-    WD_CUDA_TRY(cudaMemcpyAsync(hs, q.scal + 3, sizeof(double), cudaMemcpyDeviceToHost, q.s));
-    return WD_OK;
-}
-
-template <int PS>
-int run_graph(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stats, cudaStream_t origin)
-{
-    constexpr int K = 8;   // iterations per graph replay
     std::vector<GSolve> q(n);
-    size_t bytes = 0;
-    std::vector<size_t> off(n);
-    for (int k = 0; k < n; ++k) {
-        const int vh = d[k].gauge->geo.Vh;
-        off[k] = bytes;
-        bytes += 4 * ((size_t)vh * 192 + 256) + 5 * (half_field_bytes(vh, PS) + 256) + (size_t)vh * 96 + 256 + 256 +
-                 (size_t)MAX_RED_BLOCKS * MAX_NR * 8 + 512;
-    }
-    DevBuf work;
-    if (cudaMalloc(&work.p, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(WD_ENOMEM, "cudaMalloc of %zu bytes for the graph batch failed", bytes);
-    }
-    double *hs = nullptr;
-    WD_CUDA_TRY(cudaMallocHost(&hs, sizeof(double) * 8 * n));
-    struct HostFree { double *p; ~HostFree() { cudaFreeHost(p); } } hf{hs};
-    WD_CUDA_TRY(cudaMemset(work.p, 0, bytes));
     int rc = WD_OK;
     for (int k = 0; k < n && rc == WD_OK; ++k) {
-        GSolve &g = q[k];
-        g.d = &d[k];
-        g.vh = d[k].gauge->geo.Vh;
-        char *p = (char *)work.p + off[k];
-        auto take = [&p](size_t nbytes) {
-            char *r = p;
-            p += (nbytes + 255) & ~size_t(255);
-            return r;
-        };
-        const size_t h64 = (size_t)g.vh * 192, hs_b = half_field_bytes(g.vh, PS);
-        g.r = take(h64); g.ax = take(h64); g.t_o = take(h64); g.t_e = take(h64);
-        g.rs = take(hs_b); g.ps = take(hs_b); g.aps = take(hs_b); g.tso = take(hs_b); g.tse = take(hs_b);
-        g.xs = take((size_t)g.vh * 96);
-        g.scal = (double *)take(256);
-        g.red.ticket = (unsigned *)take(256);
-        g.red.partials = (double *)take((size_t)MAX_RED_BLOCKS * MAX_NR * 8);
-        if (cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking) != cudaSuccess) {
-            rc = set_error(WD_ECUDA, "stream creation failed");
-            break;
-        }
-    }
-    // initial state on each solve's stream: b2, x = 0, r = b, rs = ps = b (low precision), xs = 0
-    for (int k = 0; k < n && rc == WD_OK; ++k) {
-        GSolve &g = q[k];
-        const int vh = g.vh;
-        auto F64 = [&](const void *p) { return field_ref<PREC_F64>(p, vh); };
-        auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
-        rc = launch_op(ctx, OpNorm2<PREC_F64>{F64(d[k].b_e), g.scal + 0}, vh, g.red, g.s);
-        if (rc) break;
-        cudaMemsetAsync(d[k].x_e, 0, (size_t)vh * 192, g.s);
-        cudaMemcpyAsync(g.r, d[k].b_e, (size_t)vh * 192, cudaMemcpyDeviceToDevice, g.s);
-        rc = launch_op(ctx, OpConvert<PS, PREC_F64>{FS(g.rs), F64(g.r)}, vh, g.red, g.s);
-        if (rc) break;
-        cudaMemcpyAsync(g.ps, g.rs, half_field_bytes(vh, PS), cudaMemcpyDeviceToDevice, g.s);
-        cudaMemcpyAsync(hs + 8 * k, g.scal, sizeof(double), cudaMemcpyDeviceToHost, g.s);
+        q[k].gauge = d[k].gauge;
+        q[k].mass = d[k].mass;
+        q[k].tol = d[k].tol;
+        q[k].x = d[k].x_e;
+        q[k].b = d[k].b_e;
+        q[k].opts = d[k].opts;
+        rc = gs_setup(ctx, q[k]);
     }
     for (int k = 0; k < n && rc == WD_OK; ++k) {
-        GSolve &g = q[k];
-        if (cudaStreamSynchronize(g.s) != cudaSuccess) { rc = set_error(WD_ECUDA, "batch init failed"); break; }
-        g.b2 = hs[8 * k];
-        g.r2 = g.b2;
-        g.maxr = std::sqrt(g.b2);
-        g.stop2 = d[k].tol * d[k].tol * g.b2;
-        if (!(g.b2 > 0.0)) { g.active = false; g.rel = 0.0; }
-        // capture K iterations
-        cudaGraph_t graph;
-        if (cudaStreamBeginCapture(g.s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-            rc = set_error(WD_ECUDA, "stream capture failed");
-            break;
-        }
-        int crc = WD_OK;
-        for (int it = 0; it < K && crc == WD_OK; ++it) crc = graph_iteration<PS>(ctx, g);
-        cudaError_t ce = cudaStreamEndCapture(g.s, &graph);
-        if (crc != WD_OK) { rc = crc; break; }
-        if (ce != cudaSuccess) { rc = set_error(WD_ECUDA, "capture failed: %s", cudaGetErrorString(ce)); break; }
-        ce = cudaGraphInstantiate(&g.exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) { rc = set_error(WD_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce)); break; }
+        if (cudaStreamSynchronize(q[k].s) != cudaSuccess) rc = set_error(WD_ECUDA, "batch set-up failed");
+        else gs_start(q[k]);
     }
-    // replay until every solve has converged or failed
     while (rc == WD_OK) {
         bool any = false;
-        for (int k = 0; k < n; ++k) {
-            GSolve &g = q[k];
-            if (!g.active) continue;
-            any = true;
-            if (cudaGraphLaunch(g.exec, g.s) != cudaSuccess) { rc = set_error(WD_ECUDA, "graph launch failed"); break; }
-            cudaMemcpyAsync(hs + 8 * k, g.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, g.s);
-        }
-        if (!any || rc) break;
-        for (int k = 0; k < n; ++k) {
-            GSolve &g = q[k];
-            if (!g.active) continue;
-            if (cudaStreamSynchronize(g.s) != cudaSuccess) { rc = set_error(WD_ECUDA, "graph replay failed"); break; }
-            g.iters += K;
-            const double r2 = hs[8 * k + 0];
-            const bool broke = hs[8 * k + 6] != 0.0 || !std::isfinite(r2);
-            const double rn = std::sqrt(r2);
-            if (rn > g.maxr) g.maxr = rn;
-            if (broke || rn < d[k].opts.delta * g.maxr || r2 <= g.stop2 || g.iters >= d[k].opts.maxiter) {
-                int urc = graph_reliable_update<PS>(ctx, g, hs + 8 * k + 7);
-                if (urc == WD_OK && cudaStreamSynchronize(g.s) != cudaSuccess) urc = set_error(WD_ECUDA, "update failed");
-                if (urc) { rc = urc; break; }
-                const double r2t = hs[8 * k + 7];
-                g.updates++;
-                g.rel = std::sqrt(r2t / g.b2);
-                if (r2t <= g.stop2) { g.active = false; continue; }
-                if (g.iters >= d[k].opts.maxiter || !std::isfinite(r2t)) {
-                    g.active = false;
-                    g.status = WD_ENOCONV;
-                    continue;
-                }
-                // restart the direction if the iteration broke down; keep it otherwise
-                double sc[8] = {r2t, 0, 0, 0, r2t, 0, 0, 0};
-                cudaMemcpyAsync(g.scal, sc, sizeof(sc), cudaMemcpyHostToDevice, g.s);
-                if (broke) cudaMemcpyAsync(g.ps, g.rs, half_field_bytes(g.vh, PS), cudaMemcpyDeviceToDevice, g.s);
-                cudaStreamSynchronize(g.s);
-                g.maxr = std::sqrt(r2t);
+        for (int k = 0; k < n && rc == WD_OK; ++k)
+            if (q[k].active) {
+                any = true;
+                rc = gs_launch(q[k]);
             }
-        }
+        if (!any) break;
+        for (int k = 0; k < n && rc == WD_OK; ++k)
+            if (q[k].active) {
+                if (cudaStreamSynchronize(q[k].s) != cudaSuccess) rc = set_error(WD_ECUDA, "graph replay failed");
+                else rc = gs_after(ctx, q[k]);
+            }
     }
+    int first_bad = -1;
     for (int k = 0; k < n; ++k) {
-        if (q[k].exec) cudaGraphExecDestroy(q[k].exec);
-        if (q[k].s) cudaStreamDestroy(q[k].s);
         if (stats) {
             stats[k].status = rc ? rc : q[k].status;
             stats[k].iters = q[k].iters;
             stats[k].reliable_updates = q[k].updates;
             stats[k].true_rel_resid = q[k].rel;
         }
+        if (q[k].status != WD_OK && first_bad < 0) first_bad = k;
+        gs_release(q[k]);
     }
-    (void)origin;
     if (rc) return rc;
-    for (int k = 0; k < n; ++k)
-        if (q[k].status != WD_OK) return set_error(WD_ENOCONV, "solve %d of the batch did not converge", k);
+    if (first_bad >= 0) return set_error(q[first_bad].status, "solve %d of the batch failed", first_bad);
     return WD_OK;
 }
 
@@ -706,15 +547,7 @@ extern "C" int cg_solve_batch(wd_ctx *ctx, int n, const wd_solve_desc *descs, in
     if (mode == WD_BATCH_PERSISTENT) {
         rc = run_persistent(ctx, n, descs, stats, s);
     } else {
-        // one inner precision per graph batch (the first descriptor's)
-        const int ps = n > 0 ? descs[0].opts.inner_prec : WD_F32;
-        for (int k = 1; k < n; ++k)
-            if (descs[k].opts.inner_prec != ps) return set_error(WD_EINVAL, "graph batch needs one inner precision");
-        switch (ps) {
-        case WD_F16: rc = run_graph<PREC_F16>(ctx, n, descs, stats, s); break;
-        case WD_BF16: rc = run_graph<PREC_BF16>(ctx, n, descs, stats, s); break;
-        default: rc = run_graph<PREC_F32>(ctx, n, descs, stats, s); break;
-        }
+        rc = run_graph(ctx, n, descs, stats);
     }
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (stats)

@@ -1,0 +1,239 @@
+// One mixed-precision reliable-update CG solve driven by a captured CUDA graph.
+//
+// Shared by the graph batch mode and the request queue.  A solve owns its
+// workspace, a stream, per-solve reduction scratch and a graph holding
+// GS_ITERS iterations (4 hop launches and 3 BLAS kernels each, with every CG
+// scalar kept in device memory).  The host replays the graph, reads the
+// scalars, and does the FP64 reliable updates (x += x_lo, r = b - A x) and
+// the convergence test between replays.
+#pragma once
+
+#include <cmath>
+#include <cstring>
+
+#include "blas_host.cuh"
+
+namespace wd {
+
+constexpr int GS_ITERS = 8;   // CG iterations per graph replay
+
+struct GSolve {
+    // problem
+    const wd_gauge *gauge = nullptr;
+    double mass = 0, tol = 0;
+    void *x = nullptr;
+    const void *b = nullptr;
+    wd_cg_opts opts{};
+    int vh = 0, prec = WD_F32;
+    // resources
+    cudaStream_t s = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void *mem = nullptr;
+    double *h = nullptr;   // pinned host copy of the scalars
+    char *r = nullptr, *ax = nullptr, *t_o = nullptr, *t_e = nullptr;
+    char *rs = nullptr, *ps = nullptr, *aps = nullptr, *tso = nullptr, *tse = nullptr, *xs = nullptr;
+    double *scal = nullptr;   // device scalars, see OpDotAlphaDev
+    RedScratch red{};
+    // state
+    double b2 = 0, stop2 = 0, maxr = 0;
+    int iters = 0, updates = 0, status = WD_OK;
+    bool active = true;
+    double rel = 1.0;
+};
+
+inline size_t gs_footprint(int vh, int prec)
+{
+    return 4 * ((size_t)vh * 192 + 256) + 5 * (half_field_bytes(vh, prec) + 256) + (size_t)vh * 96 + 256 + 512 +
+           (size_t)MAX_RED_BLOCKS * MAX_NR * 8 + 256;
+}
+
+namespace gs_detail {
+
+inline int mdagm(const wd_gauge *g, int prec, int recon, double mass, const char *in, char *out, char *t_o,
+                 char *t_e, cudaStream_t s)
+{
+    const double a = mass + 4.0, c = 1.0 / (4.0 * (mass + 4.0));
+    WD_TRY(eo_hop(g, prec, recon, t_o, in, nullptr, WD_ODD, 0.0, 1.0, 0, s));
+    WD_TRY(eo_hop(g, prec, recon, t_e, t_o, in, WD_EVEN, a, -c, 0, s));
+    WD_TRY(eo_hop(g, prec, recon, t_o, t_e, nullptr, WD_ODD, 0.0, 1.0, 1, s));
+    WD_TRY(eo_hop(g, prec, recon, out, t_o, t_e, WD_EVEN, a, -c, 1, s));
+    return WD_OK;
+}
+
+template <typename Op> inline int launch(const wd_ctx *ctx, const Op &op, int nsite, RedScratch rs, cudaStream_t s)
+{
+    blas_kernel<Op><<<blas_grid(ctx, nsite), BLAS_THREADS, 0, s>>>(op, nsite, rs);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? WD_OK : set_error(WD_ECUDA, "BLAS launch failed: %s", cudaGetErrorString(e));
+}
+
+template <int PS> int iteration(const wd_ctx *ctx, GSolve &q)
+{
+    const int vh = q.vh;
+    auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
+    auto FX = [&](const void *p) { return field_ref<PREC_F32>(p, vh); };
+    WD_TRY(mdagm(q.gauge, PS, q.opts.inner_recon, q.mass, q.ps, q.aps, q.tso, q.tse, q.s));
+    WD_TRY(launch(ctx, OpDotAlphaDev<PS>{FS(q.ps), FS(q.aps), q.scal}, vh, q.red, q.s));
+    OpCgUpdateDev<PREC_F32, PS> up{
+        OpCgUpdate<PREC_F32, PS>{FX(q.xs), FS(q.rs), FS(q.ps), FS(q.aps), q.scal + 2, nullptr}, q.scal};
+    WD_TRY(launch(ctx, up, vh, q.red, q.s));
+    WD_TRY(launch(ctx, OpXpayDev<PS>{FS(q.rs), FS(q.ps), q.scal}, vh, q.red, q.s));
+    return WD_OK;
+}
+
+// x += x_lo; r = b - A x (FP64); r_lo = r; |r|^2 -> h[7] (asynchronous).
+template <int PS> int reliable_update(const wd_ctx *ctx, GSolve &q)
+{
+    const int vh = q.vh;
+    auto F64 = [&](const void *p) { return field_ref<PREC_F64>(p, vh); };
+    auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
+    auto FX = [&](const void *p) { return field_ref<PREC_F32>(p, vh); };
+    WD_TRY(launch(ctx, OpAxpby<PREC_F32, PREC_F64>{FX(q.xs), F64(q.x), 1.0, 1.0}, vh, q.red, q.s));
+    WD_CUDA_TRY(cudaMemsetAsync(q.xs, 0, half_field_bytes(vh, WD_F32), q.s));
+    WD_TRY(mdagm(q.gauge, WD_F64, q.opts.outer_recon, q.mass, (const char *)q.x, q.ax, q.t_o, q.t_e, q.s));
+    WD_TRY(launch(ctx, OpXmyNorm<PREC_F64>{F64(q.b), F64(q.ax), F64(q.r), q.scal + 3}, vh, q.red, q.s));
+    WD_TRY(launch(ctx, OpConvert<PS, PREC_F64>{FS(q.rs), F64(q.r)}, vh, q.red, q.s));
+    WD_CUDA_TRY(cudaMemcpyAsync(q.h + 7, q.scal + 3, sizeof(double), cudaMemcpyDeviceToHost, q.s));
+    return WD_OK;
+}
+
+template <int PS> int init(const wd_ctx *ctx, GSolve &q)
+{
+    const int vh = q.vh;
+    auto F64 = [&](const void *p) { return field_ref<PREC_F64>(p, vh); };
+    auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
+    WD_CUDA_TRY(cudaMemsetAsync(q.mem, 0, gs_footprint(vh, PS), q.s));
+    WD_TRY(launch(ctx, OpNorm2<PREC_F64>{F64(q.b), q.scal}, vh, q.red, q.s));
+    WD_CUDA_TRY(cudaMemsetAsync(q.x, 0, (size_t)vh * 192, q.s));
+    WD_CUDA_TRY(cudaMemcpyAsync(q.r, q.b, (size_t)vh * 192, cudaMemcpyDeviceToDevice, q.s));
+    WD_TRY(launch(ctx, OpConvert<PS, PREC_F64>{FS(q.rs), F64(q.r)}, vh, q.red, q.s));
+    WD_CUDA_TRY(cudaMemcpyAsync(q.ps, q.rs, half_field_bytes(vh, PS), cudaMemcpyDeviceToDevice, q.s));
+    WD_CUDA_TRY(cudaMemcpyAsync(q.h, q.scal, sizeof(double), cudaMemcpyDeviceToHost, q.s));
+    // capture GS_ITERS iterations
+    cudaGraph_t graph;
+    WD_CUDA_TRY(cudaStreamBeginCapture(q.s, cudaStreamCaptureModeThreadLocal));
+    int rc = WD_OK;
+    for (int it = 0; it < GS_ITERS && rc == WD_OK; ++it) rc = iteration<PS>(ctx, q);
+    cudaError_t ce = cudaStreamEndCapture(q.s, &graph);
+    if (rc != WD_OK) return rc;
+    if (ce != cudaSuccess) return set_error(WD_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&q.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return set_error(WD_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+    return WD_OK;
+}
+
+} // namespace gs_detail
+
+#define WD_GS_DISPATCH(prec, CALL)                                            \
+    switch (prec) {                                                           \
+    case WD_F16: { constexpr int PS = PREC_F16; return CALL; }                \
+    case WD_BF16: { constexpr int PS = PREC_BF16; return CALL; }              \
+    default: { constexpr int PS = PREC_F32; return CALL; }                    \
+    }
+
+// Allocates the solve's resources and enqueues its initial state and graph
+// capture on its own stream.  Returns WD_ENOMEM if the workspace does not fit.
+inline int gs_setup(const wd_ctx *ctx, GSolve &q, bool inject_alloc_failure = false)
+{
+    q.vh = q.gauge->geo.Vh;
+    q.prec = q.opts.inner_prec;
+    const size_t bytes = gs_footprint(q.vh, q.prec);
+    if (inject_alloc_failure) return set_error(WD_ENOMEM, "injected allocation failure (WD_FAULT=alloc)");
+    if (cudaMalloc(&q.mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        q.mem = nullptr;
+        return set_error(WD_ENOMEM, "cudaMalloc of %zu bytes of solve workspace failed", bytes);
+    }
+    WD_CUDA_TRY(cudaMallocHost(&q.h, 8 * sizeof(double)));
+    std::memset(q.h, 0, 8 * sizeof(double));
+    WD_CUDA_TRY(cudaStreamCreateWithFlags(&q.s, cudaStreamNonBlocking));
+    char *p = (char *)q.mem;
+    auto take = [&p](size_t n) {
+        char *r = p;
+        p += (n + 255) & ~size_t(255);
+        return r;
+    };
+    const size_t h64 = (size_t)q.vh * 192, hs = half_field_bytes(q.vh, q.prec);
+    q.r = take(h64); q.ax = take(h64); q.t_o = take(h64); q.t_e = take(h64);
+    q.rs = take(hs); q.ps = take(hs); q.aps = take(hs); q.tso = take(hs); q.tse = take(hs);
+    q.xs = take((size_t)q.vh * 96);
+    q.scal = (double *)take(256);
+    q.red.ticket = (unsigned *)take(256);
+    q.red.partials = (double *)take((size_t)MAX_RED_BLOCKS * MAX_NR * 8);
+    WD_GS_DISPATCH(q.prec, gs_detail::init<PS>(ctx, q));
+}
+
+// After gs_setup's work has finished: reads |b|^2 and prepares the test.
+inline void gs_start(GSolve &q)
+{
+    q.b2 = q.h[0];
+    q.stop2 = q.tol * q.tol * q.b2;
+    q.maxr = std::sqrt(q.b2);
+    if (!(q.b2 > 0.0)) {
+        q.active = false;
+        q.rel = 0.0;
+        if (!std::isfinite(q.b2)) q.status = WD_EINVAL;   // poisoned source
+    }
+}
+
+// Enqueues one replay (GS_ITERS iterations) and the scalar read-back.
+inline int gs_launch(GSolve &q)
+{
+    WD_CUDA_TRY(cudaGraphLaunch(q.exec, q.s));
+    WD_CUDA_TRY(cudaMemcpyAsync(q.h, q.scal, 7 * sizeof(double), cudaMemcpyDeviceToHost, q.s));
+    return WD_OK;
+}
+
+// After a replay has finished: residual test, reliable update, convergence.
+inline int gs_after(const wd_ctx *ctx, GSolve &q)
+{
+    q.iters += GS_ITERS;
+    const double r2 = q.h[0];
+    const bool broke = q.h[6] != 0.0 || !std::isfinite(r2);
+    const double rn = std::sqrt(r2);
+    if (rn > q.maxr) q.maxr = rn;
+    if (!(broke || rn < q.opts.delta * q.maxr || r2 <= q.stop2 || q.iters >= q.opts.maxiter)) return WD_OK;
+    int rc;
+    switch (q.prec) {
+    case WD_F16: rc = gs_detail::reliable_update<PREC_F16>(ctx, q); break;
+    case WD_BF16: rc = gs_detail::reliable_update<PREC_BF16>(ctx, q); break;
+    default: rc = gs_detail::reliable_update<PREC_F32>(ctx, q); break;
+    }
+    if (rc) return rc;
+    WD_CUDA_TRY(cudaStreamSynchronize(q.s));
+    const double r2t = q.h[7];
+    q.updates++;
+    q.rel = std::sqrt(r2t / q.b2);
+    if (r2t <= q.stop2) {
+        q.active = false;
+        return WD_OK;
+    }
+    if (q.iters >= q.opts.maxiter || !std::isfinite(r2t)) {
+        q.active = false;
+        q.status = WD_ENOCONV;
+        return WD_OK;
+    }
+    // continue from the true residual; restart the direction after a breakdown
+    double sc[8] = {r2t, 0, 0, 0, r2t, 0, 0, 0};
+    WD_CUDA_TRY(cudaMemcpyAsync(q.scal, sc, sizeof(sc), cudaMemcpyHostToDevice, q.s));
+    if (broke) WD_CUDA_TRY(cudaMemcpyAsync(q.ps, q.rs, half_field_bytes(q.vh, q.prec), cudaMemcpyDeviceToDevice, q.s));
+    WD_CUDA_TRY(cudaStreamSynchronize(q.s));
+    q.maxr = std::sqrt(r2t);
+    return WD_OK;
+}
+
+inline void gs_release(GSolve &q)
+{
+    if (q.s) cudaStreamSynchronize(q.s);
+    if (q.exec) cudaGraphExecDestroy(q.exec);
+    if (q.s) cudaStreamDestroy(q.s);
+    if (q.mem) cudaFree(q.mem);
+    if (q.h) cudaFreeHost(q.h);
+    q.exec = nullptr;
+    q.s = nullptr;
+    q.mem = nullptr;
+    q.h = nullptr;
+}
+
+} // namespace wd

@@ -1,0 +1,349 @@
+// Solve-request queue with continuous batching.
+//
+// Requests (cg_solve problems on resident gauge fields) are submitted from any
+// host thread and run by one scheduler thread.  Each scheduler step admits
+// waiting requests while free slots and the HBM budget allow (first come
+// first served, but a request that fits may pass one that does not), sets up
+// the admitted ones (workspace, stream, captured CUDA graph), replays the
+// graph of every running request on its own stream (so their work overlaps on
+// the GPU), then does each request's residual test and FP64 reliable update,
+// retires the finished ones and frees their memory.  Requests therefore join
+// and leave the running batch between steps.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gsolve.cuh"
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct Req {
+    uint64_t ticket = 0;
+    wd_solve_desc d{};
+    size_t foot = 0;
+    bool cancel = false, done = false;
+    wd_solve_result res{};
+    wd::GSolve gs;
+};
+
+} // namespace
+
+struct rq_queue {
+    wd_ctx *ctx = nullptr;
+    size_t budget = 0;
+    int max_slots = 1;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread th;
+    bool stop = false;
+    uint64_t next_ticket = 0;
+    std::deque<Req *> waiting;
+    std::vector<Req *> running;
+    std::unordered_map<uint64_t, Req *> all;
+    size_t in_use = 0;
+    clk::time_point t0;
+    // counters
+    uint64_t submitted = 0, completed = 0, stalls = 0, steps = 0, admitted = 0;
+    double occupancy_sum = 0.0;
+    int fault_alloc_at = 0;   // WD_FAULT=alloc:N -> the N-th admission fails
+};
+
+namespace wd {
+namespace {
+
+double now_s(const rq_queue *q) { return std::chrono::duration<double>(clk::now() - q->t0).count(); }
+
+void finish(rq_queue *q, Req *r, int status)
+{
+    std::lock_guard<std::mutex> lk(q->mu);
+    r->res.status = status;
+    r->res.stats.status = status;
+    r->res.stats.iters = r->gs.iters;
+    r->res.stats.reliable_updates = r->gs.updates;
+    r->res.stats.true_rel_resid = r->gs.rel;
+    r->res.t_finish = now_s(q);
+    if (r->res.t_start == 0.0) r->res.t_start = r->res.t_finish;
+    r->res.stats.seconds = r->res.t_finish - r->res.t_submit;
+    r->done = true;
+    q->in_use -= r->foot;
+    q->completed++;
+    q->cv_done.notify_all();
+}
+
+void scheduler(rq_queue *q)
+{
+    cudaSetDevice(q->ctx->device);
+    for (;;) {
+        std::vector<Req *> admit;
+        {
+            std::unique_lock<std::mutex> lk(q->mu);
+            q->cv_work.wait(lk, [q] { return q->stop || !q->waiting.empty() || !q->running.empty(); });
+            if (q->stop && q->waiting.empty() && q->running.empty()) break;
+            bool stalled = false;
+            for (auto it = q->waiting.begin(); it != q->waiting.end();) {
+                Req *r = *it;
+                if ((int)(q->running.size() + admit.size()) >= q->max_slots) break;
+                if (q->in_use + r->foot <= q->budget) {
+                    q->in_use += r->foot;
+                    admit.push_back(r);
+                    it = q->waiting.erase(it);
+                } else {
+                    stalled = true;
+                    ++it;
+                }
+            }
+            if (stalled) q->stalls++;
+        }
+        // set up the admitted requests outside the lock
+        for (Req *r : admit) {
+            r->res.t_admit = now_s(q);
+            q->admitted++;
+            const bool inject = q->fault_alloc_at > 0 && (int)q->admitted == q->fault_alloc_at;
+            int rc = gs_setup(q->ctx, r->gs, inject);
+            if (rc == WD_OK && cudaStreamSynchronize(r->gs.s) != cudaSuccess) rc = set_error(WD_ECUDA, "set-up failed");
+            if (rc != WD_OK) {
+                gs_release(r->gs);
+                finish(q, r, rc);
+                continue;
+            }
+            gs_start(r->gs);
+            r->res.t_start = now_s(q);
+            if (!r->gs.active) {
+                gs_release(r->gs);
+                finish(q, r, r->gs.status);
+                continue;
+            }
+            std::lock_guard<std::mutex> lk(q->mu);
+            q->running.push_back(r);
+        }
+        if (q->running.empty()) continue;
+        // one step of every running request
+        {
+            std::lock_guard<std::mutex> lk(q->mu);
+            q->steps++;
+            q->occupancy_sum += (double)q->running.size();
+        }
+        for (Req *r : q->running) {
+            bool cancel;
+            {
+                std::lock_guard<std::mutex> lk(q->mu);
+                cancel = r->cancel;
+            }
+            if (!cancel && gs_launch(r->gs) != WD_OK) r->gs.status = WD_ECUDA;
+        }
+        std::vector<Req *> keep;
+        for (Req *r : q->running) {
+            bool cancel;
+            {
+                std::lock_guard<std::mutex> lk(q->mu);
+                cancel = r->cancel;
+            }
+            int rc = WD_OK;
+            if (cudaStreamSynchronize(r->gs.s) != cudaSuccess) rc = WD_ECUDA;
+            else if (cancel) rc = WD_ECANCELLED;
+            else if (r->gs.status == WD_OK) rc = gs_after(q->ctx, r->gs);
+            if (rc == WD_OK && r->gs.active && r->gs.status == WD_OK) {
+                keep.push_back(r);
+                continue;
+            }
+            gs_release(r->gs);
+            finish(q, r, rc != WD_OK ? rc : r->gs.status);
+        }
+        std::lock_guard<std::mutex> lk(q->mu);
+        q->running.swap(keep);
+    }
+}
+
+int check_request(const wd_solve_desc *d)
+{
+    if (!d || !d->gauge || !d->x_e || !d->b_e) return set_error(WD_EINVAL, "NULL gauge or field in the request");
+    if (((uintptr_t)d->x_e & 15u) || ((uintptr_t)d->b_e & 15u)) return set_error(WD_EINVAL, "misaligned field");
+    if (!(d->tol > 0.0)) return set_error(WD_EINVAL, "tol must be > 0");
+    if (d->opts.maxiter < 1) return set_error(WD_EINVAL, "maxiter must be >= 1");
+    if (d->opts.inner_prec != WD_F32 && d->opts.inner_prec != WD_F16 && d->opts.inner_prec != WD_BF16)
+        return set_error(WD_EINVAL, "queued solves use mixed precision: inner_prec must be F32, F16 or BF16");
+    if (!valid_recon(d->opts.inner_recon) || !valid_recon(d->opts.outer_recon))
+        return set_error(WD_EINVAL, "bad link reconstruction");
+    if (!(d->opts.delta > 0.0 && d->opts.delta < 1.0)) return set_error(WD_EINVAL, "delta must be in (0, 1)");
+    return WD_OK;
+}
+
+} // namespace
+} // namespace wd
+
+using namespace wd;
+
+extern "C" {
+
+int rq_create(wd_ctx *ctx, size_t hbm_budget_bytes, int max_slots, rq_queue **out)
+{
+    clear_error();
+    if (!ctx || !out || max_slots < 1 || hbm_budget_bytes == 0) return set_error(WD_EINVAL, "bad arguments");
+    rq_queue *q = new (std::nothrow) rq_queue();
+    if (!q) return set_error(WD_ENOMEM, "host allocation failed");
+    q->ctx = ctx;
+    q->budget = hbm_budget_bytes;
+    q->max_slots = max_slots;
+    q->t0 = clk::now();
+    if (const char *f = std::getenv("WD_FAULT"))
+        if (const char *a = std::strstr(f, "alloc:")) q->fault_alloc_at = std::atoi(a + 6);
+    try {
+        q->th = std::thread(scheduler, q);
+    } catch (...) {
+        delete q;
+        return set_error(WD_ENOMEM, "could not start the scheduler thread");
+    }
+    *out = q;
+    return WD_OK;
+}
+
+int rq_submit(rq_queue *q, const wd_solve_desc *d, uint64_t *ticket)
+{
+    clear_error();
+    if (!q || !ticket) return set_error(WD_EINVAL, "NULL argument");
+    WD_TRY(check_request(d));
+    const wd_gauge *g = d->gauge;
+    // layouts are built here, on the caller's thread, so that the scheduler never allocates them
+    WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), WD_F64, d->opts.outer_recon));
+    WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), d->opts.inner_prec, d->opts.inner_recon));
+    Req *r = new (std::nothrow) Req();
+    if (!r) return set_error(WD_ENOMEM, "host allocation failed");
+    r->d = *d;
+    r->foot = gs_footprint(g->geo.Vh, d->opts.inner_prec);
+    if (r->foot > q->budget) {
+        delete r;
+        return set_error(WD_ENOMEM, "request needs %zu bytes, more than the queue's HBM budget", gs_footprint(g->geo.Vh, d->opts.inner_prec));
+    }
+    r->gs.gauge = g;
+    r->gs.mass = d->mass;
+    r->gs.tol = d->tol;
+    r->gs.x = d->x_e;
+    r->gs.b = d->b_e;
+    r->gs.opts = d->opts;
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        if (q->stop) {
+            delete r;
+            return set_error(WD_EINVAL, "queue is shutting down");
+        }
+        r->ticket = ++q->next_ticket;
+        r->res.t_submit = now_s(q);
+        q->all[r->ticket] = r;
+        q->waiting.push_back(r);
+        q->submitted++;
+        *ticket = r->ticket;
+    }
+    q->cv_work.notify_one();
+    return WD_OK;
+}
+
+static int take_result(rq_queue *q, std::unordered_map<uint64_t, Req *>::iterator it, wd_solve_result *out)
+{
+    Req *r = it->second;
+    if (out) *out = r->res;
+    q->all.erase(it);
+    delete r;
+    return WD_OK;
+}
+
+int rq_poll(rq_queue *q, uint64_t ticket, wd_solve_result *out)
+{
+    clear_error();
+    if (!q) return set_error(WD_EINVAL, "NULL queue");
+    std::lock_guard<std::mutex> lk(q->mu);
+    auto it = q->all.find(ticket);
+    if (it == q->all.end()) return set_error(WD_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    if (!it->second->done) return WD_EBUSY;
+    return take_result(q, it, out);
+}
+
+int rq_wait(rq_queue *q, uint64_t ticket, int timeout_ms, wd_solve_result *out)
+{
+    clear_error();
+    if (!q) return set_error(WD_EINVAL, "NULL queue");
+    std::unique_lock<std::mutex> lk(q->mu);
+    auto it = q->all.find(ticket);
+    if (it == q->all.end()) return set_error(WD_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    Req *r = it->second;
+    auto ready = [r] { return r->done; };
+    if (timeout_ms < 0) q->cv_done.wait(lk, ready);
+    else if (!q->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+        return set_error(WD_ETIMEOUT, "request %llu not finished within %d ms", (unsigned long long)ticket, timeout_ms);
+    return take_result(q, q->all.find(ticket), out);
+}
+
+int rq_cancel(rq_queue *q, uint64_t ticket)
+{
+    clear_error();
+    if (!q) return set_error(WD_EINVAL, "NULL queue");
+    std::lock_guard<std::mutex> lk(q->mu);
+    auto it = q->all.find(ticket);
+    if (it == q->all.end()) return set_error(WD_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    Req *r = it->second;
+    if (r->done) return WD_OK;
+    auto w = std::find(q->waiting.begin(), q->waiting.end(), r);
+    if (w != q->waiting.end()) {
+        q->waiting.erase(w);
+        r->res.status = r->res.stats.status = WD_ECANCELLED;
+        r->res.t_finish = now_s(q);
+        r->done = true;
+        q->completed++;
+        q->cv_done.notify_all();
+    } else {
+        r->cancel = true;   // retired by the scheduler at the end of its current step
+    }
+    return WD_OK;
+}
+
+int rq_stats(rq_queue *q, rq_counters *out)
+{
+    clear_error();
+    if (!q || !out) return set_error(WD_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(q->mu);
+    out->submitted = q->submitted;
+    out->completed = q->completed;
+    out->admission_stalls = q->stalls;
+    out->steps = q->steps;
+    out->mean_running = q->steps ? q->occupancy_sum / (double)q->steps : 0.0;
+    out->waiting = (int)q->waiting.size();
+    out->running = (int)q->running.size();
+    out->hbm_in_use = q->in_use;
+    return WD_OK;
+}
+
+int wd_solve_workspace_bytes(const int dims[4], int inner_prec, size_t *out)
+{
+    clear_error();
+    Geometry g;
+    WD_TRY(make_geometry(dims, g));
+    if (!valid_prec(inner_prec) || inner_prec == WD_F64) return set_error(WD_EINVAL, "inner precision must be F32, F16 or BF16");
+    if (!out) return set_error(WD_EINVAL, "out is NULL");
+    *out = gs_footprint(g.Vh, inner_prec);
+    return WD_OK;
+}
+
+int rq_destroy(rq_queue *q)
+{
+    clear_error();
+    if (!q) return WD_OK;
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        q->stop = true;
+    }
+    q->cv_work.notify_all();
+    if (q->th.joinable()) q->th.join();
+    for (auto &kv : q->all) delete kv.second;
+    delete q;
+    return WD_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,158 @@
+"""Request queue with continuous batching: correctness in the mix, admission, cancellation, faults.
+
+Faults are made on the host (an injected allocation failure, a source that is
+not finite, a wait that times out on the host); nothing here faults the GPU.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1901_07294_gb300 as wd
+import synth
+from tests._gpu import pack_field, unpack_field
+from tests._lattice import rel_max_err, volume
+
+pytestmark = pytest.mark.gpu
+
+LATTICES = [(4, 4, 4, 4), (8, 8, 8, 8), (4, 6, 8, 10), (8, 8, 8, 16)]
+_gauges = {}
+
+
+def _gauge(ctx, dims):
+    key = (id(ctx), dims)
+    if key not in _gauges:
+        U = synth.gauge(dims, seed=1000 + volume(dims) % 983)
+        _gauges[key] = (U, wd.Gauge(ctx, dims, U))
+    return _gauges[key]
+
+
+def _request(ctx, k, dims=None, tol=None, prec=wd.F16, seed=5001):
+    rng = np.random.default_rng(seed + k)
+    dims = dims or LATTICES[k % len(LATTICES)]
+    U, g = _gauge(ctx, dims)
+    mass = float(np.exp(rng.uniform(np.log(0.02), np.log(0.5))))
+    tol = tol or float([1e-8, 1e-10, 1e-12][k % 3])
+    b = synth.even_spinor(dims, seed=3300 + k)
+    p = dict(gauge=g, mass=mass, tol=tol, inner_prec=prec, delta=0.1,
+             b=pack_field(ctx, dims, wd.SITES_EVEN, wd.F64, b), x=wd.alloc_field(dims, wd.SITES_EVEN, wd.F64))
+    return p, (dims, U, mass, b)
+
+
+def _true_rel(ctx, host, x_field):
+    dims, U, mass, b = host
+    x = unpack_field(ctx, dims, wd.SITES_EVEN, wd.F64, x_field)
+    return float(np.linalg.norm(b - oracle.mdagm(dims, U, mass, x)) / np.linalg.norm(b)), x
+
+
+def test_queue_results_and_same_alone_as_in_mix():
+    ctx = wd.Context(0)
+    q = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=6)
+    reqs = [_request(ctx, k) for k in range(12)]
+    tickets = [q.submit(p) for p, _ in reqs]
+    res = [q.wait(t, timeout_ms=120000) for t in tickets]
+    mixed_x = []
+    for (p, host), r in zip(reqs, res):
+        assert r["status"] == 0, r
+        rel, x = _true_rel(ctx, host, p["x"])
+        assert rel <= 1.05 * p["tol"], (rel, p["tol"])
+        assert r["t_submit"] <= r["t_admit"] <= r["t_start"] <= r["t_finish"]
+        mixed_x.append(x)
+    st = q.stats()
+    assert st["completed"] == 12 and st["mean_running"] > 1.0
+    q.close()
+    # each request alone in a fresh queue gives the same solution
+    for k in (0, 5, 9):
+        p, host = reqs[k]
+        alone = dict(p)
+        alone["x"] = wd.alloc_field(host[0], wd.SITES_EVEN, wd.F64)
+        q1 = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=1)
+        r = q1.wait(q1.submit(alone), timeout_ms=60000)
+        q1.close()
+        assert r["status"] == 0
+        _, xa = _true_rel(ctx, host, alone["x"])
+        assert rel_max_err(mixed_x[k], xa) < max(1e-7, 1e3 * p["tol"])
+
+
+def test_requests_join_while_others_run():
+    """Continuous batching: a request submitted while another runs is admitted before it ends."""
+    ctx = wd.Context(0)
+    q = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=4)
+    big, _ = _request(ctx, 0, dims=(8, 8, 8, 16), tol=1e-12)
+    big["mass"] = 0.02
+    t_big = q.submit(big)
+    import time
+    t_end = time.time() + 30
+    while time.time() < t_end:
+        st = q.stats()
+        if st["running"] > 0 or st["completed"] > 0:
+            break
+        time.sleep(0.0005)
+    small = [_request(ctx, k, dims=(4, 4, 4, 4), tol=1e-8)[0] for k in range(1, 4)]
+    ts = [q.submit(p) for p in small]
+    rb = q.wait(t_big, timeout_ms=60000)
+    rs = [q.wait(t, timeout_ms=60000) for t in ts]
+    assert rb["status"] == 0 and all(r["status"] == 0 for r in rs)
+    assert any(r["t_admit"] < rb["t_finish"] for r in rs)
+    q.close()
+
+
+def test_admission_respects_hbm_budget():
+    ctx = wd.Context(0)
+    reqs = [_request(ctx, k, dims=(8, 8, 8, 8), tol=1e-10) for k in range(4)]
+    # a budget of 1.5 request workspaces admits one request at a time
+    one = wd.solve_workspace_bytes((8, 8, 8, 8), wd.F16)
+    q = wd.Queue(ctx, hbm_budget_bytes=int(one * 1.5), max_slots=8)
+    ts = [q.submit(p) for p, _ in reqs]
+    res = [q.wait(t, timeout_ms=60000) for t in ts]
+    st = q.stats()
+    q.close()
+    assert all(r["status"] == 0 for r in res)
+    assert st["mean_running"] <= 1.0 + 1e-9
+    assert st["admission_stalls"] > 0
+
+
+def test_request_larger_than_budget_is_refused():
+    ctx = wd.Context(0)
+    q = wd.Queue(ctx, hbm_budget_bytes=1 << 20, max_slots=2)
+    p, _ = _request(ctx, 0, dims=(8, 8, 8, 8))
+    with pytest.raises(wd.WdError) as e:
+        q.submit(p)
+    assert e.value.status == wd.WD_ENOMEM
+    q.close()
+
+
+def test_cancel_wait_timeout_and_poisoned_request():
+    ctx = wd.Context(0)
+    q = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=1)
+    first, _ = _request(ctx, 0, dims=(8, 8, 8, 16), tol=1e-12)
+    first["mass"] = 0.02
+    t0 = q.submit(first)
+    later = [q.submit(_request(ctx, k, dims=(4, 4, 4, 4))[0]) for k in range(1, 4)]
+    q.cancel(later[1])                                     # still waiting: cancelled at once
+    with pytest.raises(wd.WdError) as e:
+        q.wait(t0, timeout_ms=0)                           # host-side wait gives up; the request goes on
+    assert e.value.status == wd.WD_ETIMEOUT
+    poisoned, _ = _request(ctx, 7, dims=(4, 4, 4, 4))
+    nan = np.full((volume((4, 4, 4, 4)), 4, 3), np.nan, np.complex128)
+    poisoned["b"] = pack_field(ctx, (4, 4, 4, 4), wd.SITES_EVEN, wd.F64, nan)
+    tp = q.submit(poisoned)
+    assert q.wait(t0, timeout_ms=60000)["status"] == 0
+    assert q.wait(later[1], timeout_ms=60000)["status"] == wd.WD_ECANCELLED
+    assert q.wait(later[0], timeout_ms=60000)["status"] == 0
+    assert q.wait(later[2], timeout_ms=60000)["status"] == 0
+    assert q.wait(tp, timeout_ms=60000)["status"] == wd.WD_EINVAL
+    q.close()
+
+
+def test_injected_allocation_failure(monkeypatch):
+    ctx = wd.Context(0)
+    monkeypatch.setenv("WD_FAULT", "alloc:2")
+    q = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=1)
+    reqs = [_request(ctx, k, dims=(4, 4, 4, 4), tol=1e-10) for k in range(4)]
+    ts = [q.submit(p) for p, _ in reqs]
+    res = [q.wait(t, timeout_ms=60000) for t in ts]
+    q.close()
+    assert [r["status"] for r in res] == [0, wd.WD_ENOMEM, 0, 0]
+    assert _true_rel(ctx, reqs[2][1], reqs[2][0]["x"])[0] <= 1.05e-10
