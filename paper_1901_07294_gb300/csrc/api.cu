@@ -5,6 +5,7 @@
 #include <new>
 
 #include "blas.cuh"
+#include "launch.cuh"
 #include "wd_device.cuh"
 #include "wd_internal.h"
 
@@ -178,12 +179,40 @@ static int sites_to_map(const Geometry &g, int sites, int prec, SiteMap &m)
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+GraphSink *&graph_sink()
+{
+    static thread_local GraphSink *sink = nullptr;
+    return sink;
+}
+
+// Copies and clears on a private stream, so that set-up calls never
+// synchronise the whole device.
+static cudaError_t copy_private(void *dst, const void *src, size_t n, cudaMemcpyKind kind)
+{
+    cudaStream_t s;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(dst, src, n, kind, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    return e;
+}
+
+static bool zero_device(void *p, size_t n)
+{
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return false;
+    cudaError_t e = cudaMemsetAsync(p, 0, n, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    return e == cudaSuccess;
+}
+
 int ctx_workspace(wd_ctx *ctx, size_t bytes, char **out)
 {
     if (ctx->work_bytes < bytes) {
         DeviceGuard dg(ctx->device);
-        if (ctx->d_work) {
-            cudaDeviceSynchronize();
+        if (ctx->d_work) {   // solves using it are synchronous, so it is idle here
             cudaFree(ctx->d_work);
             ctx->d_work = nullptr;
             ctx->work_bytes = 0;
@@ -222,7 +251,14 @@ int gauge_layout(const wd_gauge *gc, int prec, int recon, const char **out)
     sites_to_map(g->geo, WD_SITES_FULL, prec, m);
     const int threads = 256;
     const int blocks = (int)((2 * (int64_t)g->geo.Vh + threads - 1) / threads);
-#define WD_PACK_LINKS(P, R) pack_links_kernel<P, R><<<blocks, threads>>>(g->canonical, buf, m, blk)
+    // a private stream: no device-wide synchronisation, which would disturb
+    // other threads (for example one building a graph)
+    cudaStream_t ps = nullptr;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(buf);
+        return set_error(WD_ECUDA, "stream creation failed");
+    }
+#define WD_PACK_LINKS(P, R) pack_links_kernel<P, R><<<blocks, threads, 0, ps>>>(g->canonical, buf, m, blk)
     switch (prec * 100 + recon) {
     case WD_F64 * 100 + 18: WD_PACK_LINKS(PREC_F64, 18); break;
     case WD_F64 * 100 + 12: WD_PACK_LINKS(PREC_F64, 12); break;
@@ -233,7 +269,8 @@ int gauge_layout(const wd_gauge *gc, int prec, int recon, const char **out)
     }
 #undef WD_PACK_LINKS
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+    cudaStreamDestroy(ps);
     if (e != cudaSuccess) {
         cudaFree(buf);
         return set_error(WD_ECUDA, "link packing failed: %s", cudaGetErrorString(e));
@@ -279,8 +316,7 @@ int wd_ctx_create(int device, wd_ctx **out)
         if (cudaMalloc(&c->d_partials, pbytes) != cudaSuccess || cudaMalloc(&c->d_ticket, 256) != cudaSuccess ||
             cudaMalloc(&c->d_scal, NSCAL * sizeof(double)) != cudaSuccess ||
             cudaMallocHost(&c->h_scal, NSCAL * sizeof(double)) != cudaSuccess ||
-            cudaMemset(c->d_ticket, 0, 256) != cudaSuccess || cudaMemset(c->d_scal, 0, NSCAL * sizeof(double)) != cudaSuccess ||
-            cudaDeviceSynchronize() != cudaSuccess) {
+            !zero_device(c->d_ticket, 256) || !zero_device(c->d_scal, NSCAL * sizeof(double))) {
             cudaGetLastError();
             wd_ctx_destroy(c);
             return set_error(WD_ENOMEM, "allocating the context scratch failed");
@@ -397,7 +433,7 @@ int wd_gauge_create(wd_ctx *ctx, const int dims[4], const double *links, int lin
         delete g;
         return set_error(WD_ENOMEM, "cudaMalloc of %zu bytes for the gauge field failed", nb);
     }
-    cudaError_t e = cudaMemcpy(g->canonical, links, nb, links_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice);
+    cudaError_t e = copy_private(g->canonical, links, nb, links_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice);
     if (e != cudaSuccess) {
         cudaFree(g->canonical);
         delete g;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "blas.cuh"
+#include "launch.cuh"
 #include "wd_internal.h"
 
 namespace wd {
@@ -22,8 +23,7 @@ inline int blas_grid(const wd_ctx *ctx, int nsite)
 template <typename Op> int run_blas(const wd_ctx *ctx, const Op &op, int nsite, cudaStream_t s)
 {
     RedScratch rs{ctx->d_partials, ctx->d_ticket};
-    blas_kernel<Op><<<blas_grid(ctx, nsite), BLAS_THREADS, 0, s>>>(op, nsite, rs);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = wd_launch(blas_kernel<Op>, dim3(blas_grid(ctx, nsite)), dim3(BLAS_THREADS), 0, s, op, nsite, rs);
     if (e != cudaSuccess) return set_error(WD_ECUDA, "BLAS kernel launch failed: %s", cudaGetErrorString(e));
     return WD_OK;
 }

@@ -12,6 +12,7 @@
 // components from the upper ones.  1320 flops per output site.
 #pragma once
 
+#include "launch.cuh"
 #include "wd_device.cuh"
 
 namespace wd {
@@ -379,9 +380,9 @@ template <int P, int RECON, bool DAG, bool HX>
 void launch_hop_pf(const HopArgs &A, dim3 grid, int threads, int pf, cudaStream_t s)
 {
     switch (pf) {
-    case 0: hop_kernel<P, RECON, DAG, HX, 0><<<grid, threads, 0, s>>>(A); break;
-    case 1: hop_kernel<P, RECON, DAG, HX, 1><<<grid, threads, 0, s>>>(A); break;
-    default: hop_kernel<P, RECON, DAG, HX, 2><<<grid, threads, 0, s>>>(A); break;
+    case 0: wd_launch(hop_kernel<P, RECON, DAG, HX, 0>, grid, dim3(threads), 0, s, A); break;
+    case 1: wd_launch(hop_kernel<P, RECON, DAG, HX, 1>, grid, dim3(threads), 0, s, A); break;
+    default: wd_launch(hop_kernel<P, RECON, DAG, HX, 2>, grid, dim3(threads), 0, s, A); break;
     }
 }
 
@@ -390,7 +391,7 @@ void launch_hop_mrhs(const HopArgs &A, int nrhs, int threads, cudaStream_t s)
 {
     const int ry = threads / 32;
     const int per = (A.vh + 31) / 32;
-    hop_mrhs_kernel<P, RECON, DAG, HX><<<dim3((unsigned)(per * A.nparity)), dim3(32, ry), 0, s>>>(A, nrhs);
+    wd_launch(hop_mrhs_kernel<P, RECON, DAG, HX>, dim3((unsigned)(per * A.nparity)), dim3(32, ry), 0, s, A, nrhs);
 }
 
 // Launches the hop kernel of precision P for the runtime (recon, dagger,

@@ -62,8 +62,7 @@ inline int mdagm(const wd_gauge *g, int prec, int recon, double mass, const char
 
 template <typename Op> inline int launch(const wd_ctx *ctx, const Op &op, int nsite, RedScratch rs, cudaStream_t s)
 {
-    blas_kernel<Op><<<blas_grid(ctx, nsite), BLAS_THREADS, 0, s>>>(op, nsite, rs);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = wd_launch(blas_kernel<Op>, dim3(blas_grid(ctx, nsite)), dim3(BLAS_THREADS), 0, s, op, nsite, rs);
     return e == cudaSuccess ? WD_OK : set_error(WD_ECUDA, "BLAS launch failed: %s", cudaGetErrorString(e));
 }
 
@@ -109,15 +108,22 @@ template <int PS> int init(const wd_ctx *ctx, GSolve &q)
     WD_TRY(launch(ctx, OpConvert<PS, PREC_F64>{FS(q.rs), F64(q.r)}, vh, q.red, q.s));
     WD_CUDA_TRY(cudaMemcpyAsync(q.ps, q.rs, half_field_bytes(vh, PS), cudaMemcpyDeviceToDevice, q.s));
     WD_CUDA_TRY(cudaMemcpyAsync(q.h, q.scal, sizeof(double), cudaMemcpyDeviceToHost, q.s));
-    // capture GS_ITERS iterations
+    // build a graph of GS_ITERS iterations node by node (no stream capture)
     cudaGraph_t graph;
-    WD_CUDA_TRY(cudaStreamBeginCapture(q.s, cudaStreamCaptureModeThreadLocal));
+    WD_CUDA_TRY(cudaGraphCreate(&graph, 0));
+    GraphSink sink;
+    sink.graph = graph;
+    graph_sink() = &sink;
     int rc = WD_OK;
     for (int it = 0; it < GS_ITERS && rc == WD_OK; ++it) rc = iteration<PS>(ctx, q);
-    cudaError_t ce = cudaStreamEndCapture(q.s, &graph);
-    if (rc != WD_OK) return rc;
-    if (ce != cudaSuccess) return set_error(WD_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
-    ce = cudaGraphInstantiate(&q.exec, graph, 0);
+    graph_sink() = nullptr;
+    if (rc == WD_OK && sink.err != cudaSuccess)
+        rc = set_error(WD_ECUDA, "building the solve graph failed: %s", cudaGetErrorString(sink.err));
+    if (rc != WD_OK) {
+        cudaGraphDestroy(graph);
+        return rc;
+    }
+    cudaError_t ce = cudaGraphInstantiate(&q.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return set_error(WD_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
     return WD_OK;

@@ -1,0 +1,63 @@
+// Kernel launches that can be redirected into a CUDA graph under construction.
+//
+// Every kernel launch of the library goes through wd_launch.  Normally it
+// launches on the given stream.  While the calling thread has a GraphSink
+// installed (graph_sink() != nullptr), the launch is instead appended to the
+// sink's graph as a kernel node depending on the previous one.  Graphs are
+// thus built explicitly, without stream capture, so that building one never
+// interferes with other threads' work (stream capture forbids, for example, a
+// device-wide synchronisation by any thread while it is in progress).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <tuple>
+#include <type_traits>
+#include <utility>
+
+namespace wd {
+
+struct GraphSink {
+    cudaGraph_t graph = nullptr;
+    cudaGraphNode_t last = nullptr;
+    cudaError_t err = cudaSuccess;
+};
+
+// The calling thread's sink (nullptr: launch normally).  Defined in api.cu.
+GraphSink *&graph_sink();
+
+namespace launch_detail {
+template <typename Tuple, size_t... I>
+void fill(Tuple &t, void **params, std::index_sequence<I...>)
+{
+    ((params[I] = (void *)&std::get<I>(t)), ...);
+}
+} // namespace launch_detail
+
+template <typename... KArgs, typename... Args>
+cudaError_t wd_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args)
+{
+    GraphSink *g = graph_sink();
+    if (!g) {
+        kernel<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+        return cudaGetLastError();
+    }
+    std::tuple<std::decay_t<KArgs>...> vals(std::forward<Args>(args)...);
+    void *params[sizeof...(KArgs) > 0 ? sizeof...(KArgs) : 1];
+    launch_detail::fill(vals, params, std::index_sequence_for<KArgs...>{});
+    cudaKernelNodeParams p{};
+    p.func = (void *)kernel;
+    p.gridDim = grid;
+    p.blockDim = block;
+    p.sharedMemBytes = (unsigned)smem;
+    p.kernelParams = params;
+    p.extra = nullptr;
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphAddKernelNode(&node, g->graph, g->last ? &g->last : nullptr, g->last ? 1 : 0, &p);
+    if (e == cudaSuccess) g->last = node;
+    else if (g->err == cudaSuccess) g->err = e;
+    return e;
+}
+
+} // namespace wd

@@ -76,8 +76,10 @@ int wd_tune_dslash(wd_ctx *ctx, const wd_gauge *g, int prec, int recon, int full
         cudaFree(out);
         return set_error(WD_ENOMEM, "cudaMalloc of tuning fields failed");
     }
-    cudaMemset(in, 0, field);
-    if (x) cudaMemset(x, 0, field);
+    cudaStream_t s;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaMemsetAsync(in, 0, field, s);
+    if (x) cudaMemsetAsync(x, 0, field, s);
     if (full) {
         for (int p = 0; p < 2; ++p) {
             A.in[p] = in + (size_t)(1 - p) * half;
@@ -99,9 +101,7 @@ int wd_tune_dslash(wd_ctx *ctx, const wd_gauge *g, int prec, int recon, int full
         A.b = 1.0;
     }
     const std::string key = hop_key(ctx, A, prec, recon, nrhs);
-    cudaStream_t s;
     cudaEvent_t e0, e1;
-    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int cand_threads[] = {64, 128, 192, 256};

@@ -18,10 +18,18 @@ pytestmark = pytest.mark.gpu
 
 LATTICES = [(4, 4, 4, 4), (8, 8, 8, 8), (4, 6, 8, 10), (8, 8, 8, 16)]
 _gauges = {}
+_context = []
+
+
+def _ctx():
+    """One context for the module: the cached gauges below use its tuning cache."""
+    if not _context:
+        _context.append(wd.Context(0))
+    return _context[0]
 
 
 def _gauge(ctx, dims):
-    key = (id(ctx), dims)
+    key = dims
     if key not in _gauges:
         U = synth.gauge(dims, seed=1000 + volume(dims) % 983)
         _gauges[key] = (U, wd.Gauge(ctx, dims, U))
@@ -47,7 +55,7 @@ def _true_rel(ctx, host, x_field):
 
 
 def test_queue_results_and_same_alone_as_in_mix():
-    ctx = wd.Context(0)
+    ctx = _ctx()
     q = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=6)
     reqs = [_request(ctx, k) for k in range(12)]
     tickets = [q.submit(p) for p, _ in reqs]
@@ -77,9 +85,10 @@ def test_queue_results_and_same_alone_as_in_mix():
 
 def test_requests_join_while_others_run():
     """Continuous batching: a request submitted while another runs is admitted before it ends."""
-    ctx = wd.Context(0)
+    ctx = _ctx()
     q = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=4)
-    big, _ = _request(ctx, 0, dims=(8, 8, 8, 16), tol=1e-12)
+    small = [_request(ctx, k, dims=(4, 4, 4, 4), tol=1e-8)[0] for k in range(1, 4)]
+    big, _ = _request(ctx, 0, dims=(16, 16, 16, 32), tol=1e-12)
     big["mass"] = 0.02
     t_big = q.submit(big)
     import time
@@ -89,7 +98,6 @@ def test_requests_join_while_others_run():
         if st["running"] > 0 or st["completed"] > 0:
             break
         time.sleep(0.0005)
-    small = [_request(ctx, k, dims=(4, 4, 4, 4), tol=1e-8)[0] for k in range(1, 4)]
     ts = [q.submit(p) for p in small]
     rb = q.wait(t_big, timeout_ms=60000)
     rs = [q.wait(t, timeout_ms=60000) for t in ts]
@@ -99,7 +107,7 @@ def test_requests_join_while_others_run():
 
 
 def test_admission_respects_hbm_budget():
-    ctx = wd.Context(0)
+    ctx = _ctx()
     reqs = [_request(ctx, k, dims=(8, 8, 8, 8), tol=1e-10) for k in range(4)]
     # a budget of 1.5 request workspaces admits one request at a time
     one = wd.solve_workspace_bytes((8, 8, 8, 8), wd.F16)
@@ -114,7 +122,7 @@ def test_admission_respects_hbm_budget():
 
 
 def test_request_larger_than_budget_is_refused():
-    ctx = wd.Context(0)
+    ctx = _ctx()
     q = wd.Queue(ctx, hbm_budget_bytes=1 << 20, max_slots=2)
     p, _ = _request(ctx, 0, dims=(8, 8, 8, 8))
     with pytest.raises(wd.WdError) as e:
@@ -124,7 +132,7 @@ def test_request_larger_than_budget_is_refused():
 
 
 def test_cancel_wait_timeout_and_poisoned_request():
-    ctx = wd.Context(0)
+    ctx = _ctx()
     q = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=1)
     first, _ = _request(ctx, 0, dims=(8, 8, 8, 16), tol=1e-12)
     first["mass"] = 0.02
@@ -147,7 +155,7 @@ def test_cancel_wait_timeout_and_poisoned_request():
 
 
 def test_injected_allocation_failure(monkeypatch):
-    ctx = wd.Context(0)
+    ctx = _ctx()
     monkeypatch.setenv("WD_FAULT", "alloc:2")
     q = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=1)
     reqs = [_request(ctx, k, dims=(4, 4, 4, 4), tol=1e-10) for k in range(4)]
