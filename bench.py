@@ -135,6 +135,21 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_time_ms(local_ms: float, ws: int, device) -> float:
+    """Whole-job time of the timed region: the slowest rank's (max over ranks)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value_gbs(bytes_per_step: float, steps: int, ws: int, job_ms: float) -> float:
+    """Whole-job throughput: all replicas' compulsory bytes over the whole-job time."""
+    return bytes_per_step * steps * ws / (job_ms * 1e-3) / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -252,14 +267,10 @@ def run_gpu(args):
     if ws > 1:
         torch.distributed.barrier()
     launch_ms = [events[k].elapsed_time(events[k + 1]) for k in range(args.steps)]
-    total_ms = events[0].elapsed_time(events[-1])
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = job_time_ms(events[0].elapsed_time(events[-1]), ws, "cuda")
     ms_per_step = total_ms / args.steps
     bytes_step = BYTES_PER_SITE[("f32", "full", 18)] * v
-    value = bytes_step * args.steps * ws / (total_ms * 1e-3) / 1e9
+    value = job_value_gbs(bytes_step, args.steps, ws, total_ms)
     mean_launch = sum(launch_ms) / len(launch_ms)
     achieved = bytes_step / (mean_launch * 1e-3) / 1e9
     peak, peak_kind = _peaks()
