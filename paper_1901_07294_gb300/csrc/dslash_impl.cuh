@@ -98,13 +98,16 @@ __device__ __forceinline__ void su3_mul(const cpx<T> (&U)[3][3], const cpx<T> (&
     }
 }
 
+// One direction.  For 16-bit storage the neighbour's per-site scale is applied
+// to the 12 reals of U h (the operation is linear) rather than to its 24
+// stored reals.
 template <int P, int RECON, int MU, int S, bool FWD>
 __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh, int nb, int li,
                                         cpx<typename Prec<P>::real> (&acc)[4][3])
 {
     using T = typename Prec<P>::real;
     T psi[24];
-    Spinor<P>::load(in, vh, nb, psi);
+    const float sc = Spinor<P>::load_unscaled(in, vh, nb, psi);
     cpx<T> h0[3], h1[3];
     project<MU, S>(psi, h0, h1);
     cpx<T> U[3][3];
@@ -112,6 +115,13 @@ __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh
     cpx<T> w0[3], w1[3];
     su3_mul<FWD>(U, h0, w0);
     su3_mul<FWD>(U, h1, w1);
+    if constexpr (Prec<P>::scaled) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            w0[c].re *= sc; w0[c].im *= sc;
+            w1[c].re *= sc; w1[c].im *= sc;
+        }
+    }
     accumulate<MU, S>(acc, w0, w1);
 }
 
@@ -180,7 +190,7 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) LK::prefetch(gf + mu * lb, vh, i);
         Spinor<P>::prefetch(in, vh, tf);
-        if constexpr (PF >= 2) {
+        if constexpr (PF == 2) {
             LK::prefetch(gb + 0 * lb, vh, xb);
             LK::prefetch(gb + 1 * lb, vh, yb);
             LK::prefetch(gb + 2 * lb, vh, zb);
@@ -219,8 +229,11 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
     Spinor<P>::store((p ? A.out[1] : A.out[0]) + roff, vh, i, o);
 }
 
+// PF 4 is schedule 1 compiled for 3 resident blocks of 256 threads per SM
+// (at most 85 registers): more warps to hide latency, at the price of
+// registers the compiler would otherwise use to hoist loads.
 template <int P, int RECON, bool DAG, bool HAS_X, int PF>
-__global__ void __launch_bounds__(256, 2) hop_kernel(const HopArgs A)
+__global__ void __launch_bounds__(256, PF == 4 ? 3 : 2) hop_kernel(const HopArgs A)
 {
     int p, blk;
     if (A.nparity == 2) { p = blockIdx.x & 1; blk = blockIdx.x >> 1; }
@@ -373,8 +386,9 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(const HopArgs A, const in
     }
 }
 
-constexpr int HOP_VARIANTS = 3;   // values of PF
+constexpr int HOP_VARIANTS = 3;       // memory schedules 0..2 (one site per thread, linear blocks)
 constexpr int HOP_MRHS_VARIANT = 3;   // variant index of the shared-link multi-RHS kernel
+constexpr int HOP_OCC_VARIANT = 4;    // schedule 1 compiled for 3 blocks of 256 threads per SM
 
 template <int P, int RECON, bool DAG, bool HX>
 void launch_hop_pf(const HopArgs &A, dim3 grid, int threads, int pf, cudaStream_t s)
@@ -382,7 +396,8 @@ void launch_hop_pf(const HopArgs &A, dim3 grid, int threads, int pf, cudaStream_
     switch (pf) {
     case 0: wd_launch(hop_kernel<P, RECON, DAG, HX, 0>, grid, dim3(threads), 0, s, A); break;
     case 1: wd_launch(hop_kernel<P, RECON, DAG, HX, 1>, grid, dim3(threads), 0, s, A); break;
-    default: wd_launch(hop_kernel<P, RECON, DAG, HX, 2>, grid, dim3(threads), 0, s, A); break;
+    case 2: wd_launch(hop_kernel<P, RECON, DAG, HX, 2>, grid, dim3(threads), 0, s, A); break;
+    default: wd_launch(hop_kernel<P, RECON, DAG, HX, 4>, grid, dim3(threads), 0, s, A); break;
     }
 }
 
@@ -416,19 +431,20 @@ cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int th
         }
         return cudaGetLastError();
     }
+    const HopArgs &B = A;
     const int per = (A.vh + threads - 1) / threads;
-    dim3 grid((unsigned)(per * A.nparity), (unsigned)nrhs);
+    const dim3 grid((unsigned)(per * A.nparity), (unsigned)nrhs);
     const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
     const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
     switch (key) {
-    case 0: launch_hop_pf<P, 18, false, false>(A, grid, threads, pf, s); break;
-    case 1: launch_hop_pf<P, 18, false, true>(A, grid, threads, pf, s); break;
-    case 2: launch_hop_pf<P, 18, true, false>(A, grid, threads, pf, s); break;
-    case 3: launch_hop_pf<P, 18, true, true>(A, grid, threads, pf, s); break;
-    case 4: launch_hop_pf<P, 12, false, false>(A, grid, threads, pf, s); break;
-    case 5: launch_hop_pf<P, 12, false, true>(A, grid, threads, pf, s); break;
-    case 6: launch_hop_pf<P, 12, true, false>(A, grid, threads, pf, s); break;
-    case 7: launch_hop_pf<P, 12, true, true>(A, grid, threads, pf, s); break;
+    case 0: launch_hop_pf<P, 18, false, false>(B, grid, threads, pf, s); break;
+    case 1: launch_hop_pf<P, 18, false, true>(B, grid, threads, pf, s); break;
+    case 2: launch_hop_pf<P, 18, true, false>(B, grid, threads, pf, s); break;
+    case 3: launch_hop_pf<P, 18, true, true>(B, grid, threads, pf, s); break;
+    case 4: launch_hop_pf<P, 12, false, false>(B, grid, threads, pf, s); break;
+    case 5: launch_hop_pf<P, 12, false, true>(B, grid, threads, pf, s); break;
+    case 6: launch_hop_pf<P, 12, true, false>(B, grid, threads, pf, s); break;
+    case 7: launch_hop_pf<P, 12, true, true>(B, grid, threads, pf, s); break;
     }
     return cudaGetLastError();
 }

@@ -147,6 +147,20 @@ template <int P> struct Spinor {
         if (Prec<P>::scaled) prefetch_l2(reinterpret_cast<const float *>(f + (size_t)nplane * vh * 16) + i);
     }
 
+    // The stored values without the per-site scale, which is returned (1 for
+    // unscaled types); lets a linear consumer apply the scale once at the end.
+    __device__ static __forceinline__ float load_unscaled(const char *f, int vh, int i, real (&v)[24])
+    {
+        float s = 1.0f;
+        if (Prec<P>::scaled) s = __ldg(reinterpret_cast<const float *>(f + (size_t)nplane * vh * 16) + i);
+#pragma unroll
+        for (int k = 0; k < nplane; ++k) {
+            uint4 w = ldg16(f + ((size_t)k * vh + i) * 16);
+            unpack16<P>(w, v + k * Prec<P>::per16, 1.0f);
+        }
+        return s;
+    }
+
     __device__ static __forceinline__ void load(const char *f, int vh, int i, real (&v)[24])
     {
         float s = 1.0f;

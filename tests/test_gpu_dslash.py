@@ -9,7 +9,7 @@ import pytest
 import oracle
 import paper_1901_07294_gb300 as wd
 import synth
-from tests._gpu import TOL, pack_field, to_dev, unpack_field
+from tests._gpu import TOL, check_dslash, pack_field, to_dev, unpack_field
 from tests._lattice import parity, rel_max_err, volume
 
 pytestmark = pytest.mark.gpu
@@ -199,6 +199,37 @@ def test_autotuner_table_and_choice():
     U, _ = _inputs(dims)
     g = wd.Gauge(ctx, dims, U)
     table = wd.tune_dslash(ctx, g, wd.F32, 18, full=True)
-    assert len(table) == 12
-    assert {t["variant"] for t in table} == {0, 1, 2}
+    # 4 block sizes x 4 single-field variants (schedules 0, 1, 2 and the high-occupancy build 4)
+    assert len(table) == 16
+    assert {t["variant"] for t in table} == {0, 1, 2, 4}
     assert all(t["ms"] > 0 for t in table)
+
+
+@pytest.mark.parametrize("prec", ALL_PREC)
+@pytest.mark.parametrize("dims,threads", [((8, 8, 8, 8), 64), ((16, 16, 16, 32), 256), ((4, 6, 8, 10), 96)])
+def test_high_occupancy_variant_matches_oracle(prec, dims, threads):
+    """Variant 4: schedule 1 compiled for 3 blocks of 256 threads per SM, with an axpby term."""
+    ctx = wd.Context(0)
+    U, psi = _inputs(dims)
+    g = wd.Gauge(ctx, dims, U)
+    for recon in (18, 12):
+        wd.tune_set_dslash(ctx, g, prec, recon, True, True, 1, threads, 4)
+        wd.tune_set_dslash(ctx, g, prec, recon, False, True, 1, threads, 4)
+        fin = pack_field(ctx, dims, wd.SITES_FULL, prec, psi)
+        fout = wd.alloc_field(dims, wd.SITES_FULL, prec)
+        wd.dslash_apply(ctx, g, fout, fin, 0.1, prec=prec, recon=recon)
+        check_dslash(unpack_field(ctx, dims, wd.SITES_FULL, prec, fout), oracle.dirac(dims, U, psi, 0.1), prec,
+                     dims, U, psi, recon, lambda u, p: oracle.dirac(dims, u, p, 0.1))
+        fo = pack_field(ctx, dims, wd.SITES_ODD, prec, psi)
+        fx = pack_field(ctx, dims, wd.SITES_EVEN, prec, psi)
+        fe = wd.alloc_field(dims, wd.SITES_EVEN, prec)
+        wd.dslash_eo_apply(ctx, g, fe, fo, fx, 0, 1.5, -0.25, prec=prec, recon=recon)
+        par = parity(dims)
+
+        def eo(u, p):
+            src = p.copy()
+            src[par == 0] = 0
+            return (1.5 * p - 0.25 * oracle.hop(dims, u, src, out_parity=0))[par == 0]
+
+        got = unpack_field(ctx, dims, wd.SITES_EVEN, prec, fe)
+        check_dslash(got[par == 0], eo(U, psi), prec, dims, U, psi, recon, eo)
