@@ -625,6 +625,9 @@ def _cg_section(wd, torch, ctx, with_cpu: bool):
             ("fp16", dict(inner_prec=wd.F16, reliable=True, delta=0.1)),
             ("bf16", dict(inner_prec=wd.BF16, reliable=True, delta=0.1)),
             ("fp16_r12", dict(inner_prec=wd.F16, inner_recon=12, reliable=True, delta=0.1)),
+            ("fp16_delta0.01", dict(inner_prec=wd.F16, reliable=True, delta=0.01)),
+            ("fp16_delta0.001", dict(inner_prec=wd.F16, reliable=True, delta=0.001)),
+            ("fp32_delta0.001", dict(inner_prec=wd.F32, reliable=True, delta=0.001)),
             ("fp16_refine", dict(inner_prec=wd.F16, reliable=False, delta=1e-3))]
     out = {"lattice": list(dims), "tol": 1e-10, "source": "Gaussian on even sites, seed 3001", "runs": {}}
     for mass in (0.1, 0.05):

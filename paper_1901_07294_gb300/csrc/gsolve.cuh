@@ -138,22 +138,35 @@ template <int PS> int init(const wd_ctx *ctx, GSolve &q)
     default: { constexpr int PS = PREC_F32; return CALL; }                    \
     }
 
-// Allocates the solve's resources and enqueues its initial state and graph
-// capture on its own stream.  Returns WD_ENOMEM if the workspace does not fit.
-inline int gs_setup(const wd_ctx *ctx, GSolve &q, bool inject_alloc_failure = false)
+// Allocates a solve's device workspace, pinned scalars and stream.  Returns
+// WD_ENOMEM if the workspace does not fit.
+inline int gs_alloc(GSolve &q)
 {
     q.vh = q.gauge->geo.Vh;
     q.prec = q.opts.inner_prec;
     const size_t bytes = gs_footprint(q.vh, q.prec);
-    if (inject_alloc_failure) return set_error(WD_ENOMEM, "injected allocation failure (WD_FAULT=alloc)");
     if (cudaMalloc(&q.mem, bytes) != cudaSuccess) {
         cudaGetLastError();
         q.mem = nullptr;
         return set_error(WD_ENOMEM, "cudaMalloc of %zu bytes of solve workspace failed", bytes);
     }
     WD_CUDA_TRY(cudaMallocHost(&q.h, 8 * sizeof(double)));
-    std::memset(q.h, 0, 8 * sizeof(double));
     WD_CUDA_TRY(cudaStreamCreateWithFlags(&q.s, cudaStreamNonBlocking));
+    return WD_OK;
+}
+
+// Lays the solve's fields out in its workspace (from gs_alloc, or reused from
+// an earlier solve with the same footprint), enqueues the initial state and
+// builds the graph.  Allocates no device memory.
+inline int gs_bind(const wd_ctx *ctx, GSolve &q)
+{
+    q.vh = q.gauge->geo.Vh;
+    q.prec = q.opts.inner_prec;
+    q.iters = q.updates = 0;
+    q.status = WD_OK;
+    q.active = true;
+    q.rel = 1.0;
+    std::memset(q.h, 0, 8 * sizeof(double));
     char *p = (char *)q.mem;
     auto take = [&p](size_t n) {
         char *r = p;
@@ -170,7 +183,14 @@ inline int gs_setup(const wd_ctx *ctx, GSolve &q, bool inject_alloc_failure = fa
     WD_GS_DISPATCH(q.prec, gs_detail::init<PS>(ctx, q));
 }
 
-// After gs_setup's work has finished: reads |b|^2 and prepares the test.
+// gs_alloc + gs_bind.
+inline int gs_setup(const wd_ctx *ctx, GSolve &q)
+{
+    WD_TRY(gs_alloc(q));
+    return gs_bind(ctx, q);
+}
+
+// After gs_bind's work has finished: reads |b|^2 and prepares the test.
 inline void gs_start(GSolve &q)
 {
     q.b2 = q.h[0];
@@ -227,6 +247,14 @@ inline int gs_after(const wd_ctx *ctx, GSolve &q)
     WD_CUDA_TRY(cudaStreamSynchronize(q.s));
     q.maxr = std::sqrt(r2t);
     return WD_OK;
+}
+
+// Drops the solve's graph but keeps workspace, scalars and stream for reuse.
+inline void gs_release_graph(GSolve &q)
+{
+    if (q.s) cudaStreamSynchronize(q.s);
+    if (q.exec) cudaGraphExecDestroy(q.exec);
+    q.exec = nullptr;
 }
 
 inline void gs_release(GSolve &q)

@@ -55,6 +55,16 @@ struct rq_queue {
     uint64_t submitted = 0, completed = 0, stalls = 0, steps = 0, admitted = 0;
     double occupancy_sum = 0.0;
     int fault_alloc_at = 0;   // WD_FAULT=alloc:N -> the N-th admission fails
+    // idle workspaces of finished requests, reused by requests of the same
+    // footprint (scheduler thread only); they count against the budget
+    struct Idle {
+        size_t foot;
+        void *mem;
+        double *h;
+        cudaStream_t s;
+    };
+    std::vector<Idle> pool;
+    size_t pool_bytes = 0;
 };
 
 namespace wd {
@@ -77,6 +87,54 @@ void finish(rq_queue *q, Req *r, int status)
     q->in_use -= r->foot;
     q->completed++;
     q->cv_done.notify_all();
+}
+
+void free_idle(rq_queue::Idle &e)
+{
+    cudaStreamSynchronize(e.s);
+    cudaStreamDestroy(e.s);
+    cudaFree(e.mem);
+    cudaFreeHost(e.h);
+}
+
+// Workspace for an admitted request: an idle one of the same footprint if
+// there is one, else a new allocation after idle ones are freed until the
+// budget holds in-use plus idle memory.
+int acquire(rq_queue *q, Req *r)
+{
+    for (size_t k = 0; k < q->pool.size(); ++k)
+        if (q->pool[k].foot == r->foot) {
+            r->gs.mem = q->pool[k].mem;
+            r->gs.h = q->pool[k].h;
+            r->gs.s = q->pool[k].s;
+            q->pool_bytes -= r->foot;
+            q->pool.erase(q->pool.begin() + (long)k);
+            return WD_OK;
+        }
+    size_t in_use;
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        in_use = q->in_use;
+    }
+    while (!q->pool.empty() && in_use + q->pool_bytes > q->budget) {
+        q->pool_bytes -= q->pool.front().foot;
+        free_idle(q->pool.front());
+        q->pool.erase(q->pool.begin());
+    }
+    return gs_alloc(r->gs);
+}
+
+// Returns a finished request's workspace to the pool.
+void park(rq_queue *q, Req *r)
+{
+    gs_release_graph(r->gs);
+    if (r->gs.mem) {
+        q->pool.push_back({r->foot, r->gs.mem, r->gs.h, r->gs.s});
+        q->pool_bytes += r->foot;
+    }
+    r->gs.mem = nullptr;
+    r->gs.h = nullptr;
+    r->gs.s = nullptr;
 }
 
 void scheduler(rq_queue *q)
@@ -108,7 +166,8 @@ void scheduler(rq_queue *q)
             r->res.t_admit = now_s(q);
             q->admitted++;
             const bool inject = q->fault_alloc_at > 0 && (int)q->admitted == q->fault_alloc_at;
-            int rc = gs_setup(q->ctx, r->gs, inject);
+            int rc = inject ? set_error(WD_ENOMEM, "injected allocation failure (WD_FAULT=alloc)") : acquire(q, r);
+            if (rc == WD_OK) rc = gs_bind(q->ctx, r->gs);
             if (rc == WD_OK && cudaStreamSynchronize(r->gs.s) != cudaSuccess) rc = set_error(WD_ECUDA, "set-up failed");
             if (rc != WD_OK) {
                 gs_release(r->gs);
@@ -118,7 +177,7 @@ void scheduler(rq_queue *q)
             gs_start(r->gs);
             r->res.t_start = now_s(q);
             if (!r->gs.active) {
-                gs_release(r->gs);
+                park(q, r);
                 finish(q, r, r->gs.status);
                 continue;
             }
@@ -155,12 +214,16 @@ void scheduler(rq_queue *q)
                 keep.push_back(r);
                 continue;
             }
-            gs_release(r->gs);
+            if (rc == WD_ECUDA) gs_release(r->gs);
+            else park(q, r);
             finish(q, r, rc != WD_OK ? rc : r->gs.status);
         }
         std::lock_guard<std::mutex> lk(q->mu);
         q->running.swap(keep);
     }
+    for (auto &e : q->pool) free_idle(e);
+    q->pool.clear();
+    q->pool_bytes = 0;
 }
 
 int check_request(const wd_solve_desc *d)
