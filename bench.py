@@ -135,6 +135,14 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+_T0 = time.perf_counter()
+
+
+def _log(section: str) -> None:
+    """Progress of the benchmark sections on stderr (the JSON line goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {section}", file=sys.stderr, flush=True)
+
+
 def job_time_ms(local_ms: float, ws: int, device) -> float:
     """Whole-job time of the timed region: the slowest rank's (max over ranks)."""
     import torch
@@ -302,19 +310,25 @@ def run_gpu(args):
 
     variants = {}
     if not args.no_variants:
+        _log("variants")
         variants = _variants(wd, torch, ctx, dims, U, psi, stream, peak)
     mrhs = None
     if not args.no_variants:
+        _log("multi_rhs")
         mrhs = _mrhs_section(wd, torch, ctx, U, psi, peak)
     batch = None
     if not args.no_cg:
+        _log("batch")
         batch = _batch_section(wd, torch, ctx)
     serving = None
     if not args.no_cg and not args.no_serving:
+        _log("serving")
         serving = _serving_section(wd, torch, ctx)
     cg = None
     if not args.no_cg:
+        _log("cg")
         cg = _cg_section(wd, torch, ctx, with_cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline))
+    _log("done")
 
     line = {
         "metric": "dslash_hbm_gbs", "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
@@ -487,14 +501,14 @@ def _batch_section(wd, torch, ctx):
         fb = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
         wd.pack(ctx, dims, wd.SITES_EVEN, wd.F64, torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
         probs.append(dict(gauge=gauges[dims], mass=float(rng.uniform(0.05, 0.5)), tol=1e-10, b=fb,
-                          x=wd.alloc_field(dims, wd.SITES_EVEN, wd.F64), inner_prec=wd.F32, delta=0.1))
+                          x=wd.alloc_field(dims, wd.SITES_EVEN, wd.F64), inner_prec=wd.F32, delta=0.01))
     t0 = time.perf_counter()
     for p in probs[:1] + probs[8:9] + probs[16:17]:
         for with_x in (False, True):
             wd.tune_dslash(ctx, p["gauge"], wd.F32, 18, full=False, with_x=with_x)
             wd.tune_dslash(ctx, p["gauge"], wd.F64, 18, full=False, with_x=with_x)
     tune_s = time.perf_counter() - t0
-    out = {"solves": 24, "lattices": [list(d) for d in lattices], "tol": 1e-10, "inner": "fp32 reliable-update",
+    out = {"solves": 24, "lattices": [list(d) for d in lattices], "tol": 1e-10, "inner": "fp32 reliable-update, delta 0.01",
            "autotune_seconds": round(tune_s, 3)}
     for name, mode in (("sequential", wd.BATCH_SEQUENTIAL), ("graph", wd.BATCH_GRAPH),
                        ("persistent", wd.BATCH_PERSISTENT)):
@@ -575,7 +589,7 @@ def _serving_section(wd, torch, ctx, n_main=600, n_sweep=150, warm=60):
                 time.sleep(max(0.0, min(0.0005, t_next - time.perf_counter())))
             x = pools[dims].pop() if pools[dims] else wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
             t = q.submit(dict(gauge=gauges[dims], mass=mass, tol=tol, b=srcs[dims][i % 2], x=x,
-                              inner_prec=wd.F16, delta=0.1))
+                              inner_prec=wd.F16, delta=0.01))
             waits.put((t, dims, x, tol))
         waits.put(None)
         wt.join()
@@ -621,13 +635,12 @@ def _cg_section(wd, torch, ctx, with_cpu: bool):
     wd.pack(ctx, dims, wd.SITES_EVEN, wd.F64, torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
     fx = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
     runs = [("fp64", dict(inner_prec=wd.F64)),
-            ("fp32", dict(inner_prec=wd.F32, reliable=True, delta=0.1)),
-            ("fp16", dict(inner_prec=wd.F16, reliable=True, delta=0.1)),
-            ("bf16", dict(inner_prec=wd.BF16, reliable=True, delta=0.1)),
-            ("fp16_r12", dict(inner_prec=wd.F16, inner_recon=12, reliable=True, delta=0.1)),
-            ("fp16_delta0.01", dict(inner_prec=wd.F16, reliable=True, delta=0.01)),
+            ("fp32", dict(inner_prec=wd.F32, reliable=True, delta=0.01)),
+            ("fp16", dict(inner_prec=wd.F16, reliable=True, delta=0.01)),
+            ("bf16", dict(inner_prec=wd.BF16, reliable=True, delta=0.01)),
+            ("fp16_r12", dict(inner_prec=wd.F16, inner_recon=12, reliable=True, delta=0.01)),
+            ("fp16_delta0.1", dict(inner_prec=wd.F16, reliable=True, delta=0.1)),
             ("fp16_delta0.001", dict(inner_prec=wd.F16, reliable=True, delta=0.001)),
-            ("fp32_delta0.001", dict(inner_prec=wd.F32, reliable=True, delta=0.001)),
             ("fp16_refine", dict(inner_prec=wd.F16, reliable=False, delta=1e-3))]
     out = {"lattice": list(dims), "tol": 1e-10, "source": "Gaussian on even sites, seed 3001", "runs": {}}
     for mass in (0.1, 0.05):

@@ -278,7 +278,7 @@ def convert(ctx: Context, dims, sites: int, prec_out: int, out, prec_in: int, in
 
 
 def cg_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-10, inner_prec: int = F64,
-             inner_recon: int = 18, outer_recon: int = 18, reliable: bool = True, delta: float = 0.1,
+             inner_recon: int = 18, outer_recon: int = 18, reliable: bool = True, delta: float = 0.01,
              maxiter: int = 20000, autotune: bool = False, stream=None, check: bool = True) -> dict:
     """Solve Mhat^dagger Mhat x = b on even half fields (FP64).  Returns the solve statistics;
     raises WdError on failure unless check=False (then 'status' carries the code)."""
@@ -341,7 +341,7 @@ def cg_solve_batch(ctx: Context, problems: list[dict], mode: int = BATCH_SEQUENT
     descs = (SolveDesc * max(n, 1))()
     for k, p in enumerate(problems):
         o = CgOpts(int(p.get("inner_prec", F32)), int(p.get("inner_recon", 18)), int(p.get("outer_recon", 18)),
-                   int(bool(p.get("reliable", True))), float(p.get("delta", 0.1)), int(p.get("maxiter", 20000)),
+                   int(bool(p.get("reliable", True))), float(p.get("delta", 0.01)), int(p.get("maxiter", 20000)),
                    int(bool(p.get("autotune", False))))
         descs[k] = SolveDesc(p["gauge"].handle, float(p["mass"]), float(p["tol"]), _ptr(p["x"]), _ptr(p["b"]), o)
     stats = (CgStats * max(n, 1))()
@@ -374,7 +374,7 @@ class RqCounters(ctypes.Structure):
 
 def _desc(p: dict) -> SolveDesc:
     o = CgOpts(int(p.get("inner_prec", F16)), int(p.get("inner_recon", 18)), int(p.get("outer_recon", 18)),
-               int(bool(p.get("reliable", True))), float(p.get("delta", 0.1)), int(p.get("maxiter", 20000)),
+               int(bool(p.get("reliable", True))), float(p.get("delta", 0.01)), int(p.get("maxiter", 20000)),
                int(bool(p.get("autotune", False))))
     return SolveDesc(p["gauge"].handle, float(p["mass"]), float(p["tol"]), _ptr(p["x"]), _ptr(p["b"]), o)
 

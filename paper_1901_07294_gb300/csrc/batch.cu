@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256, 1) cg_persistent_kernel(const PSolve *__r
     double one[1] = {v[0]};
     if (!group_sum(g, one)) return;
     const double b2 = one[0];
-    int status = WD_OK, it = 0, nupd = 0;
+    int status = WD_OK, it = 0, nupd = 0, it_update = 0;
     double r2t = b2;
     if (b2 > 0.0) {
         const double stop2 = S->tol * S->tol * b2;
@@ -237,7 +237,8 @@ __global__ void __launch_bounds__(256, 1) cg_persistent_kernel(const PSolve *__r
             double r2new = rr[0];
             const double rn = sqrt(r2new);
             if (rn > maxr) maxr = rn;
-            if (rn < S->delta * maxr || r2new <= stop2) {
+            if (rn < S->delta * maxr || r2new <= stop2 || it - it_update >= RELIABLE_MAX_GAP) {
+                it_update = it;
                 // reliable update: x += xs (FP64), true residual with the FP64 operator
                 for (int i = i0; i < vh; i += stride) {
                     double xv[24];

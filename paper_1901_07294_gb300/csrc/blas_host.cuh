@@ -7,6 +7,10 @@
 
 namespace wd {
 
+// Mixed-precision CG: iterations after which a reliable update is forced
+// even if the low-precision residual has not yet dropped by delta.
+constexpr int RELIABLE_MAX_GAP = 128;
+
 template <int P> inline FieldRef<P> field_ref(const void *p, int vh)
 {
     return FieldRef<P>{(char *)p, half_field_bytes(vh, P), vh};

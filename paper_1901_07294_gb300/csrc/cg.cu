@@ -98,7 +98,7 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
     double r2 = b2, maxr = std::sqrt(b2), r2_restart = b2, r2_true = b2;
     bool converged = false;
     int status = WD_OK;
-    int it = 0;
+    int it = 0, it_update = 0;
     while (it < o.maxiter) {
         WD_TRY(apply_mdagm(g, PS, o.inner_recon, mass, ps, aps, tso, tse, s));
         WD_TRY(run_blas(ctx, OpDotReAlpha<PS>{FS(ps), FS(aps), r2, d + 1}, vh, s));   // d1 = pAp, d2 = alpha
@@ -114,7 +114,11 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
         const double rn = std::sqrt(r2_new);
         if (rn > maxr) maxr = rn;
         bool update;
-        if (reliable) update = (rn < delta * maxr) || (r2_new <= stop2);
+        // a reliable update also when the low-precision residual has gone
+        // RELIABLE_MAX_GAP iterations without one (it can stall above
+        // delta * max|r| once rounding noise dominates)
+        if (reliable)
+            update = (rn < delta * maxr) || (r2_new <= stop2) || (PS != PREC_F64 && it - it_update >= RELIABLE_MAX_GAP);
         else update = r2_new <= std::fmax(stop2, delta * delta * r2_restart);
         if (update) {
             // x += x_lo (FP64), then the true residual with the FP64 operator
@@ -125,6 +129,7 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
             WD_TRY(read_scalars(ctx, 4, 1, s));
             r2_true = h[4];
             ++st.reliable_updates;
+            it_update = it;
             if (r2_true <= stop2) {
                 converged = true;
                 break;

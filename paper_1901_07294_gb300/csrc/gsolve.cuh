@@ -36,7 +36,7 @@ struct GSolve {
     RedScratch red{};
     // state
     double b2 = 0, stop2 = 0, maxr = 0;
-    int iters = 0, updates = 0, status = WD_OK;
+    int iters = 0, updates = 0, status = WD_OK, iters_at_update = 0;
     bool active = true;
     double rel = 1.0;
 };
@@ -66,17 +66,22 @@ template <typename Op> inline int launch(const wd_ctx *ctx, const Op &op, int ns
     return e == cudaSuccess ? WD_OK : set_error(WD_ECUDA, "BLAS launch failed: %s", cudaGetErrorString(e));
 }
 
+// One iteration, starting with the direction update p = r + beta p
+// (beta = s[0]/s[4]; s[4] = +inf gives p = r).  A replay therefore ends right
+// after the residual update, and a host-side reliable update that replaces r
+// and s[0] between replays is picked up by the next direction update, as in
+// the sequential solver.
 template <int PS> int iteration(const wd_ctx *ctx, GSolve &q)
 {
     const int vh = q.vh;
     auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
     auto FX = [&](const void *p) { return field_ref<PREC_F32>(p, vh); };
+    WD_TRY(launch(ctx, OpXpayDev<PS>{FS(q.rs), FS(q.ps), q.scal}, vh, q.red, q.s));
     WD_TRY(mdagm(q.gauge, PS, q.opts.inner_recon, q.mass, q.ps, q.aps, q.tso, q.tse, q.s));
     WD_TRY(launch(ctx, OpDotAlphaDev<PS>{FS(q.ps), FS(q.aps), q.scal}, vh, q.red, q.s));
     OpCgUpdateDev<PREC_F32, PS> up{
         OpCgUpdate<PREC_F32, PS>{FX(q.xs), FS(q.rs), FS(q.ps), FS(q.aps), q.scal + 2, nullptr}, q.scal};
     WD_TRY(launch(ctx, up, vh, q.red, q.s));
-    WD_TRY(launch(ctx, OpXpayDev<PS>{FS(q.rs), FS(q.ps), q.scal}, vh, q.red, q.s));
     return WD_OK;
 }
 
@@ -107,6 +112,8 @@ template <int PS> int init(const wd_ctx *ctx, GSolve &q)
     WD_CUDA_TRY(cudaMemcpyAsync(q.r, q.b, (size_t)vh * 192, cudaMemcpyDeviceToDevice, q.s));
     WD_TRY(launch(ctx, OpConvert<PS, PREC_F64>{FS(q.rs), F64(q.r)}, vh, q.red, q.s));
     WD_CUDA_TRY(cudaMemcpyAsync(q.ps, q.rs, half_field_bytes(vh, PS), cudaMemcpyDeviceToDevice, q.s));
+    static const double inf = INFINITY;   // s[4] = inf: the first direction update gives p = r
+    WD_CUDA_TRY(cudaMemcpyAsync(q.scal + 4, &inf, sizeof(double), cudaMemcpyHostToDevice, q.s));
     WD_CUDA_TRY(cudaMemcpyAsync(q.h, q.scal, sizeof(double), cudaMemcpyDeviceToHost, q.s));
     // build a graph of GS_ITERS iterations node by node (no stream capture)
     cudaGraph_t graph;
@@ -162,7 +169,7 @@ inline int gs_bind(const wd_ctx *ctx, GSolve &q)
 {
     q.vh = q.gauge->geo.Vh;
     q.prec = q.opts.inner_prec;
-    q.iters = q.updates = 0;
+    q.iters = q.updates = q.iters_at_update = 0;
     q.status = WD_OK;
     q.active = true;
     q.rel = 1.0;
@@ -219,7 +226,10 @@ inline int gs_after(const wd_ctx *ctx, GSolve &q)
     const bool broke = q.h[6] != 0.0 || !std::isfinite(r2);
     const double rn = std::sqrt(r2);
     if (rn > q.maxr) q.maxr = rn;
-    if (!(broke || rn < q.opts.delta * q.maxr || r2 <= q.stop2 || q.iters >= q.opts.maxiter)) return WD_OK;
+    if (!(broke || rn < q.opts.delta * q.maxr || r2 <= q.stop2 || q.iters >= q.opts.maxiter ||
+          q.iters - q.iters_at_update >= RELIABLE_MAX_GAP))
+        return WD_OK;
+    q.iters_at_update = q.iters;
     int rc;
     switch (q.prec) {
     case WD_F16: rc = gs_detail::reliable_update<PREC_F16>(ctx, q); break;
@@ -241,9 +251,13 @@ inline int gs_after(const wd_ctx *ctx, GSolve &q)
         return WD_OK;
     }
     // continue from the true residual; restart the direction after a breakdown
-    double sc[8] = {r2t, 0, 0, 0, r2t, 0, 0, 0};
-    WD_CUDA_TRY(cudaMemcpyAsync(q.scal, sc, sizeof(sc), cudaMemcpyHostToDevice, q.s));
-    if (broke) WD_CUDA_TRY(cudaMemcpyAsync(q.ps, q.rs, half_field_bytes(q.vh, q.prec), cudaMemcpyDeviceToDevice, q.s));
+    // s[0] = true |r|^2, so the next direction update uses beta = |r_true|^2 / |r_old|^2
+    // (s[4] still holds |r_old|^2); after a breakdown restart with p = r (s[4] = inf)
+    WD_CUDA_TRY(cudaMemcpyAsync(q.scal, &q.h[7], sizeof(double), cudaMemcpyHostToDevice, q.s));
+    if (broke) {
+        static const double restart[3] = {INFINITY, 0.0, 0.0};   // s[4], s[5], s[6]
+        WD_CUDA_TRY(cudaMemcpyAsync(q.scal + 4, restart, sizeof(restart), cudaMemcpyHostToDevice, q.s));
+    }
     WD_CUDA_TRY(cudaStreamSynchronize(q.s));
     q.maxr = std::sqrt(r2t);
     return WD_OK;

@@ -164,3 +164,23 @@ def test_injected_allocation_failure(monkeypatch):
     q.close()
     assert [r["status"] for r in res] == [0, wd.WD_ENOMEM, 0, 0]
     assert _true_rel(ctx, reqs[2][1], reqs[2][0]["x"])[0] <= 1.05e-10
+
+
+@pytest.mark.parametrize("prec", [wd.F16, wd.BF16])
+def test_hard_solves_with_small_delta(prec):
+    """Small mass, tight tolerance and delta = 0.01 (few reliable updates): every solve converges,
+    with its true residual checked by the oracle."""
+    ctx = _ctx()
+    q = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=8)
+    reqs = []
+    for k in range(6):
+        p, host = _request(ctx, 20 + k, dims=[(8, 8, 8, 16), (8, 8, 8, 8), (4, 6, 8, 10)][k % 3], tol=1e-12, prec=prec)
+        p["mass"] = 0.02
+        p["delta"] = 0.01
+        reqs.append((p, (host[0], host[1], 0.02, host[3])))
+    ts = [q.submit(p) for p, _ in reqs]
+    res = [q.wait(t, timeout_ms=120000) for t in ts]
+    q.close()
+    for (p, host), r in zip(reqs, res):
+        assert r["status"] == 0, r
+        assert _true_rel(ctx, host, p["x"])[0] <= 1.05e-12
