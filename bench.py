@@ -311,7 +311,11 @@ def run_gpu(args):
     variants = {}
     if not args.no_variants:
         _log("variants")
-        variants = _variants(wd, torch, ctx, dims, U, psi, stream, peak)
+        device_peaks = {"fp64_tflops": round(wd.probe_fma_tflops(ctx, wd.F64), 3),
+                        "fp32_tflops": round(wd.probe_fma_tflops(ctx, wd.F32), 2),
+                        "how": "FMA chains on every SM, CUDA events (wd_probe_fma)"}
+        variants = _variants(wd, torch, ctx, dims, U, psi, stream, peak, device_peaks["fp64_tflops"])
+        variants["device_peaks"] = device_peaks
     mrhs = None
     if not args.no_variants:
         _log("multi_rhs")
@@ -368,7 +372,7 @@ def run_gpu(args):
     return 0
 
 
-def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, reps=50):
+def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, fp64_tflops=None, reps=50):
     """Per-launch GB/s of every operator variant of the 32^4 / 16^3x32 configuration."""
     import numpy as np
 
@@ -418,6 +422,10 @@ def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, reps=50
                     key = f"{'x'.join(map(str, dims))}/{pn}/{kind}/r{recon}"
                     out[key] = {"ms": round(ms, 5), "gbs": round(gbs, 1), "frac_hbm": round(gbs / peak, 4),
                                 "gflops": round(FLOPS_PER_SITE * nsite / (ms * 1e-3) / 1e9, 1)}
+                    if pn == "f64" and fp64_tflops:
+                        # FP64 is bounded by the FP64 units: the useful 1320 flops/site
+                        # against the measured FP64 FMA rate
+                        out[key]["frac_fp64_alu"] = round(out[key]["gflops"] / 1e3 / fp64_tflops, 4)
         g.close()
     return out
 
@@ -639,6 +647,7 @@ def _cg_section(wd, torch, ctx, with_cpu: bool):
             ("fp16", dict(inner_prec=wd.F16, reliable=True, delta=0.01)),
             ("bf16", dict(inner_prec=wd.BF16, reliable=True, delta=0.01)),
             ("fp16_r12", dict(inner_prec=wd.F16, inner_recon=12, reliable=True, delta=0.01)),
+            ("fp16_graph", dict(inner_prec=wd.F16, reliable=True, delta=0.01, use_graph=True)),
             ("fp16_delta0.1", dict(inner_prec=wd.F16, reliable=True, delta=0.1)),
             ("fp16_delta0.001", dict(inner_prec=wd.F16, reliable=True, delta=0.001)),
             ("fp16_refine", dict(inner_prec=wd.F16, reliable=False, delta=1e-3))]
@@ -663,6 +672,7 @@ def _cg_section(wd, torch, ctx, with_cpu: bool):
     for mass in (0.1, 0.05):
         t64 = out["runs"][f"m{mass}/fp64"]["seconds"]
         out[f"speedup_fp16_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/fp16"]["seconds"], 2)
+        out[f"speedup_fp16_graph_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/fp16_graph"]["seconds"], 2)
         out[f"speedup_bf16_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/bf16"]["seconds"], 2)
     if with_cpu:
         import oracle

@@ -146,6 +146,12 @@ int dslash_eo_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, c
                     int out_parity, double a, double b, int dagger, int nrhs, int prec, int recon,
                     void *stream);
 
+/* Measured FMA throughput of the device (TFLOP/s, one FMA = 2 flops) for
+ * prec WD_F64 or WD_F32: the ALU roofline of the FP64 operator, which is
+ * bounded by the FP64 units rather than by HBM.  The paper has no
+ * counterpart; this is measurement support.  Synchronous, about 0.1 s. */
+int wd_probe_fma(wd_ctx *ctx, int prec, double *tflops);
+
 /* ---- Autotuning of the operator launches ------------------------------------
  * The hop kernel has tunable launch parameters: threads per block (32..256,
  * multiple of 32) and a memory-schedule variant (0: directions x+,x-,..,t-
@@ -229,6 +235,9 @@ typedef struct {
     double delta;      /* see above; ignored for inner_prec = WD_F64 */
     int maxiter;       /* limit on inner iterations */
     int autotune;      /* 1: tune the hop launches the solve uses (once per context) */
+    int use_graph;     /* 1 (mixed precision, reliable = 1): run 8 iterations per CUDA-graph
+                          replay with the CG scalars on the device; the host checks the
+                          residual and does reliable updates between replays */
 } wd_cg_opts;
 
 typedef struct {

@@ -71,6 +71,7 @@ _SIGS = {
     "rq_stats": (_ip, [_vp, _vp]),
     "rq_destroy": (_ip, [_vp]),
     "wd_solve_workspace_bytes": (_ip, [_DIMS, _ip, ctypes.POINTER(_sz)]),
+    "wd_probe_fma": (_ip, [_vp, _ip, ctypes.POINTER(_dp)]),
 }
 
 
@@ -82,7 +83,7 @@ class TuneEntry(ctypes.Structure):
 class CgOpts(ctypes.Structure):
     """wd_cg_opts"""
     _fields_ = [("inner_prec", _ip), ("inner_recon", _ip), ("outer_recon", _ip), ("reliable", _ip),
-                ("delta", _dp), ("maxiter", _ip), ("autotune", _ip)]
+                ("delta", _dp), ("maxiter", _ip), ("autotune", _ip), ("use_graph", _ip)]
 
 
 class CgStats(ctypes.Structure):
@@ -279,11 +280,12 @@ def convert(ctx: Context, dims, sites: int, prec_out: int, out, prec_in: int, in
 
 def cg_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-10, inner_prec: int = F64,
              inner_recon: int = 18, outer_recon: int = 18, reliable: bool = True, delta: float = 0.01,
-             maxiter: int = 20000, autotune: bool = False, stream=None, check: bool = True) -> dict:
+             maxiter: int = 20000, autotune: bool = False, use_graph: bool = False, stream=None,
+             check: bool = True) -> dict:
     """Solve Mhat^dagger Mhat x = b on even half fields (FP64).  Returns the solve statistics;
     raises WdError on failure unless check=False (then 'status' carries the code)."""
     opts = CgOpts(int(inner_prec), int(inner_recon), int(outer_recon), int(bool(reliable)), float(delta),
-                  int(maxiter), int(bool(autotune)))
+                  int(maxiter), int(bool(autotune)), int(bool(use_graph)))
     st = CgStats()
     rc = load().cg_solve(ctx.handle, gauge.handle, float(mass), _ptr(x), _ptr(b), float(tol), ctypes.byref(opts),
                          ctypes.byref(st), _stream(stream))
@@ -342,7 +344,7 @@ def cg_solve_batch(ctx: Context, problems: list[dict], mode: int = BATCH_SEQUENT
     for k, p in enumerate(problems):
         o = CgOpts(int(p.get("inner_prec", F32)), int(p.get("inner_recon", 18)), int(p.get("outer_recon", 18)),
                    int(bool(p.get("reliable", True))), float(p.get("delta", 0.01)), int(p.get("maxiter", 20000)),
-                   int(bool(p.get("autotune", False))))
+                   int(bool(p.get("autotune", False))), int(bool(p.get("use_graph", False))))
         descs[k] = SolveDesc(p["gauge"].handle, float(p["mass"]), float(p["tol"]), _ptr(p["x"]), _ptr(p["b"]), o)
     stats = (CgStats * max(n, 1))()
     rc = load().cg_solve_batch(ctx.handle, n, descs, int(mode), stats, _stream(stream))
@@ -375,7 +377,7 @@ class RqCounters(ctypes.Structure):
 def _desc(p: dict) -> SolveDesc:
     o = CgOpts(int(p.get("inner_prec", F16)), int(p.get("inner_recon", 18)), int(p.get("outer_recon", 18)),
                int(bool(p.get("reliable", True))), float(p.get("delta", 0.01)), int(p.get("maxiter", 20000)),
-               int(bool(p.get("autotune", False))))
+               int(bool(p.get("autotune", False))), int(bool(p.get("use_graph", False))))
     return SolveDesc(p["gauge"].handle, float(p["mass"]), float(p["tol"]), _ptr(p["x"]), _ptr(p["b"]), o)
 
 
@@ -431,3 +433,10 @@ def solve_workspace_bytes(dims, inner_prec: int) -> int:
     out = _sz()
     _check(load().wd_solve_workspace_bytes(_dims(dims), int(inner_prec), ctypes.byref(out)))
     return int(out.value)
+
+
+def probe_fma_tflops(ctx: Context, prec: int) -> float:
+    """Measured FMA throughput (TFLOP/s) of the device in FP64 or FP32."""
+    out = _dp(0.0)
+    _check(load().wd_probe_fma(ctx.handle, int(prec), ctypes.byref(out)))
+    return float(out.value)

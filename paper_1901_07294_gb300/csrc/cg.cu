@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "blas_host.cuh"
+#include "gsolve.cuh"
 
 namespace wd {
 
@@ -167,6 +168,38 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
     return status;
 }
 
+// The same solve driven by a CUDA graph of GS_ITERS iterations (gsolve.cuh):
+// one host synchronisation per replay instead of one per iteration.  Runs on
+// the solve's own stream; the call is synchronous either way.
+int cg_run_graph(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, double tol,
+                 const wd_cg_opts &o, wd_cg_stats &st)
+{
+    GSolve q;
+    q.gauge = g;
+    q.mass = mass;
+    q.tol = tol;
+    q.x = x;
+    q.b = b;
+    q.opts = o;
+    int rc = gs_setup(ctx, q);
+    if (rc == WD_OK && cudaStreamSynchronize(q.s) != cudaSuccess) rc = set_error(WD_ECUDA, "solve set-up failed");
+    if (rc == WD_OK) gs_start(q);
+    while (rc == WD_OK && q.active) {
+        rc = gs_launch(q);
+        if (rc == WD_OK && cudaStreamSynchronize(q.s) != cudaSuccess) rc = set_error(WD_ECUDA, "graph replay failed");
+        if (rc == WD_OK) rc = gs_after(ctx, q);
+    }
+    gs_release(q);
+    st.iters = q.iters;
+    st.reliable_updates = q.updates;
+    st.true_rel_resid = q.rel;
+    if (rc != WD_OK) return rc;
+    if (q.status == WD_ENOCONV)
+        return set_error(WD_ENOCONV, "CG did not converge in %d iterations (relative residual %.3e)", q.iters, q.rel);
+    if (q.status != WD_OK) return set_error(q.status, "CG failed");
+    return WD_OK;
+}
+
 } // namespace
 
 } // namespace wd
@@ -207,11 +240,15 @@ int cg_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x_e, const void 
     char *x = (char *)x_e;
     const char *b = (const char *)b_e;
     int rc;
-    switch (opts->inner_prec) {
-    case WD_F64: rc = cg_run<PREC_F64, PREC_F64>(ctx, g, mass, x, b, tol, *opts, st, s); break;
-    case WD_F32: rc = cg_run<PREC_F32, PREC_F32>(ctx, g, mass, x, b, tol, *opts, st, s); break;
-    case WD_F16: rc = cg_run<PREC_F16, PREC_F32>(ctx, g, mass, x, b, tol, *opts, st, s); break;
-    default: rc = cg_run<PREC_BF16, PREC_F32>(ctx, g, mass, x, b, tol, *opts, st, s); break;
+    if (opts->use_graph && opts->inner_prec != WD_F64 && opts->reliable) {
+        rc = cg_run_graph(ctx, g, mass, x, b, tol, *opts, st);
+    } else {
+        switch (opts->inner_prec) {
+        case WD_F64: rc = cg_run<PREC_F64, PREC_F64>(ctx, g, mass, x, b, tol, *opts, st, s); break;
+        case WD_F32: rc = cg_run<PREC_F32, PREC_F32>(ctx, g, mass, x, b, tol, *opts, st, s); break;
+        case WD_F16: rc = cg_run<PREC_F16, PREC_F32>(ctx, g, mass, x, b, tol, *opts, st, s); break;
+        default: rc = cg_run<PREC_BF16, PREC_F32>(ctx, g, mass, x, b, tol, *opts, st, s); break;
+        }
     }
     st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     st.status = rc;

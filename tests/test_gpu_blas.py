@@ -68,3 +68,12 @@ def test_axpby_and_convert(ctx, prec):
     wd.convert(ctx, DIMS, sites, wd.F64, f64, prec, fa)
     back = unpack_field(ctx, DIMS, sites, wd.F64, f64)
     assert np.array_equal(back[par == 0], ra[par == 0])
+
+
+def test_fma_probe_reports_plausible_rates(ctx):
+    f64 = wd.probe_fma_tflops(ctx, wd.F64)
+    f32 = wd.probe_fma_tflops(ctx, wd.F32)
+    assert 0.1 < f64 < 200.0 and 1.0 < f32 < 500.0
+    assert f32 > f64
+    with pytest.raises(wd.WdError):
+        wd.probe_fma_tflops(ctx, wd.F16)

@@ -55,6 +55,9 @@ CASES = [
     dict(inner_prec=wd.BF16, reliable=True, delta=0.1),
     dict(inner_prec=wd.F16, inner_recon=12, reliable=True, delta=0.1),
     dict(inner_prec=wd.F32, reliable=False, delta=1e-4),
+    dict(inner_prec=wd.F16, reliable=True, delta=0.01, use_graph=True),
+    dict(inner_prec=wd.BF16, reliable=True, delta=0.01, use_graph=True),
+    dict(inner_prec=wd.F32, reliable=True, delta=0.1, use_graph=True),
     dict(inner_prec=wd.F16, reliable=False, delta=1e-3),
 ]
 

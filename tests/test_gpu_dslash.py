@@ -233,3 +233,22 @@ def test_high_occupancy_variant_matches_oracle(prec, dims, threads):
 
         got = unpack_field(ctx, dims, wd.SITES_EVEN, prec, fe)
         check_dslash(got[par == 0], eo(U, psi), prec, dims, U, psi, recon, eo)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 2, 6), (6, 2, 2, 2), (2, 2, 10, 2)])
+@pytest.mark.parametrize("prec", ALL_PREC)
+@pytest.mark.parametrize("threads,variant", [(32, 0), (64, 1), (256, 2), (192, 4)])
+def test_degenerate_extents_and_ragged_tails(dims, prec, threads, variant):
+    """L_mu = 2 (x+mu and x-mu are the same site, both terms added) and half-lattice sizes far
+    below or not a multiple of the block size."""
+    ctx = wd.Context(0)
+    U = synth.gauge(dims, seed=1111)
+    psi = synth.spinor(dims, seed=2222)
+    g = wd.Gauge(ctx, dims, U)
+    for recon in (18, 12):
+        wd.tune_set_dslash(ctx, g, prec, recon, True, True, 1, threads, variant)
+        fin = pack_field(ctx, dims, wd.SITES_FULL, prec, psi)
+        fout = wd.alloc_field(dims, wd.SITES_FULL, prec)
+        wd.dslash_apply(ctx, g, fout, fin, 0.3, prec=prec, recon=recon)
+        check_dslash(unpack_field(ctx, dims, wd.SITES_FULL, prec, fout), oracle.dirac(dims, U, psi, 0.3), prec,
+                     dims, U, psi, recon, lambda u, p: oracle.dirac(dims, u, p, 0.3))
