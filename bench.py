@@ -461,8 +461,13 @@ def _mrhs_section(wd, torch, ctx, U, psi, peak, reps=20):
         fin = src.repeat(nrhs)
         fout = wd.alloc_field(dims, sites_out, wd.F32, nrhs)
         full = kind == "full"
-        wd.tune_dslash(ctx, g, wd.F32, 18, full=full, with_x=False, nrhs=nrhs)
+        table = wd.tune_dslash(ctx, g, wd.F32, 18, full=full, with_x=False, nrhs=nrhs)
         wd.tune_dslash(ctx, g, wd.F32, 18, full=full, with_x=False, nrhs=1)
+        tuned = min(table, key=lambda t: t["ms"])
+        by_variant = {}
+        for t in table:
+            k = str(t["variant"])
+            by_variant[k] = round(min(by_variant.get(k, 1e30), t["ms"]), 4)
         nb_out = wd.field_bytes(dims, sites_out, wd.F32)
 
         def multi():
@@ -496,7 +501,9 @@ def _mrhs_section(wd, torch, ctx, U, psi, peak, reps=20):
                      "speedup": round(res["singles"] / res["multi"], 2),
                      "multi_gbs": round(b_multi / (res["multi"] * 1e-3) / 1e9, 1),
                      "multi_frac_hbm": round(b_multi / (res["multi"] * 1e-3) / 1e9 / peak, 4),
-                     "bytes_per_site_rhs": round(b_multi / (nsite * nrhs), 1)}
+                     "bytes_per_site_rhs": round(b_multi / (nsite * nrhs), 1),
+                     "tuned": {"threads": tuned["threads"], "variant": tuned["variant"]},
+                     "tune_best_ms_by_variant": by_variant}
     g.close()
     return out
 

@@ -156,7 +156,11 @@ int wd_probe_fma(wd_ctx *ctx, int prec, double *tflops);
  * The hop kernel has tunable launch parameters: threads per block (32..256,
  * multiple of 32) and a memory-schedule variant (0: directions x+,x-,..,t-
  * with no prefetch; 1: backward directions first with the forward links and
- * t-forward neighbour prefetched into L2; 2: as 1 plus the backward links).
+ * t-forward neighbour prefetched into L2; 2: as 1 plus the backward links;
+ * 4: as 1 compiled for 3 resident blocks of 256 threads per SM; for nrhs > 1
+ * also 3: links of 32 sites staged once in shared memory for all nrhs fields,
+ * and 5, 6, 7: as 3 with the (z, t) slices visited in z-strips of width 16,
+ * 8, 4, which shortens the reuse distance of t-neighbours in L2).
  * wd_tune_dslash times every candidate for one problem shape (full = 1: the
  * dslash_apply shape; full = 0: dslash_eo_apply with (with_x = 1) or without
  * the x term) on private scratch fields (allocated and freed by the call),

@@ -36,7 +36,7 @@ static std::pair<int, int> hop_default(int prec, int nrhs)
 int hop_launch_cfg(const HopArgs &A, int prec, int recon, int dagger, int nrhs, int threads, int variant,
                    cudaStream_t s)
 {
-    if (threads < 32 || threads > 256 || (threads & 31) || variant < 0 || variant > HOP_OCC_VARIANT)
+    if (threads < 32 || threads > 256 || (threads & 31) || variant < 0 || variant > HOP_MAX_VARIANT)
         return set_error(WD_EINVAL, "bad hop launch configuration (%d threads, variant %d)", threads, variant);
     cudaError_t e = cudaSuccess;
     switch (prec) {

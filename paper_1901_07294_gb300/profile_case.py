@@ -1,0 +1,66 @@
+"""Runs one operator case a few times, for profiling (e.g. under ncu).
+
+    python -m paper_1901_07294_gb300.profile_case --op eo --prec f32 --dims 32,32,32,32 --nrhs 12 \
+        --launches 4 [--threads 128 --variant 3]
+
+Inputs are the seeded synthetic gauge field and source of the benchmark.  With
+--threads/--variant the launch shape is pinned; otherwise the library default
+is used (no tuning, so few launches precede the profiled ones).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", choices=["full", "eo"], default="full")
+    ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--recon", type=int, default=18)
+    ap.add_argument("--dims", default="32,32,32,32")
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--launches", type=int, default=4)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=-1)
+    a = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import numpy as np
+    import torch
+
+    import paper_1901_07294_gb300 as wd
+    import synth
+
+    prec = {"f64": wd.F64, "f32": wd.F32, "f16": wd.F16, "bf16": wd.BF16}[a.prec]
+    dims = tuple(int(t) for t in a.dims.split(","))
+    ctx = wd.Context(0)
+    g = wd.Gauge(ctx, dims, synth.gauge(dims, seed=1001))
+    g.prepare(prec, a.recon)
+    full = a.op == "full"
+    if a.threads and a.variant >= 0:
+        wd.tune_set_dslash(ctx, g, prec, a.recon, full, False, a.nrhs, a.threads, a.variant)
+    aos = torch.from_numpy(synth.spinor(dims, seed=2001).view(np.float64).reshape(-1).copy()).cuda()
+    one = wd.alloc_field(dims, wd.SITES_FULL, prec)
+    wd.pack(ctx, dims, wd.SITES_FULL, prec, aos, one)
+    if full:
+        fin = one.repeat(a.nrhs)
+        fout = wd.alloc_field(dims, wd.SITES_FULL, prec, a.nrhs)
+    else:
+        half = wd.field_bytes(dims, wd.SITES_ODD, prec)
+        fin = one[half:].repeat(a.nrhs)
+        fout = wd.alloc_field(dims, wd.SITES_EVEN, prec, a.nrhs)
+    for _ in range(a.launches):
+        if full:
+            wd.dslash_apply(ctx, g, fout, fin, 0.1, nrhs=a.nrhs, prec=prec, recon=a.recon)
+        else:
+            wd.dslash_eo_apply(ctx, g, fout, fin, None, wd.EVEN, 0.0, 1.0, nrhs=a.nrhs, prec=prec, recon=a.recon)
+    torch.cuda.synchronize()
+    print(f"profile_case: {a.op} {a.prec} r{a.recon} {a.dims} nrhs={a.nrhs} launches={a.launches} ok")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
