@@ -327,9 +327,12 @@ def run_gpu(args):
         variants = _variants(wd, torch, ctx, dims, U, psi, stream, peak, device_peaks["fp64_tflops"])
         variants["device_peaks"] = device_peaks
     mrhs = None
+    blas = None
     if not args.no_variants:
         _log("multi_rhs")
         mrhs = _mrhs_section(wd, torch, ctx, U, psi, peak)
+        _log("blas")
+        blas = _blas_section(wd, torch, ctx, psi, peak, stream)
     batch = None
     if not args.no_cg:
         _log("batch")
@@ -370,6 +373,7 @@ def run_gpu(args):
         "clocks": clk.summary(),
         "variants": variants,
         "multi_rhs": mrhs,
+        "blas": blas,
         "cg": cg,
         "batch": batch,
         "serving": serving,
@@ -438,6 +442,74 @@ def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, fp64_tf
                         # against the measured FP64 FMA rate
                         out[key]["frac_fp64_alu"] = round(out[key]["gflops"] / 1e3 / fp64_tflops, 4)
         g.close()
+    return out
+
+
+def _blas_section(wd, torch, ctx, psi, peak, stream, reps=30):
+    """Per-call GB/s of the field conversions (pack, unpack, convert) and of the
+    BLAS-1 kernels with FP64 reductions (norm2, dot, axpby) on 32^4 full-lattice
+    fields.  Bytes are the algorithmic ones: each input element read once and each
+    output element written once (sizes from wd.field_bytes, so FP16 includes its
+    per-site scale).  Consecutive calls rotate over enough buffer sets that more
+    than twice the L2 size is touched between two uses of one buffer."""
+    import numpy as np
+
+    dims = DIMS
+    v = int(np.prod(dims))
+    full = wd.SITES_FULL
+    aos_bytes = v * 24 * 8
+    l2 = 129e6
+    aos0 = torch.from_numpy(psi.view(np.float64).reshape(-1).copy()).cuda()
+    res = torch.zeros(2, dtype=torch.float64, device="cuda")
+    fb = {p: wd.field_bytes(dims, full, p) for p in (wd.F64, wd.F32, wd.F16)}
+    out = {"lattice": list(dims), "sites": v}
+
+    def nsets(call_bytes):
+        return int(min(16, max(2, int(np.ceil(2 * l2 / call_bytes)) + 1)))
+
+    def timed(name, call_bytes, make, fn):
+        n = nsets(call_bytes)
+        sets = [make(k) for k in range(n)]
+        for k in range(3):
+            fn(sets[k % n])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(reps):
+            fn(sets[k % n])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = call_bytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": round(ms, 5), "bytes": int(call_bytes), "gbs": round(gbs, 1),
+                     "frac_hbm": round(gbs / peak, 4), "buffer_sets": n}
+        del sets
+
+    def packed(p, k):
+        f = wd.alloc_field(dims, full, p)
+        wd.pack(ctx, dims, full, p, aos0, f, stream=stream)
+        return f
+
+    for p in (wd.F64, wd.F32, wd.F16):
+        pn = wd.PREC_NAMES[p]
+        timed(f"pack_aos_f64_to_{pn}", aos_bytes + fb[p],
+              lambda k, p=p: (aos0.clone(), wd.alloc_field(dims, full, p)),
+              lambda st, p=p: wd.pack(ctx, dims, full, p, st[0], st[1], stream=stream))
+        timed(f"unpack_{pn}_to_aos_f64", aos_bytes + fb[p],
+              lambda k, p=p: (packed(p, k), torch.empty_like(aos0)),
+              lambda st, p=p: wd.unpack(ctx, dims, full, p, st[0], st[1], stream=stream))
+        timed(f"norm2_{pn}", fb[p], lambda k, p=p: packed(p, k),
+              lambda f, p=p: wd.norm2(ctx, dims, full, p, f, res, stream=stream))
+        timed(f"dot_{pn}", 2 * fb[p], lambda k, p=p: (packed(p, k), packed(p, k)),
+              lambda st, p=p: wd.dot(ctx, dims, full, p, st[0], st[1], res, stream=stream))
+        timed(f"axpby_{pn}", 3 * fb[p], lambda k, p=p: (packed(p, k), packed(p, k)),
+              lambda st, p=p: wd.axpby(ctx, dims, full, p, 0.5, st[0], -0.25, st[1], stream=stream))
+    for pi, po in ((wd.F64, wd.F32), (wd.F64, wd.F16), (wd.F16, wd.F64), (wd.F32, wd.F16)):
+        ni, no = wd.PREC_NAMES[pi], wd.PREC_NAMES[po]
+        timed(f"convert_{ni}_to_{no}", fb[pi] + fb[po],
+              lambda k, pi=pi, po=po: (packed(pi, k), wd.alloc_field(dims, full, po)),
+              lambda st, pi=pi, po=po: wd.convert(ctx, dims, full, po, st[1], pi, st[0], stream=stream))
+    timed("norm2_noalloc_f64", fb[wd.F64], lambda k: packed(wd.F64, k),
+          lambda f: wd.norm2_noalloc(dims, full, wd.F64, f, res, stream=stream))
     return out
 
 

@@ -3,7 +3,7 @@
 #include <cstdio>
 #include <string>
 
-#include "dslash_impl.cuh"
+#include "dslash_launch.cuh"
 #include "wd_internal.h"
 
 namespace wd {

@@ -1,0 +1,51 @@
+// Dispatch of a hop launch (precision, link format, dagger, axpy term and
+// variant) to the single-field kernel or the multi right-hand-side kernel.
+#pragma once
+
+#include "dslash_impl.cuh"
+#include "dslash_mrhs.cuh"
+
+namespace wd {
+
+// Launches the hop kernel of precision P for the runtime (recon, dagger,
+// has_x) with `threads` per block (at most 256) and memory schedule `pf`
+// (pf = HOP_MRHS_VARIANT and 5..7: the shared-link multi-RHS kernel, threads/32
+// fields at a time, in the site order hop_mrhs_strip(pf) names).
+template <int P>
+cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int threads, int pf, cudaStream_t s)
+{
+    const int zs = hop_mrhs_strip(pf);
+    if (zs >= 0) {
+        const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
+        const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
+        switch (key) {
+        case 0: launch_hop_mrhs<P, 18, false, false>(A, nrhs, threads, zs, s); break;
+        case 1: launch_hop_mrhs<P, 18, false, true>(A, nrhs, threads, zs, s); break;
+        case 2: launch_hop_mrhs<P, 18, true, false>(A, nrhs, threads, zs, s); break;
+        case 3: launch_hop_mrhs<P, 18, true, true>(A, nrhs, threads, zs, s); break;
+        case 4: launch_hop_mrhs<P, 12, false, false>(A, nrhs, threads, zs, s); break;
+        case 5: launch_hop_mrhs<P, 12, false, true>(A, nrhs, threads, zs, s); break;
+        case 6: launch_hop_mrhs<P, 12, true, false>(A, nrhs, threads, zs, s); break;
+        case 7: launch_hop_mrhs<P, 12, true, true>(A, nrhs, threads, zs, s); break;
+        }
+        return cudaGetLastError();
+    }
+    const HopArgs &B = A;
+    const int per = (A.vh + threads - 1) / threads;
+    const dim3 grid((unsigned)(per * A.nparity), (unsigned)nrhs);
+    const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
+    const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
+    switch (key) {
+    case 0: launch_hop_pf<P, 18, false, false>(B, grid, threads, pf, s); break;
+    case 1: launch_hop_pf<P, 18, false, true>(B, grid, threads, pf, s); break;
+    case 2: launch_hop_pf<P, 18, true, false>(B, grid, threads, pf, s); break;
+    case 3: launch_hop_pf<P, 18, true, true>(B, grid, threads, pf, s); break;
+    case 4: launch_hop_pf<P, 12, false, false>(B, grid, threads, pf, s); break;
+    case 5: launch_hop_pf<P, 12, false, true>(B, grid, threads, pf, s); break;
+    case 6: launch_hop_pf<P, 12, true, false>(B, grid, threads, pf, s); break;
+    case 7: launch_hop_pf<P, 12, true, true>(B, grid, threads, pf, s); break;
+    }
+    return cudaGetLastError();
+}
+
+} // namespace wd

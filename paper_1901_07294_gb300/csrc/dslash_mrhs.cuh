@@ -1,0 +1,225 @@
+// Multi right-hand-side Wilson hop: the links of 32 sites are staged once in
+// shared memory and applied to all fields of the launch (variants
+// HOP_MRHS_VARIANT and 5..7 of the hop launch).
+#pragma once
+
+#include "dslash_impl.cuh"
+
+namespace wd {
+
+// Neighbour checkerboard indices of site i of parity p, order
+// x+, y+, z+, t+, x-, y-, z-, t- (same arithmetic as in hop_kernel).
+__device__ __forceinline__ void site_neighbours(const HopArgs &A, int p, int i, int (&nb)[8])
+{
+    const int Lx = A.L[0], Ly = A.L[1], Lz = A.L[2], Lt = A.L[3];
+    const int lxh = Lx >> 1;
+    int r = i / lxh;
+    const int xh = i - r * lxh;
+    const int y = r % Ly;
+    r /= Ly;
+    const int z = r % Lz;
+    const int t = r / Lz;
+    const int x = 2 * xh + ((p + y + z + t) & 1);
+    const int sy = lxh, sz = lxh * Ly, st = sz * Lz;
+    const int row = i - xh;
+    nb[0] = row + ((x + 1 == Lx ? 0 : x + 1) >> 1);
+    nb[4] = row + ((x == 0 ? Lx - 1 : x - 1) >> 1);
+    nb[1] = (y == Ly - 1) ? i - (Ly - 1) * sy : i + sy;
+    nb[5] = (y == 0) ? i + (Ly - 1) * sy : i - sy;
+    nb[2] = (z == Lz - 1) ? i - (Lz - 1) * sz : i + sz;
+    nb[6] = (z == 0) ? i + (Lz - 1) * sz : i - sz;
+    nb[3] = (t == Lt - 1) ? i - (Lt - 1) * st : i + st;
+    nb[7] = (t == 0) ? i + (Lt - 1) * st : i - st;
+}
+
+// A link of the multi-RHS shared tile: its 18 reals (row-major, re/im
+// interleaved) in NV 16-byte vectors, vector k of site s at [k][s] so that a
+// warp reads 32 consecutive vectors (FP32: 5 float4, the last two reals
+// padding; FP64: 9 double2).
+template <typename T> struct LinkTile;
+template <> struct LinkTile<float> { using V = float4; static constexpr int NV = 5; };
+template <> struct LinkTile<double> { using V = double2; static constexpr int NV = 9; };
+
+template <typename T>
+__device__ __forceinline__ void tile_put(typename LinkTile<T>::V *lk, const cpx<T> (&U)[3][3])
+{
+    using LT = LinkTile<T>;
+    alignas(16) T r[16 / sizeof(T) * LT::NV];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            r[6 * a + 2 * c] = U[a][c].re;
+            r[6 * a + 2 * c + 1] = U[a][c].im;
+        }
+#pragma unroll
+    for (int k = 18; k < (int)(sizeof(r) / sizeof(T)); ++k) r[k] = T(0);
+#pragma unroll
+    for (int k = 0; k < LT::NV; ++k) lk[k * 32] = reinterpret_cast<const typename LT::V *>(r)[k];
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_get(const typename LinkTile<T>::V *lk, cpx<T> (&U)[3][3])
+{
+    using LT = LinkTile<T>;
+    typename LT::V v[LT::NV];
+#pragma unroll
+    for (int k = 0; k < LT::NV; ++k) v[k] = lk[k * 32];
+    const T *r = reinterpret_cast<const T *>(v);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) U[a][c] = {r[6 * a + 2 * c], r[6 * a + 2 * c + 1]};
+}
+
+template <int P, int MU, int S, bool FWD>
+__device__ __forceinline__ void hop_dir_smem(const char *in, int vh, int nb,
+                                             const typename LinkTile<typename Prec<P>::real>::V *lk,
+                                             cpx<typename Prec<P>::real> (&acc)[4][3])
+{
+    using T = typename Prec<P>::real;
+    T psi[24];
+    Spinor<P>::load(in, vh, nb, psi);
+    cpx<T> h0[3], h1[3];
+    project<MU, S>(psi, h0, h1);
+    cpx<T> U[3][3];
+    tile_get<T>(lk, U);
+    cpx<T> w0[3], w1[3];
+    su3_mul<FWD>(U, h0, w0);
+    su3_mul<FWD>(U, h1, w1);
+    accumulate<MU, S>(acc, w0, w1);
+}
+
+// Multi right-hand-side hop: a block owns 32 consecutive checkerboard sites
+// and all nrhs fields.  The 8 links of each site are loaded once (row 3
+// rebuilt once for 12-real storage) into shared memory, then warp y of the
+// block computes right-hand sides y, y + blockDim.y, ... from them, so links
+// cost 1/nrhs of their single-field traffic.  Spinors are read per field as in
+// hop_kernel.  blockDim = (32, RY).  Reduced precisions are compiled for 3
+// resident blocks of 256 threads per SM (at most 80 registers, no spills);
+// FP64 needs twice the registers per complex number and is left unbounded.
+//
+// Site order.  With zs = 0 block b takes checkerboard sites 32b .. 32b+31, so
+// the (z, t) slices of the lattice are visited t-major and a source spinor read
+// as the t+ neighbour of slice (z, t-1) is read again as the t- neighbour of
+// slice (z, t+1) 2*Lz slices later: with all nrhs fields per block that span
+// (inputs, outputs and links of 2*Lz slices) can exceed what L2 keeps.  With
+// 0 < zs < Lz the slices are visited in z-strips of width zs, t
+// outer and z inner within a strip, which brings that distance down to 2*zs
+// slices at the price of re-reading the two z-planes at each strip boundary.
+// The last strip is narrower when zs does not divide Lz.  j -> site is a
+// bijection of [0, vh) that keeps the order within a slice.
+__device__ __forceinline__ int mrhs_site(const HopArgs &A, int j, int zs)
+{
+    if (zs == 0) return j;
+    const int sxy = (A.L[0] >> 1) * A.L[1];
+    const int q = j / sxy;
+    const int off = j - q * sxy;
+    const int per_strip = zs * A.L[3];
+    const int k = q / per_strip;
+    const int w = min(zs, A.L[2] - k * zs);
+    const int l = q - k * per_strip;
+    const int t = l / w;
+    const int z = k * zs + (l - t * w);
+    return off + sxy * (z + A.L[2] * t);
+}
+
+template <int P, int RECON, bool DAG, bool HAS_X>
+__global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 3) hop_mrhs_kernel(const HopArgs A, const int nrhs, const int zs)
+{
+    using T = typename Prec<P>::real;
+    using LT = LinkTile<T>;
+    __shared__ typename LT::V lk[8][LT::NV][32];
+    __shared__ int nbs[9][32];   // rows 0..7: neighbours, row 8: the site itself (-1: none)
+    int p, blk;
+    if (A.nparity == 2) { p = blockIdx.x & 1; blk = blockIdx.x >> 1; }
+    else { p = A.parity0; blk = blockIdx.x; }
+    const int vh = A.vh;
+    const int s = threadIdx.x;
+    const int j = blk * 32 + s;
+    const bool active = j < vh;
+    const int i = active ? mrhs_site(A, j, zs) : -1;
+    const char *gf = p ? A.gauge[1] : A.gauge[0];
+    const char *gb = p ? A.gauge[0] : A.gauge[1];
+    const size_t lb = A.link_blk;
+    using LK = Link<link_prec(P), RECON>;
+    if (threadIdx.y == 0) {
+        nbs[8][s] = i;
+        if (active) {
+            int nb[8];
+            site_neighbours(A, p, i, nb);
+#pragma unroll
+            for (int d = 0; d < 8; ++d) nbs[d][s] = nb[d];
+        }
+    }
+    __syncthreads();
+    // stage the 8 links of the 32 sites: pair (direction d, site ss)
+    const int tid = threadIdx.y * 32 + threadIdx.x, nthr = 32 * blockDim.y;
+    for (int pr = tid; pr < 256; pr += nthr) {
+        const int d = pr >> 5, ss = pr & 31;
+        const int is = nbs[8][ss];
+        if (is < 0) continue;
+        const int mu = d & 3;
+        const char *lblk = d < 4 ? gf + mu * lb : gb + mu * lb;
+        const int li = d < 4 ? is : nbs[d][ss];
+        cpx<T> U[3][3];
+        LK::load(lblk, vh, li, U);
+        tile_put<T>(&lk[d][0][ss], U);
+    }
+    __syncthreads();
+    if (!active) return;
+    int nb[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) nb[d] = nbs[d][s];
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    const T a = (T)A.a, b = (T)A.b;
+    for (int rhs = threadIdx.y; rhs < nrhs; rhs += blockDim.y) {
+        const size_t roff = (size_t)rhs * A.rhs_stride;
+        const char *in = (p ? A.in[1] : A.in[0]) + roff;
+        cpx<T> acc[4][3];
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[sp][c] = {T(0), T(0)};
+        hop_dir_smem<P, 0, SB, false>(in, vh, nb[4], &lk[4][0][s], acc);
+        hop_dir_smem<P, 1, SB, false>(in, vh, nb[5], &lk[5][0][s], acc);
+        hop_dir_smem<P, 2, SB, false>(in, vh, nb[6], &lk[6][0][s], acc);
+        hop_dir_smem<P, 3, SB, false>(in, vh, nb[7], &lk[7][0][s], acc);
+        hop_dir_smem<P, 0, SF, true>(in, vh, nb[0], &lk[0][0][s], acc);
+        hop_dir_smem<P, 1, SF, true>(in, vh, nb[1], &lk[1][0][s], acc);
+        hop_dir_smem<P, 2, SF, true>(in, vh, nb[2], &lk[2][0][s], acc);
+        hop_dir_smem<P, 3, SF, true>(in, vh, nb[3], &lk[3][0][s], acc);
+        T o[24];
+        if constexpr (HAS_X) {
+            Spinor<P>::load((p ? A.x[1] : A.x[0]) + roff, vh, i, o);
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    o[6 * sp + 2 * c] = a * o[6 * sp + 2 * c] + b * acc[sp][c].re;
+                    o[6 * sp + 2 * c + 1] = a * o[6 * sp + 2 * c + 1] + b * acc[sp][c].im;
+                }
+        } else {
+#pragma unroll
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    o[6 * sp + 2 * c] = b * acc[sp][c].re;
+                    o[6 * sp + 2 * c + 1] = b * acc[sp][c].im;
+                }
+        }
+        Spinor<P>::store((p ? A.out[1] : A.out[0]) + roff, vh, i, o);
+    }
+}
+
+template <int P, int RECON, bool DAG, bool HX>
+void launch_hop_mrhs(const HopArgs &A, int nrhs, int threads, int zs, cudaStream_t s)
+{
+    const int ry = threads / 32;
+    const int per = (A.vh + 31) / 32;
+    if (zs <= 0 || zs >= A.L[2]) zs = 0;
+    wd_launch(hop_mrhs_kernel<P, RECON, DAG, HX>, dim3((unsigned)(per * A.nparity)), dim3(32, ry), 0, s, A, nrhs, zs);
+}
+
+} // namespace wd

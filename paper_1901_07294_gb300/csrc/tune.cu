@@ -12,7 +12,7 @@
 #include <sstream>
 #include <string>
 
-#include "dslash_impl.cuh"
+#include "dslash_launch.cuh"
 #include "wd_internal.h"
 
 namespace wd {
