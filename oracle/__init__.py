@@ -70,6 +70,10 @@ def _load():
             lib.oracle_cg.argtypes = [_DIMS, vp, ctypes.c_double, vp, vp, ctypes.c_double, ip,
                                       ctypes.POINTER(ctypes.c_double)]
             lib.oracle_cg.restype = ip
+            for fn in (lib.oracle_bicgstab, lib.oracle_solve_full):
+                fn.argtypes = [_DIMS, vp, ctypes.c_double, vp, vp, ctypes.c_double, ip,
+                               ctypes.POINTER(ctypes.c_double)]
+                fn.restype = ip
             _lib = lib
     return _lib
 
@@ -164,4 +168,34 @@ def cg(dims, links, mass: float, b, tol: float = 1e-10, maxiter: int = 20000):
     rel = ctypes.c_double(0.0)
     it = _load().oracle_cg(_dims(dims), links.ctypes.data, float(mass), b.ctypes.data, x.ctypes.data,
                            float(tol), int(maxiter), ctypes.byref(rel))
+    return x, int(it), float(rel.value)
+
+
+def bicgstab(dims, links, mass: float, b, tol: float = 1e-10, maxiter: int = 20000):
+    """Textbook FP64 BiCGStab (van der Vorst 1992) on Mhat x = b (even sites, x_0 = 0).
+
+    Returns (x, iterations, true relative residual |b - Mhat x| / |b|); iterations < 0
+    means not converged."""
+    v = _vol(dims)
+    links = _cf(links, (v, 4, 3, 3))
+    b = _cf(b, (v, 4, 3))
+    x = np.empty((v, 4, 3), dtype=np.complex128)
+    rel = ctypes.c_double(0.0)
+    it = _load().oracle_bicgstab(_dims(dims), links.ctypes.data, float(mass), b.ctypes.data, x.ctypes.data,
+                                 float(tol), int(maxiter), ctypes.byref(rel))
+    return x, int(it), float(rel.value)
+
+
+def solve_full(dims, links, mass: float, b, tol: float = 1e-10, maxiter: int = 20000):
+    """D x = b on the full lattice by even-odd reduction: b^_e = b_e + H_eo b_o / (2(m+4)),
+    BiCGStab on Mhat x_e = b^_e, x_o = (b_o + H_oe x_e / 2) / (m+4).
+
+    Returns (x, iterations, true relative residual |b - D x| / |b|)."""
+    v = _vol(dims)
+    links = _cf(links, (v, 4, 3, 3))
+    b = _cf(b, (v, 4, 3))
+    x = np.empty((v, 4, 3), dtype=np.complex128)
+    rel = ctypes.c_double(0.0)
+    it = _load().oracle_solve_full(_dims(dims), links.ctypes.data, float(mass), b.ctypes.data, x.ctypes.data,
+                                   float(tol), int(maxiter), ctypes.byref(rel))
     return x, int(it), float(rel.value)

@@ -279,3 +279,50 @@ def test_planted_sign_error_is_caught():
     wrong = (m + 4) * psi - 0.5 * oracle.hop(dims, U, psi, convention=1)
     dp = (m + np.sum(1 - np.cos(p))) * I4 + 1j * sum(G[mu] * np.sin(p[mu]) for mu in range(4))
     assert rel_max_err(wrong, plane_wave(dims, n, dp @ u)) > 1e-2
+
+
+def test_bicgstab_against_dense_solve():
+    """BiCGStab on Mhat (not Hermitian) reaches the dense solution of the Schur system."""
+    dims = (4, 2, 2, 4)
+    U = synth.gauge(dims, seed=1009)
+    m = 0.05
+    D = _dense_numpy(dims, U, m)
+    e, o = _eo_perm(dims)
+    schur = D[np.ix_(e, e)] - D[np.ix_(e, o)] @ np.linalg.solve(D[np.ix_(o, o)], D[np.ix_(o, e)])
+    b = synth.even_spinor(dims, seed=3002)
+    x, it, rel = oracle.bicgstab(dims, U, m, b, tol=1e-12)
+    assert it > 0 and rel <= 1e-12
+    xd = np.linalg.solve(schur, b.reshape(-1)[e])
+    assert rel_max_err(x.reshape(-1)[e], xd) < 1e-10
+    assert np.all(x.reshape(-1)[o] == 0)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 2, 2, 4)])
+def test_solve_full_against_dense_solve(dims):
+    """Source reduction, Schur solve and odd reconstruction together give D^{-1} b."""
+    U = synth.gauge(dims, seed=1010)
+    m = 0.1
+    D = _dense_numpy(dims, U, m)
+    b = synth.spinor(dims, seed=3003)
+    x, it, rel = oracle.solve_full(dims, U, m, b, tol=1e-12)
+    assert it > 0 and rel <= 1e-12
+    xd = np.linalg.solve(D, b.reshape(-1))
+    assert rel_max_err(x.reshape(-1), xd) < 1e-10
+
+
+def test_solve_full_free_field_inverse():
+    """Free field: D(p) = a + i gamma.s with a = m + sum(1 - cos p), s = sin p, so
+    D(p)^{-1} = (a - i gamma.s) / (a^2 + |s|^2) on a plane wave."""
+    dims = (8, 4, 4, 8)
+    m = 0.05
+    U = synth.unit_gauge(dims)
+    n = (3, 1, 2, 5)
+    p = 2 * np.pi * np.asarray(n) / np.asarray(dims)
+    a = m + np.sum(1 - np.cos(p))
+    gs = sum(G[mu] * np.sin(p[mu]) for mu in range(4))
+    dinv = (a * I4 - 1j * gs) / (a * a + np.sum(np.sin(p) ** 2))
+    u = _random_u(np.random.default_rng(21))
+    b = plane_wave(dims, n, u)
+    x, it, rel = oracle.solve_full(dims, U, m, b, tol=1e-12)
+    assert it > 0 and rel <= 1e-12
+    assert rel_max_err(x, plane_wave(dims, n, dinv @ u)) < 1e-10
