@@ -332,7 +332,8 @@ def run_gpu(args):
         _log("multi_rhs")
         mrhs = _mrhs_section(wd, torch, ctx, U, psi, peak)
         _log("blas")
-        blas = _blas_section(wd, torch, ctx, psi, peak, stream)
+        blas = _blas_section(wd, torch, ctx, psi, peak, stream,
+                             fp64_tflops=variants.get("device_peaks", {}).get("fp64_tflops"))
     batch = None
     if not args.no_cg:
         _log("batch")
@@ -341,10 +342,14 @@ def run_gpu(args):
     if not args.no_cg and not args.no_serving:
         _log("serving")
         serving = _serving_section(wd, torch, ctx)
+    solve = None
+    if not args.no_cg:
+        _log("solve")
+        solve = _solve_section(wd, torch, ctx)
     cg = None
     if not args.no_cg:
         _log("cg")
-        cg = _cg_section(wd, torch, ctx, with_cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline))
+        cg = _cg_section(wd, torch, ctx, with_cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline), peak=peak)
     _log("done")
 
     line = {
@@ -375,6 +380,7 @@ def run_gpu(args):
         "multi_rhs": mrhs,
         "blas": blas,
         "cg": cg,
+        "solve": solve,
         "batch": batch,
         "serving": serving,
     }
@@ -445,13 +451,17 @@ def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, fp64_tf
     return out
 
 
-def _blas_section(wd, torch, ctx, psi, peak, stream, reps=30):
+def _blas_section(wd, torch, ctx, psi, peak, stream, fp64_tflops=None, reps=30):
     """Per-call GB/s of the field conversions (pack, unpack, convert) and of the
     BLAS-1 kernels with FP64 reductions (norm2, dot, axpby) on 32^4 full-lattice
     fields.  Bytes are the algorithmic ones: each input element read once and each
     output element written once (sizes from wd.field_bytes, so FP16 includes its
     per-site scale).  Consecutive calls rotate over enough buffer sets that more
-    than twice the L2 size is touched between two uses of one buffer."""
+    than twice the L2 size is touched between two uses of one buffer.
+
+    FP64 arithmetic has its own floor on this part: FP64 instructions per site
+    (DFMA, DMUL, DADD; conversions not counted) over the measured FP64 FMA rate.
+    `bound` names the larger of the two floors and `frac_bound` = floor / time."""
     import numpy as np
 
     dims = DIMS
@@ -467,6 +477,9 @@ def _blas_section(wd, torch, ctx, psi, peak, stream, reps=30):
     def nsets(call_bytes):
         return int(min(16, max(2, int(np.ceil(2 * l2 / call_bytes)) + 1)))
 
+    dp_per_site = {"norm2_f64": 25, "dot_f64": 50, "axpby_f64": 48, "norm2_noalloc_f64": 25,
+                   "norm2_f32": 1, "norm2_f16": 1, "dot_f32": 2, "dot_f16": 2}
+
     def timed(name, call_bytes, make, fn):
         n = nsets(call_bytes)
         sets = [make(k) for k in range(n)]
@@ -480,9 +493,15 @@ def _blas_section(wd, torch, ctx, psi, peak, stream, reps=30):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         gbs = call_bytes / (ms * 1e-3) / 1e9
-        out[name] = {"ms": round(ms, 5), "bytes": int(call_bytes), "gbs": round(gbs, 1),
-                     "frac_hbm": round(gbs / peak, 4), "buffer_sets": n}
-        del sets
+        rec = {"ms": round(ms, 5), "bytes": int(call_bytes), "gbs": round(gbs, 1),
+               "frac_hbm": round(gbs / peak, 4), "buffer_sets": n}
+        t_hbm = call_bytes / (peak * 1e9)
+        dp = dp_per_site.get(name, 0)
+        t_alu = v * dp / (fp64_tflops * 1e12 / 2) if (fp64_tflops and dp) else 0.0
+        rec["fp64_instr_per_site"] = dp
+        rec["bound"] = "fp64_alu" if t_alu > t_hbm else "hbm"
+        rec["frac_bound"] = round(max(t_hbm, t_alu) / (ms * 1e-3), 4)
+        out[name] = rec
 
     def packed(p, k):
         f = wd.alloc_field(dims, full, p)
@@ -720,12 +739,68 @@ def _serving_section(wd, torch, ctx, n_main=600, n_sweep=150, warm=60):
     return out
 
 
-def _cg_section(wd, torch, ctx, with_cpu: bool):
+def _cg_iteration_bytes(inner_prec, recon):
+    """Bytes per even site that one CG iteration on Mhat^dagger Mhat moves by design
+    (every kernel's inputs read once, outputs written once): four even-odd hops
+    (spinor in and out, 8 links; the two Mhat hops also read their axpy term),
+    Re<p, Ap> with alpha (p, Ap), the fused update (r and x read and written, Ap and
+    p read; |r|^2) and p = r + beta p.  That is 19 passes over inner-precision
+    fields, two over the x accumulator (FP32 for the reduced precisions, FP64 for
+    FP64) and four link sets.  Reliable updates and the final true residual come
+    on top."""
+    fb = {0: 192, 1: 96, 2: 52, 3: 52}[inner_prec]
+    link_b = {0: 8, 1: 4, 2: 2, 3: 2}[inner_prec] * recon * 8
+    fx = 192 if inner_prec == 0 else 96
+    return 19 * fb + 4 * link_b + 2 * fx
+
+
+def _solve_section(wd, torch, ctx):
+    """Full-system solve D x = b on 24^3x48 (Gaussian source on all sites, seed 3201), tol 1e-10:
+    BiCGStab on Mhat vs CG on the normal equations, FP64 and mixed FP16 (reliable updates,
+    delta 0.01).  Best of 2 after one warm solve."""
+    import numpy as np
+
+    import synth
+    dims = (24, 24, 24, 48)
+    U = synth.gauge(dims, seed=1000 + 3)
+    b = synth.spinor(dims, seed=3201)
+    g = wd.Gauge(ctx, dims, U)
+    fb = wd.alloc_field(dims, wd.SITES_FULL, wd.F64)
+    wd.pack(ctx, dims, wd.SITES_FULL, wd.F64, torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
+    fx = wd.alloc_field(dims, wd.SITES_FULL, wd.F64)
+    out = {"lattice": list(dims), "tol": 1e-10, "mass": 0.1, "runs": {}}
+    runs = [("bicgstab_fp64", wd.SOLVER_BICGSTAB, dict(inner_prec=wd.F64)),
+            ("bicgstab_fp16", wd.SOLVER_BICGSTAB, dict(inner_prec=wd.F16, reliable=True, delta=0.01)),
+            ("bicgstab_fp32", wd.SOLVER_BICGSTAB, dict(inner_prec=wd.F32, reliable=True, delta=0.01)),
+            ("cgne_fp64", wd.SOLVER_CGNE, dict(inner_prec=wd.F64)),
+            ("cgne_fp16", wd.SOLVER_CGNE, dict(inner_prec=wd.F16, reliable=True, delta=0.01)),
+            ("cgne_fp16_graph", wd.SOLVER_CGNE, dict(inner_prec=wd.F16, reliable=True, delta=0.01, use_graph=True))]
+    for name, solver, kw in runs:
+        wd.wilson_solve(ctx, g, 0.1, fx, fb, tol=1e-10, solver=solver, autotune=True, **kw)
+        best = None
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = wd.wilson_solve(ctx, g, 0.1, fx, fb, tol=1e-10, solver=solver, **kw)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if best is None or ms < best[0]:
+                best = (ms, st)
+        ms, st = best
+        out["runs"][name] = {"seconds": round(ms / 1e3, 5), "iters": st["iters"],
+                             "reliable_updates": st["reliable_updates"], "true_rel_resid": st["true_rel_resid"]}
+    g.close()
+    return out
+
+
+def _cg_section(wd, torch, ctx, with_cpu: bool, peak: float):
     """Mixed-precision vs FP64 CG on the even-odd normal equations, 24^3x48, tol 1e-10."""
     import numpy as np
 
     import synth
     dims = (24, 24, 24, 48)
+    vh = int(np.prod(dims)) // 2
     U = synth.gauge(dims, seed=1000 + 3)
     b = synth.even_spinor(dims, seed=3001)
     g = wd.Gauge(ctx, dims, U)
@@ -756,9 +831,16 @@ def _cg_section(wd, torch, ctx, with_cpu: bool):
                 if best is None or ms < best[0]:
                     best = (ms, st)
             ms, st = best
-            out["runs"][f"m{mass}/{name}"] = {"seconds": round(ms / 1e3, 5), "iters": st["iters"],
-                                              "reliable_updates": st["reliable_updates"],
-                                              "true_rel_resid": st["true_rel_resid"]}
+            rec = {"seconds": round(ms / 1e3, 5), "iters": st["iters"],
+                   "reliable_updates": st["reliable_updates"], "true_rel_resid": st["true_rel_resid"]}
+            if st["iters"] > 0:
+                ps = kw["inner_prec"]
+                it_bytes = _cg_iteration_bytes(ps, kw.get("inner_recon", 18)) * vh
+                per_it = ms / 1e3 / st["iters"]
+                rec.update({"ms_per_iter": round(per_it * 1e3, 5), "iter_model_bytes": it_bytes,
+                            "iter_gbs": round(it_bytes / per_it / 1e9, 1),
+                            "iter_frac_hbm": round(it_bytes / per_it / 1e9 / peak, 4)})
+            out["runs"][f"m{mass}/{name}"] = rec
     for mass in (0.1, 0.05):
         t64 = out["runs"][f"m{mass}/fp64"]["seconds"]
         out[f"speedup_fp16_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/fp16"]["seconds"], 2)

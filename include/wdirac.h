@@ -255,6 +255,42 @@ typedef struct {
 int cg_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x_e, const void *b_e, double tol,
              const wd_cg_opts *opts, wd_cg_stats *stats, void *stream);
 
+/* ---- BiCGStab on Mhat and the full-system solve -----------------------------
+ * The paper names only CG (Sec. II-A); these are the steps either side of the
+ * CG path.
+ *
+ * bicgstab_solve: Mhat x_e = b_e on the even sites (Mhat as for cg_solve, not
+ * Hermitian) by BiCGStab (van der Vorst 1992), x_0 = 0, shadow residual b_e.
+ * x_e, b_e: even half fields in WD_F64 (device).  Converged when the FP64 true
+ * residual |b - Mhat x| / |b| <= tol.  Options as for cg_solve: inner_prec =
+ * WD_F64 plain FP64; otherwise the iterated vectors and operator use
+ * inner_prec storage with FP32 arithmetic, the solution, the true residual and
+ * all inner products FP64, and reliable = 1 replaces the iterated residual by
+ * the true one (FP64 operator) when it has dropped by `delta` since the last
+ * replacement (the Krylov state is kept), reliable = 0 restarts BiCGStab on the
+ * true residual each time (iterative refinement).  A breakdown (zero <r^, v>,
+ * omega or rho) restarts from the true residual.  use_graph is ignored.
+ * stats->iters counts BiCGStab iterations (two Mhat applications each).
+ *
+ * wilson_solve: D x = b on the full lattice, D = (m+4) - H/2.  x, b: full
+ * fields in WD_F64 (even half, then odd half; device).  Even-odd reduction:
+ * b^_e = b_e + H_eo b_o / (2(m+4)), solve Mhat x_e = b^_e to the relative
+ * residual tol |b| / |b^_e| (the even rows of D x = b then leave exactly that
+ * residual), then x_o = (b_o + H_oe x_e / 2) / (m+4), which satisfies the odd
+ * rows.  solver = WD_SOLVER_BICGSTAB: the Schur system by BiCGStab as above;
+ * WD_SOLVER_CGNE: by CG on Mhat^dagger Mhat x_e = Mhat^dagger b^_e (all
+ * cg_solve options, use_graph included), repeated on the Schur residual until
+ * it is small enough.  stats->true_rel_resid = |b - D x| / |b| with the FP64
+ * operator; WD_ENOCONV if it is above tol.
+ *
+ * Both: synchronous; workspace owned by the context; x must not alias b. */
+typedef enum { WD_SOLVER_CGNE = 0, WD_SOLVER_BICGSTAB = 1 } wd_solver;
+
+int bicgstab_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x_e, const void *b_e, double tol,
+                   const wd_cg_opts *opts, wd_cg_stats *stats, void *stream);
+int wilson_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x, const void *b, double tol, int solver,
+                 const wd_cg_opts *opts, wd_cg_stats *stats, void *stream);
+
 /* ---- Batches of solves (different lattices, masses, tolerances) --------------
  * Each descriptor is one cg_solve problem; its lattice comes from its gauge.
  * Modes:

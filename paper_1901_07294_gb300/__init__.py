@@ -58,6 +58,8 @@ _SIGS = {
     "wd_axpby": (_ip, [_vp, _DIMS, _ip, _ip, _dp, _vp, _dp, _vp, _vp]),
     "wd_convert": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _ip, _vp, _vp]),
     "cg_solve": (_ip, [_vp, _vp, _dp, _vp, _vp, _dp, _vp, _vp, _vp]),
+    "bicgstab_solve": (_ip, [_vp, _vp, _dp, _vp, _vp, _dp, _vp, _vp, _vp]),
+    "wilson_solve": (_ip, [_vp, _vp, _dp, _vp, _vp, _dp, _ip, _vp, _vp, _vp]),
     "wd_norm2_noalloc": (_ip, [_DIMS, _ip, _ip, _vp, _vp, _vp]),
     "wd_tune_dslash": (_ip, [_vp, _vp, _ip, _ip, _ip, _ip, _ip, _vp, _ip, ctypes.POINTER(_ip)]),
     "wd_tune_set_dslash": (_ip, [_vp, _vp, _ip, _ip, _ip, _ip, _ip, _ip, _ip]),
@@ -289,6 +291,48 @@ def cg_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-10, 
     st = CgStats()
     rc = load().cg_solve(ctx.handle, gauge.handle, float(mass), _ptr(x), _ptr(b), float(tol), ctypes.byref(opts),
                          ctypes.byref(st), _stream(stream))
+    if check:
+        _check(rc)
+    out = st.as_dict()
+    out["status"] = rc
+    return out
+
+
+SOLVER_CGNE, SOLVER_BICGSTAB = 0, 1
+
+
+def _solve_opts(inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune, use_graph):
+    return CgOpts(int(inner_prec), int(inner_recon), int(outer_recon), int(bool(reliable)), float(delta),
+                  int(maxiter), int(bool(autotune)), int(bool(use_graph)))
+
+
+def bicgstab_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-10, inner_prec: int = F64,
+                   inner_recon: int = 18, outer_recon: int = 18, reliable: bool = True, delta: float = 0.01,
+                   maxiter: int = 20000, autotune: bool = False, stream=None, check: bool = True) -> dict:
+    """Solve Mhat x = b on even half fields (FP64) by BiCGStab.  Returns the solve statistics;
+    raises WdError on failure unless check=False (then 'status' carries the code)."""
+    opts = _solve_opts(inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune, False)
+    st = CgStats()
+    rc = load().bicgstab_solve(ctx.handle, gauge.handle, float(mass), _ptr(x), _ptr(b), float(tol),
+                               ctypes.byref(opts), ctypes.byref(st), _stream(stream))
+    if check:
+        _check(rc)
+    out = st.as_dict()
+    out["status"] = rc
+    return out
+
+
+def wilson_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-10, solver: int = SOLVER_BICGSTAB,
+                 inner_prec: int = F64, inner_recon: int = 18, outer_recon: int = 18, reliable: bool = True,
+                 delta: float = 0.01, maxiter: int = 20000, autotune: bool = False, use_graph: bool = False,
+                 stream=None, check: bool = True) -> dict:
+    """Solve D x = b on full fields (FP64) by even-odd reduction; solver SOLVER_BICGSTAB
+    (BiCGStab on Mhat) or SOLVER_CGNE (CG on the normal equations).  Returns the solve
+    statistics (true_rel_resid = |b - D x| / |b|)."""
+    opts = _solve_opts(inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune, use_graph)
+    st = CgStats()
+    rc = load().wilson_solve(ctx.handle, gauge.handle, float(mass), _ptr(x), _ptr(b), float(tol), int(solver),
+                             ctypes.byref(opts), ctypes.byref(st), _stream(stream))
     if check:
         _check(rc)
     out = st.as_dict()

@@ -113,6 +113,71 @@ __global__ void unpack_spinor_kernel(const char *__restrict__ field, double *__r
     for (int k = 0; k < 12; ++k) dst[k] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
 }
 
+// Full-lattice fields (both parities) in lexicographic order: block b takes
+// sites [LEX_TILE*b, LEX_TILE*b + LEX_TILE), so the canonical array moves as
+// contiguous 16-byte chunks staged in shared memory (a site's 12 double2 at a
+// padded stride of 13, which keeps the 16-byte shared accesses conflict-free),
+// while the field side is read or written per site from its parity's planes.
+// (In checkerboard order the canonical side is touched at a 2-site stride, so
+// each cache line is filled in two passes that lie a half field apart.)
+constexpr int LEX_TILE = 128;
+constexpr int LEX_PAD = 13;
+
+__device__ __forceinline__ void lex_to_cb(const SiteMap &m, int64_t s, int &p, int &i)
+{
+    const int64_t r = s / m.Lx;
+    const int x = (int)(s - r * m.Lx);
+    const int y = (int)(r % m.Ly);
+    const int64_t r2 = r / m.Ly;
+    const int z = (int)(r2 % m.Lz);
+    const int t = (int)(r2 / m.Lz);
+    p = (x + y + z + t) & 1;
+    i = (int)(r * (m.Lx >> 1) + (x >> 1));
+}
+
+template <int P>
+__global__ void __launch_bounds__(LEX_TILE) pack_lex_kernel(const double *__restrict__ aos, char *__restrict__ field,
+                                                            SiteMap m, int64_t V)
+{
+    __shared__ double2 sh[LEX_TILE * LEX_PAD];
+    const int64_t s0 = (int64_t)blockIdx.x * LEX_TILE;
+    const int n = (int)min((int64_t)LEX_TILE, V - s0);
+    const double2 *src = reinterpret_cast<const double2 *>(aos + s0 * 24);
+    for (int c = threadIdx.x; c < n * 12; c += LEX_TILE) sh[(c / 12) * LEX_PAD + c % 12] = src[c];
+    __syncthreads();
+    if ((int)threadIdx.x >= n) return;
+    int p, i;
+    lex_to_cb(m, s0 + threadIdx.x, p, i);
+    typename Prec<P>::real v[24];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const double2 d = sh[threadIdx.x * LEX_PAD + k];
+        v[2 * k] = (typename Prec<P>::real)d.x;
+        v[2 * k + 1] = (typename Prec<P>::real)d.y;
+    }
+    Spinor<P>::store(field + p * m.half_bytes, m.vh, i, v);
+}
+
+template <int P>
+__global__ void __launch_bounds__(LEX_TILE) unpack_lex_kernel(const char *__restrict__ field, double *__restrict__ aos,
+                                                              SiteMap m, int64_t V)
+{
+    __shared__ double2 sh[LEX_TILE * LEX_PAD];
+    const int64_t s0 = (int64_t)blockIdx.x * LEX_TILE;
+    const int n = (int)min((int64_t)LEX_TILE, V - s0);
+    if ((int)threadIdx.x < n) {
+        int p, i;
+        lex_to_cb(m, s0 + threadIdx.x, p, i);
+        typename Prec<P>::real v[24];
+        Spinor<P>::load(field + p * m.half_bytes, m.vh, i, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) sh[threadIdx.x * LEX_PAD + k] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
+    }
+    __syncthreads();
+    double2 *dst = reinterpret_cast<double2 *>(aos + s0 * 24);
+    for (int c = threadIdx.x; c < n * 12; c += LEX_TILE) dst[c] = sh[(c / 12) * LEX_PAD + c % 12];
+}
+
 // ---- link pack -----------------------------------------------------------
 template <int P, int RECON>
 __global__ void pack_links_kernel(const double *__restrict__ links, char *__restrict__ out, SiteMap m, size_t blk)
@@ -227,6 +292,25 @@ int ctx_workspace(wd_ctx *ctx, size_t bytes, char **out)
     return WD_OK;
 }
 
+int ctx_aux_workspace(wd_ctx *ctx, size_t bytes, char **out)
+{
+    if (ctx->aux_bytes < bytes) {
+        DeviceGuard dg(ctx->device);
+        if (ctx->d_aux) {   // its users are synchronous, so it is idle here
+            cudaFree(ctx->d_aux);
+            ctx->d_aux = nullptr;
+            ctx->aux_bytes = 0;
+        }
+        if (cudaMalloc(&ctx->d_aux, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(WD_ENOMEM, "cudaMalloc of %zu bytes of solver workspace failed", bytes);
+        }
+        ctx->aux_bytes = bytes;
+    }
+    *out = ctx->d_aux;
+    return WD_OK;
+}
+
 int gauge_layout(const wd_gauge *gc, int prec, int recon, const char **out)
 {
     wd_gauge *g = const_cast<wd_gauge *>(gc);
@@ -337,6 +421,7 @@ int wd_ctx_destroy(wd_ctx *ctx)
         cudaFree(ctx->d_ticket);
         cudaFree(ctx->d_scal);
         cudaFree(ctx->d_work);
+        cudaFree(ctx->d_aux);
         if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     }
     delete ctx;
@@ -380,10 +465,22 @@ int wd_pack(wd_ctx *ctx, const int dims[4], int sites, int prec, const double *a
     Geometry g;
     SiteMap m;
     WD_TRY(pack_common(ctx, dims, sites, prec, aos, field, g, m));
-    const int threads = 256;
-    const int blocks = (int)(((int64_t)m.np * m.vh + threads - 1) / threads);
     cudaStream_t s = (cudaStream_t)stream;
     char *f = (char *)field;
+    if (m.np == 2) {
+        const int64_t V = 2 * (int64_t)m.vh;
+        const int blocks = (int)((V + LEX_TILE - 1) / LEX_TILE);
+        switch (prec) {
+        case WD_F64: pack_lex_kernel<PREC_F64><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
+        case WD_F32: pack_lex_kernel<PREC_F32><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
+        case WD_F16: pack_lex_kernel<PREC_F16><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
+        case WD_BF16: pack_lex_kernel<PREC_BF16><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
+        }
+        WD_CUDA_TRY(cudaGetLastError());
+        return WD_OK;
+    }
+    const int threads = 256;
+    const int blocks = (int)(((int64_t)m.np * m.vh + threads - 1) / threads);
     switch (prec) {
     case WD_F64: pack_spinor_kernel<PREC_F64><<<blocks, threads, 0, s>>>(aos, f, m); break;
     case WD_F32: pack_spinor_kernel<PREC_F32><<<blocks, threads, 0, s>>>(aos, f, m); break;
@@ -400,10 +497,22 @@ int wd_unpack(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *f
     Geometry g;
     SiteMap m;
     WD_TRY(pack_common(ctx, dims, sites, prec, field, aos, g, m));
-    const int threads = 256;
-    const int blocks = (int)(((int64_t)m.np * m.vh + threads - 1) / threads);
     cudaStream_t s = (cudaStream_t)stream;
     const char *f = (const char *)field;
+    if (m.np == 2) {
+        const int64_t V = 2 * (int64_t)m.vh;
+        const int blocks = (int)((V + LEX_TILE - 1) / LEX_TILE);
+        switch (prec) {
+        case WD_F64: unpack_lex_kernel<PREC_F64><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
+        case WD_F32: unpack_lex_kernel<PREC_F32><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
+        case WD_F16: unpack_lex_kernel<PREC_F16><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
+        case WD_BF16: unpack_lex_kernel<PREC_BF16><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
+        }
+        WD_CUDA_TRY(cudaGetLastError());
+        return WD_OK;
+    }
+    const int threads = 256;
+    const int blocks = (int)(((int64_t)m.np * m.vh + threads - 1) / threads);
     switch (prec) {
     case WD_F64: unpack_spinor_kernel<PREC_F64><<<blocks, threads, 0, s>>>(f, aos, m); break;
     case WD_F32: unpack_spinor_kernel<PREC_F32><<<blocks, threads, 0, s>>>(f, aos, m); break;

@@ -4,7 +4,8 @@
 // compute type of the field (FP32 for the 16/32-bit formats), each site's
 // contribution is added in FP64, then FP64 warp shuffles, a fixed-order sum
 // over the warps of the block, per-block partials in scratch memory, and the
-// last block to finish (atomic ticket) sums the partials in block order.  The
+// last block to finish (atomic ticket) sums the partials the same way (thread
+// t takes partials t, t+256, ...), so the order is fixed.  The
 // grid size depends only on the field size and the SM count, so repeated calls
 // give bitwise identical results.
 #pragma once
@@ -14,7 +15,7 @@
 namespace wd {
 
 constexpr int BLAS_THREADS = 256;
-constexpr int MAX_RED_BLOCKS = 1024;
+constexpr int MAX_RED_BLOCKS = 2048;
 constexpr int MAX_NR = 4;
 
 // Scratch used by one reduction: MAX_RED_BLOCKS*MAX_NR partials + a ticket.
@@ -72,19 +73,28 @@ __global__ void __launch_bounds__(BLAS_THREADS) blas_kernel(const Op op, const i
             last = (t == gridDim.x - 1);
         }
         __syncthreads();
-        if (last && warp == 0) {
+        if (last) {   // block-uniform: the whole last block sums the partials
             __threadfence();
             double s[NR];
 #pragma unroll
             for (int k = 0; k < NR; ++k) s[k] = 0.0;
-            for (int b = lane; b < (int)gridDim.x; b += 32)
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += BLAS_THREADS)
 #pragma unroll
                 for (int k = 0; k < NR; ++k) s[k] += __ldcg(rs.partials + b * NR + k);
 #pragma unroll
             for (int k = 0; k < NR; ++k)
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) s[k] += __shfl_down_sync(0xffffffffu, s[k], off);
-            if (lane == 0) {
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < NR; ++k) sm[warp][k] = s[k];
+            __syncthreads();
+            if (threadIdx.x == 0) {
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    s[k] = 0.0;
+                    for (int w = 0; w < BLAS_THREADS / 32; ++w) s[k] += sm[w][k];
+                }
                 op.finish(s);
                 *rs.ticket = 0u;   // ready for the next reduction
             }

@@ -16,10 +16,14 @@ template <int P> inline FieldRef<P> field_ref(const void *p, int vh)
     return FieldRef<P>{(char *)p, half_field_bytes(vh, P), vh};
 }
 
+// One site per thread up to 8 blocks of 256 threads per SM (the BLAS kernels
+// use at most 78 registers, most of them 32-48, so a full SM holds 4-8 blocks):
+// short fields finish in one wave and long ones loop with as many loads in
+// flight as the SM allows.
 inline int blas_grid(const wd_ctx *ctx, int nsite)
 {
     int want = (nsite + BLAS_THREADS - 1) / BLAS_THREADS;
-    int cap = 4 * (ctx->num_sms > 0 ? ctx->num_sms : 132);
+    int cap = 8 * (ctx->num_sms > 0 ? ctx->num_sms : 132);
     if (cap > MAX_RED_BLOCKS) cap = MAX_RED_BLOCKS;
     return want < cap ? (want > 0 ? want : 1) : cap;
 }

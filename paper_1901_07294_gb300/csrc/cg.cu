@@ -202,6 +202,18 @@ int cg_run_graph(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const cha
 
 } // namespace
 
+int cg_dispatch(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, double tol,
+                const wd_cg_opts &o, wd_cg_stats &st, cudaStream_t s)
+{
+    if (o.use_graph && o.inner_prec != WD_F64 && o.reliable) return cg_run_graph(ctx, g, mass, x, b, tol, o, st);
+    switch (o.inner_prec) {
+    case WD_F64: return cg_run<PREC_F64, PREC_F64>(ctx, g, mass, x, b, tol, o, st, s);
+    case WD_F32: return cg_run<PREC_F32, PREC_F32>(ctx, g, mass, x, b, tol, o, st, s);
+    case WD_F16: return cg_run<PREC_F16, PREC_F32>(ctx, g, mass, x, b, tol, o, st, s);
+    default: return cg_run<PREC_BF16, PREC_F32>(ctx, g, mass, x, b, tol, o, st, s);
+    }
+}
+
 } // namespace wd
 
 using namespace wd;
@@ -236,20 +248,7 @@ int cg_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x_e, const void 
     clear_error();
     wd_cg_stats st{};
     const auto t0 = std::chrono::steady_clock::now();
-    cudaStream_t s = (cudaStream_t)stream;
-    char *x = (char *)x_e;
-    const char *b = (const char *)b_e;
-    int rc;
-    if (opts->use_graph && opts->inner_prec != WD_F64 && opts->reliable) {
-        rc = cg_run_graph(ctx, g, mass, x, b, tol, *opts, st);
-    } else {
-        switch (opts->inner_prec) {
-        case WD_F64: rc = cg_run<PREC_F64, PREC_F64>(ctx, g, mass, x, b, tol, *opts, st, s); break;
-        case WD_F32: rc = cg_run<PREC_F32, PREC_F32>(ctx, g, mass, x, b, tol, *opts, st, s); break;
-        case WD_F16: rc = cg_run<PREC_F16, PREC_F32>(ctx, g, mass, x, b, tol, *opts, st, s); break;
-        default: rc = cg_run<PREC_BF16, PREC_F32>(ctx, g, mass, x, b, tol, *opts, st, s); break;
-        }
-    }
+    const int rc = cg_dispatch(ctx, g, mass, (char *)x_e, (const char *)b_e, tol, *opts, st, (cudaStream_t)stream);
     st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     st.status = rc;
     if (stats) *stats = st;

@@ -88,6 +88,24 @@ int eo_hop(const wd_gauge *g, int prec, int recon, void *out, const void *in, co
     return hop_launch(g->ctx, A, prec, recon, dagger ? 1 : 0, 1, s);
 }
 
+int full_hop(const wd_gauge *g, int prec, int recon, void *out, const void *in, double a, double b, cudaStream_t s)
+{
+    HopArgs A{};
+    WD_TRY(hop_setup(g, prec, recon, A));
+    const size_t half = half_field_bytes(A.vh, prec);
+    for (int p = 0; p < 2; ++p) {
+        A.in[p] = (const char *)in + (size_t)(1 - p) * half;
+        A.x[p] = (const char *)in + (size_t)p * half;
+        A.out[p] = (char *)out + (size_t)p * half;
+    }
+    A.rhs_stride = 2 * half;
+    A.nparity = 2;
+    A.parity0 = 0;
+    A.a = a;
+    A.b = b;
+    return hop_launch(g->ctx, A, prec, recon, 0, 1, s);
+}
+
 } // namespace wd
 
 using namespace wd;

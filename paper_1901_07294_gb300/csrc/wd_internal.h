@@ -79,6 +79,8 @@ struct wd_ctx {
     // solver workspace (device), grown on demand
     char *d_work = nullptr;
     size_t work_bytes = 0;
+    char *d_aux = nullptr;         // second workspace (ctx_aux_workspace)
+    size_t aux_bytes = 0;
     // launch-shape cache filled by the autotuner: problem key -> (threads, variant)
     std::mutex tune_mu;
     std::map<std::string, std::pair<int, int>> tuned;
@@ -99,6 +101,8 @@ constexpr int NSCAL = 64;
 // Even-odd hop on half fields: out_p = a x_p + b H^(d)_{p,1-p} in (see dslash_eo_apply).
 int eo_hop(const wd_gauge *g, int prec, int recon, void *out, const void *in, const void *x, int p, double a,
            double b, int dagger, cudaStream_t s);
+// Full-lattice hop on a full field: out = a in + b H in (both parities).
+int full_hop(const wd_gauge *g, int prec, int recon, void *out, const void *in, double a, double b, cudaStream_t s);
 // Launch configuration of a tunable kernel: the tuned one if the context has
 // it, else `def`.
 std::pair<int, int> tuned_config(wd_ctx *ctx, const std::string &key, std::pair<int, int> def);
@@ -107,6 +111,13 @@ void load_tune_file(wd_ctx *ctx);
 int hop_ensure_tuned(wd_ctx *ctx, const wd_gauge *g, int prec, int recon, int full, int with_x);
 // Solver workspace of at least `bytes` bytes (device), owned by the context.
 int ctx_workspace(wd_ctx *ctx, size_t bytes, char **out);
+// A second context-owned device buffer for drivers that call a solver (which
+// takes ctx_workspace) and need vectors of their own meanwhile.
+int ctx_aux_workspace(wd_ctx *ctx, size_t bytes, char **out);
+// The CG solve of cg_solve without its argument checks, locking and timing
+// (x, b: FP64 even half fields; the gauge layouts must be prepared).
+int cg_dispatch(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, double tol,
+                const wd_cg_opts &o, wd_cg_stats &st, cudaStream_t s);
 // Device pointer of the (prec, recon) layout, built on first use.
 int gauge_layout(const wd_gauge *g, int prec, int recon, const char **out);
 // Per-(parity, mu) block pointer inside a layout buffer.

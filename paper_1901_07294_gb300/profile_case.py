@@ -2,10 +2,14 @@
 
     python -m paper_1901_07294_gb300.profile_case --op eo --prec f32 --dims 32,32,32,32 --nrhs 12 \
         --launches 4 [--threads 128 --variant 3]
+    python -m paper_1901_07294_gb300.profile_case --op cg --prec f16 --dims 24,24,24,48 --launches 1
 
 Inputs are the seeded synthetic gauge field and source of the benchmark.  With
 --threads/--variant the launch shape is pinned; otherwise the library default
-is used (no tuning, so few launches precede the profiled ones).
+is used (no tuning, so few launches precede the profiled ones).  --op cg runs
+`launches` mixed-precision CG solves (inner precision --prec, reliable updates,
+delta 0.01, tol 1e-10, mass 0.1) on an even Gaussian source; --graph drives
+them with CUDA graphs.
 """
 from __future__ import annotations
 
@@ -16,7 +20,7 @@ import sys
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["full", "eo"], default="full")
+    ap.add_argument("--op", choices=["full", "eo", "cg"], default="full")
     ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16"], default="f32")
     ap.add_argument("--recon", type=int, default=18)
     ap.add_argument("--dims", default="32,32,32,32")
@@ -24,6 +28,7 @@ def main(argv=None) -> int:
     ap.add_argument("--launches", type=int, default=4)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--variant", type=int, default=-1)
+    ap.add_argument("--graph", action="store_true")
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -38,6 +43,18 @@ def main(argv=None) -> int:
     dims = tuple(int(t) for t in a.dims.split(","))
     ctx = wd.Context(0)
     g = wd.Gauge(ctx, dims, synth.gauge(dims, seed=1001))
+    if a.op == "cg":
+        b = synth.even_spinor(dims, seed=3001)
+        fb = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+        wd.pack(ctx, dims, wd.SITES_EVEN, wd.F64, torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
+        fx = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+        for _ in range(a.launches):
+            st = wd.cg_solve(ctx, g, 0.1, fx, fb, tol=1e-10, inner_prec=prec, inner_recon=a.recon, reliable=True,
+                             delta=0.01, use_graph=a.graph)
+        torch.cuda.synchronize()
+        print(f"profile_case: cg {a.prec} r{a.recon} {a.dims} solves={a.launches} iters={st['iters']} "
+              f"updates={st['reliable_updates']} seconds={st['seconds']:.4f} ok")
+        return 0
     g.prepare(prec, a.recon)
     full = a.op == "full"
     if a.threads and a.variant >= 0:

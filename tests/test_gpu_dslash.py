@@ -52,6 +52,35 @@ def test_pack_unpack_round_trip(ctx, prec):
     assert np.max(err) <= u * 1.01
 
 
+@pytest.mark.parametrize("prec", ALL_PREC)
+@pytest.mark.parametrize("dims", [(4, 6, 8, 10), (2, 2, 2, 6), (6, 6, 6, 6)])
+def test_full_pack_equals_half_packs(ctx, prec, dims):
+    """A full field is packed and unpacked in lexicographic tiles of 128 sites
+    (last tile partial for 48 and 1296 sites); half fields go site by site in
+    checkerboard order.  The two routes give the same bytes both ways."""
+    import torch
+    psi = synth.spinor(dims, seed=2013)
+    aos = torch.from_numpy(psi.view(np.float64).reshape(-1).copy()).cuda()
+    full = wd.alloc_field(dims, wd.SITES_FULL, prec)
+    wd.pack(ctx, dims, wd.SITES_FULL, prec, aos, full)
+    half = wd.field_bytes(dims, wd.SITES_EVEN, prec)
+    ev = wd.alloc_field(dims, wd.SITES_EVEN, prec)
+    od = wd.alloc_field(dims, wd.SITES_ODD, prec)
+    wd.pack(ctx, dims, wd.SITES_EVEN, prec, aos, ev)
+    wd.pack(ctx, dims, wd.SITES_ODD, prec, aos, od)
+    torch.cuda.synchronize()
+    assert torch.equal(full[:half], ev) and torch.equal(full[half:], od)
+    out_full = torch.full_like(aos, float("nan"))
+    wd.unpack(ctx, dims, wd.SITES_FULL, prec, full, out_full)
+    out_half = torch.full_like(aos, float("nan"))
+    wd.unpack(ctx, dims, wd.SITES_EVEN, prec, ev, out_half)
+    wd.unpack(ctx, dims, wd.SITES_ODD, prec, od, out_half)
+    torch.cuda.synchronize()
+    assert torch.equal(out_full, out_half)
+    if prec == wd.F64:
+        assert torch.equal(out_full, aos)
+
+
 def test_pack_half_fields_touch_only_their_parity(ctx):
     dims = (4, 4, 4, 6)
     psi = synth.spinor(dims, seed=2012)
