@@ -116,6 +116,15 @@ int wd_gauge_create(wd_ctx *ctx, const int dims[4], const double *links, int lin
  * missing layouts themselves; call this first when the operator call must not
  * allocate (for example before capturing a CUDA graph).  Synchronous. */
 int wd_gauge_prepare(wd_gauge *g, int prec, int recon);
+/* Boundary condition in t for every operator call with this gauge (and every
+ * solve): t_sign = +1 periodic (the default), -1 antiperiodic, i.e. a hop
+ * across the t boundary (forward from t = Lt-1, backward from t = 0) changes
+ * sign; the same as negating the links U_t on the slice t = Lt-1.  The paper
+ * does not fix the boundary conditions; this is the usual fermion choice in
+ * time.  Applied in the kernels (the stored links are unchanged).  Must not be
+ * called while operator calls or solves with this gauge are in flight.
+ * WD_EINVAL unless t_sign is +1 or -1. */
+int wd_gauge_set_boundary(wd_gauge *g, int t_sign);
 int wd_gauge_bytes(const wd_gauge *g, int prec, int recon, size_t *out);
 int wd_gauge_destroy(wd_gauge *g);
 

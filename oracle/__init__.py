@@ -199,3 +199,17 @@ def solve_full(dims, links, mass: float, b, tol: float = 1e-10, maxiter: int = 2
     it = _load().oracle_solve_full(_dims(dims), links.ctypes.data, float(mass), b.ctypes.data, x.ctypes.data,
                                    float(tol), int(maxiter), ctypes.byref(rel))
     return x, int(it), float(rel.value)
+
+
+def antiperiodic_links(dims, links) -> np.ndarray:
+    """Links for antiperiodic boundary conditions in t: the operator with these
+    links (and periodic wrap-around) is the antiperiodic one, because every hop
+    across the t boundary goes through a link U_t on the slice t = Lt-1
+    (forward from t = Lt-1 by U_t(x), backward from t = 0 by U_t(x - t)^dagger).
+    Pinned by the free-field plane waves with half-integer t momenta."""
+    v = _vol(dims)
+    out = _cf(links, (v, 4, 3, 3)).copy()
+    lt = int(dims[3])
+    slab = v // lt
+    out[(lt - 1) * slab:, 3] *= -1.0
+    return out

@@ -49,6 +49,7 @@ _SIGS = {
     "wd_unpack": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _vp, _vp]),
     "wd_gauge_create": (_ip, [_vp, _DIMS, _vp, _ip, ctypes.POINTER(_vp)]),
     "wd_gauge_prepare": (_ip, [_vp, _ip, _ip]),
+    "wd_gauge_set_boundary": (_ip, [_vp, _ip]),
     "wd_gauge_bytes": (_ip, [_vp, _ip, _ip, ctypes.POINTER(_sz)]),
     "wd_gauge_destroy": (_ip, [_vp]),
     "dslash_apply": (_ip, [_vp, _vp, _vp, _vp, _dp, _ip, _ip, _ip, _vp]),
@@ -224,6 +225,10 @@ class Gauge:
 
     def prepare(self, prec: int, recon: int) -> None:
         _check(load().wd_gauge_prepare(self._h, int(prec), int(recon)))
+
+    def set_boundary(self, t_sign: int) -> None:
+        """+1: periodic in t (default); -1: antiperiodic in t."""
+        _check(load().wd_gauge_set_boundary(self._h, int(t_sign)))
 
     def nbytes(self, prec: int, recon: int) -> int:
         out = _sz()

@@ -552,6 +552,15 @@ int wd_gauge_create(wd_ctx *ctx, const int dims[4], const double *links, int lin
     return WD_OK;
 }
 
+int wd_gauge_set_boundary(wd_gauge *g, int t_sign)
+{
+    clear_error();
+    if (!g) return set_error(WD_EINVAL, "gauge is NULL");
+    if (t_sign != 1 && t_sign != -1) return set_error(WD_EINVAL, "t_sign = %d must be +1 or -1", t_sign);
+    g->t_sign = t_sign;
+    return WD_OK;
+}
+
 int wd_gauge_prepare(wd_gauge *g, int prec, int recon)
 {
     clear_error();

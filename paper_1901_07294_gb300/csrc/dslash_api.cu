@@ -69,6 +69,7 @@ int hop_setup(const wd_gauge *g, int prec, int recon, HopArgs &A)
     A.gauge[1] = base + 4 * A.link_blk;
     for (int mu = 0; mu < 4; ++mu) A.L[mu] = g->geo.L[mu];
     A.vh = vh;
+    A.tneg = g->t_sign < 0 ? 1 : 0;
     return WD_OK;
 }
 

@@ -28,6 +28,7 @@ struct HopArgs {
     int vh;
     int nparity;          // 2: blocks alternate parity (full operator); 1: parity0 only
     int parity0;
+    int tneg;             // 1: antiperiodic in t (hops across the t boundary change sign)
     double a, b;
 };
 
@@ -100,9 +101,11 @@ __device__ __forceinline__ void su3_mul(const cpx<T> (&U)[3][3], const cpx<T> (&
 
 // One direction.  For 16-bit storage the neighbour's per-site scale is applied
 // to the 12 reals of U h (the operation is linear) rather than to its 24
-// stored reals.
+// stored reals.  neg: the hop crosses an antiperiodic boundary, U h changes
+// sign (done here rather than in the stored links, whose 12-real form
+// rebuilds row 3 assuming det U = 1).
 template <int P, int RECON, int MU, int S, bool FWD>
-__device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh, int nb, int li,
+__device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh, int nb, int li, bool neg,
                                         cpx<typename Prec<P>::real> (&acc)[4][3])
 {
     using T = typename Prec<P>::real;
@@ -116,10 +119,19 @@ __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh
     su3_mul<FWD>(U, h0, w0);
     su3_mul<FWD>(U, h1, w1);
     if constexpr (Prec<P>::scaled) {
+        const T f = neg ? -sc : sc;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            w0[c].re *= sc; w0[c].im *= sc;
-            w1[c].re *= sc; w1[c].im *= sc;
+            w0[c].re *= f; w0[c].im *= f;
+            w1[c].re *= f; w1[c].im *= f;
+        }
+    } else {
+        if (neg) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                w0[c].re = -w0[c].re; w0[c].im = -w0[c].im;
+                w1[c].re = -w1[c].re; w1[c].im = -w1[c].im;
+            }
         }
     }
     accumulate<MU, S>(acc, w0, w1);
@@ -165,6 +177,7 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
     const int zb = (z == 0) ? i + (Lz - 1) * sz : i - sz;
     const int tf = (t == Lt - 1) ? i - (Lt - 1) * st : i + st;
     const int tb = (t == 0) ? i + (Lt - 1) * st : i - st;
+    const bool ntf = A.tneg && t == Lt - 1, ntb = A.tneg && t == 0;
 
     constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF gamma
     constexpr int SB = -SF;             // backward projector
@@ -178,14 +191,14 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
 
     using LK = Link<link_prec(P), RECON>;
     if constexpr (PF == 0) {
-        hop_dir<P, RECON, 0, SF, true>(in, gf + 0 * lb, vh, xf, i, acc);
-        hop_dir<P, RECON, 0, SB, false>(in, gb + 0 * lb, vh, xb, xb, acc);
-        hop_dir<P, RECON, 1, SF, true>(in, gf + 1 * lb, vh, yf, i, acc);
-        hop_dir<P, RECON, 1, SB, false>(in, gb + 1 * lb, vh, yb, yb, acc);
-        hop_dir<P, RECON, 2, SF, true>(in, gf + 2 * lb, vh, zf, i, acc);
-        hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, acc);
-        hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, acc);
-        hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, acc);
+        hop_dir<P, RECON, 0, SF, true>(in, gf + 0 * lb, vh, xf, i, false, acc);
+        hop_dir<P, RECON, 0, SB, false>(in, gb + 0 * lb, vh, xb, xb, false, acc);
+        hop_dir<P, RECON, 1, SF, true>(in, gf + 1 * lb, vh, yf, i, false, acc);
+        hop_dir<P, RECON, 1, SB, false>(in, gb + 1 * lb, vh, yb, yb, false, acc);
+        hop_dir<P, RECON, 2, SF, true>(in, gf + 2 * lb, vh, zf, i, false, acc);
+        hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, false, acc);
+        hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
+        hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
     } else {
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) LK::prefetch(gf + mu * lb, vh, i);
@@ -196,14 +209,14 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
             LK::prefetch(gb + 2 * lb, vh, zb);
             LK::prefetch(gb + 3 * lb, vh, tb);
         }
-        hop_dir<P, RECON, 0, SB, false>(in, gb + 0 * lb, vh, xb, xb, acc);
-        hop_dir<P, RECON, 1, SB, false>(in, gb + 1 * lb, vh, yb, yb, acc);
-        hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, acc);
-        hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, acc);
-        hop_dir<P, RECON, 0, SF, true>(in, gf + 0 * lb, vh, xf, i, acc);
-        hop_dir<P, RECON, 1, SF, true>(in, gf + 1 * lb, vh, yf, i, acc);
-        hop_dir<P, RECON, 2, SF, true>(in, gf + 2 * lb, vh, zf, i, acc);
-        hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, acc);
+        hop_dir<P, RECON, 0, SB, false>(in, gb + 0 * lb, vh, xb, xb, false, acc);
+        hop_dir<P, RECON, 1, SB, false>(in, gb + 1 * lb, vh, yb, yb, false, acc);
+        hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, false, acc);
+        hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
+        hop_dir<P, RECON, 0, SF, true>(in, gf + 0 * lb, vh, xf, i, false, acc);
+        hop_dir<P, RECON, 1, SF, true>(in, gf + 1 * lb, vh, yf, i, false, acc);
+        hop_dir<P, RECON, 2, SF, true>(in, gf + 2 * lb, vh, zf, i, false, acc);
+        hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
     }
 
     const T a = (T)A.a, b = (T)A.b;

@@ -74,7 +74,7 @@ __device__ __forceinline__ void tile_get(const typename LinkTile<T>::V *lk, cpx<
 
 template <int P, int MU, int S, bool FWD>
 __device__ __forceinline__ void hop_dir_smem(const char *in, int vh, int nb,
-                                             const typename LinkTile<typename Prec<P>::real>::V *lk,
+                                             const typename LinkTile<typename Prec<P>::real>::V *lk, bool neg,
                                              cpx<typename Prec<P>::real> (&acc)[4][3])
 {
     using T = typename Prec<P>::real;
@@ -87,6 +87,13 @@ __device__ __forceinline__ void hop_dir_smem(const char *in, int vh, int nb,
     cpx<T> w0[3], w1[3];
     su3_mul<FWD>(U, h0, w0);
     su3_mul<FWD>(U, h1, w1);
+    if (neg) {   // hop across an antiperiodic boundary
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            w0[c].re = -w0[c].re; w0[c].im = -w0[c].im;
+            w1[c].re = -w1[c].re; w1[c].im = -w1[c].im;
+        }
+    }
     accumulate<MU, S>(acc, w0, w1);
 }
 
@@ -173,6 +180,9 @@ __global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 3) hop_mrhs_kernel(co
     for (int d = 0; d < 8; ++d) nb[d] = nbs[d][s];
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
+    // a t hop wraps (t = Lt-1 forward, t = 0 backward) exactly when the
+    // neighbour's checkerboard index falls below / above the site's
+    const bool ntf = A.tneg && nb[3] < i, ntb = A.tneg && nb[7] > i;
     const T a = (T)A.a, b = (T)A.b;
     for (int rhs = threadIdx.y; rhs < nrhs; rhs += blockDim.y) {
         const size_t roff = (size_t)rhs * A.rhs_stride;
@@ -182,14 +192,14 @@ __global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 3) hop_mrhs_kernel(co
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc[sp][c] = {T(0), T(0)};
-        hop_dir_smem<P, 0, SB, false>(in, vh, nb[4], &lk[4][0][s], acc);
-        hop_dir_smem<P, 1, SB, false>(in, vh, nb[5], &lk[5][0][s], acc);
-        hop_dir_smem<P, 2, SB, false>(in, vh, nb[6], &lk[6][0][s], acc);
-        hop_dir_smem<P, 3, SB, false>(in, vh, nb[7], &lk[7][0][s], acc);
-        hop_dir_smem<P, 0, SF, true>(in, vh, nb[0], &lk[0][0][s], acc);
-        hop_dir_smem<P, 1, SF, true>(in, vh, nb[1], &lk[1][0][s], acc);
-        hop_dir_smem<P, 2, SF, true>(in, vh, nb[2], &lk[2][0][s], acc);
-        hop_dir_smem<P, 3, SF, true>(in, vh, nb[3], &lk[3][0][s], acc);
+        hop_dir_smem<P, 0, SB, false>(in, vh, nb[4], &lk[4][0][s], false, acc);
+        hop_dir_smem<P, 1, SB, false>(in, vh, nb[5], &lk[5][0][s], false, acc);
+        hop_dir_smem<P, 2, SB, false>(in, vh, nb[6], &lk[6][0][s], false, acc);
+        hop_dir_smem<P, 3, SB, false>(in, vh, nb[7], &lk[7][0][s], ntb, acc);
+        hop_dir_smem<P, 0, SF, true>(in, vh, nb[0], &lk[0][0][s], false, acc);
+        hop_dir_smem<P, 1, SF, true>(in, vh, nb[1], &lk[1][0][s], false, acc);
+        hop_dir_smem<P, 2, SF, true>(in, vh, nb[2], &lk[2][0][s], false, acc);
+        hop_dir_smem<P, 3, SF, true>(in, vh, nb[3], &lk[3][0][s], ntf, acc);
         T o[24];
         if constexpr (HAS_X) {
             Spinor<P>::load((p ? A.x[1] : A.x[0]) + roff, vh, i, o);

@@ -92,6 +92,7 @@ struct wd_gauge {
     int device = 0;                // kept here so destruction does not need ctx
     wd::Geometry geo{};
     double *canonical = nullptr;   // device, FP64 canonical links (V*4*18 doubles)
+    int t_sign = 1;                // +1 periodic in t, -1 antiperiodic
     std::mutex mu;
     std::map<std::pair<int, int>, char *> layouts;  // (prec, recon) -> device buffer
 };

@@ -326,3 +326,45 @@ def test_solve_full_free_field_inverse():
     x, it, rel = oracle.solve_full(dims, U, m, b, tol=1e-12)
     assert it > 0 and rel <= 1e-12
     assert rel_max_err(x, plane_wave(dims, n, dinv @ u)) < 1e-10
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 2, 6), (2, 2, 2, 2)])
+def test_antiperiodic_free_field_half_integer_momenta(dims):
+    """Antiperiodic in t: exp(i p.x) u with p_t = (2 n_t + 1) pi / L_t changes sign
+    around t and is an eigenvector with the same symbol D(p) = a + i gamma.s."""
+    m = 0.1
+    U = oracle.antiperiodic_links(dims, synth.unit_gauge(dims))
+    n = (1, 1, 0, 0.5)                     # p_t = pi / L_t
+    p = 2 * np.pi * np.asarray(n) / np.asarray(dims)
+    u = _random_u(np.random.default_rng(41))
+    psi = plane_wave(dims, n, u)
+    dp = (m + np.sum(1 - np.cos(p))) * I4 + 1j * sum(G[mu] * np.sin(p[mu]) for mu in range(4))
+    assert rel_max_err(oracle.dirac(dims, U, psi, m), plane_wave(dims, n, dp @ u)) < 1e-13
+    # the periodic operator does not have this eigenvector
+    assert rel_max_err(oracle.dirac(dims, synth.unit_gauge(dims), psi, m), plane_wave(dims, n, dp @ u)) > 1e-2
+
+
+def test_antiperiodic_links_touch_only_the_last_time_slice():
+    dims = (4, 2, 2, 6)
+    U = synth.gauge(dims, seed=1011)
+    A = oracle.antiperiodic_links(dims, U)
+    t = coords(dims)[:, 3]
+    assert np.array_equal(A[t < 5], U[t < 5])
+    assert np.array_equal(A[t == 5][:, :3], U[t == 5][:, :3])
+    assert np.array_equal(A[t == 5][:, 3], -U[t == 5][:, 3])
+
+
+def test_antiperiodic_full_solve_free_field():
+    """D^{-1} on an antiperiodic plane wave is (a - i gamma.s) / (a^2 + |s|^2)."""
+    dims = (4, 4, 4, 8)
+    m = 0.05
+    U = oracle.antiperiodic_links(dims, synth.unit_gauge(dims))
+    n = (1, 3, 2, 2.5)
+    p = 2 * np.pi * np.asarray(n) / np.asarray(dims)
+    a = m + np.sum(1 - np.cos(p))
+    gs = sum(G[mu] * np.sin(p[mu]) for mu in range(4))
+    dinv = (a * I4 - 1j * gs) / (a * a + np.sum(np.sin(p) ** 2))
+    u = _random_u(np.random.default_rng(42))
+    x, it, rel = oracle.solve_full(dims, U, m, plane_wave(dims, n, u), tol=1e-12)
+    assert it > 0 and rel <= 1e-12
+    assert rel_max_err(x, plane_wave(dims, n, dinv @ u)) < 1e-10
