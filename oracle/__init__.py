@@ -213,3 +213,33 @@ def antiperiodic_links(dims, links) -> np.ndarray:
     slab = v // lt
     out[(lt - 1) * slab:, 3] *= -1.0
     return out
+
+
+# Element-wise products of Sec. IV (and the complex multiply-add forms of
+# Sec. III-D), written out on interleaved (re, im) float64 arrays.
+STREAM_REAL_MUL, STREAM_CPLX_MUL, STREAM_CPLX_CONJ_MUL, STREAM_CPLX_MADD, STREAM_CPLX_CONJ_MADD = range(5)
+
+
+def stream_mul(kind: int, x, y, z=None) -> np.ndarray:
+    """kind 0: z_i = x_i y_i on real float64 arrays;
+    kind 1: z = x y, 2: z = conj(x) y, 3: z = z + x y, 4: z = z + conj(x) y on complex
+    numbers stored as interleaved (re, im) float64 pairs.  Returns the new z."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    if kind == STREAM_REAL_MUL:
+        return x * y
+    xr, xi = x[0::2], x[1::2]
+    yr, yi = y[0::2], y[1::2]
+    if kind in (STREAM_CPLX_CONJ_MUL, STREAM_CPLX_CONJ_MADD):
+        xi = -xi
+    re = xr * yr - xi * yi
+    im = xr * yi + xi * yr
+    out = np.empty_like(x)
+    if kind in (STREAM_CPLX_MADD, STREAM_CPLX_CONJ_MADD):
+        z = np.asarray(z, dtype=np.float64)
+        out[0::2] = z[0::2] + re
+        out[1::2] = z[1::2] + im
+    else:
+        out[0::2] = re
+        out[1::2] = im
+    return out

@@ -368,3 +368,33 @@ def test_antiperiodic_full_solve_free_field():
     x, it, rel = oracle.solve_full(dims, U, m, plane_wave(dims, n, u), tol=1e-12)
     assert it > 0 and rel <= 1e-12
     assert rel_max_err(x, plane_wave(dims, n, dinv @ u)) < 1e-10
+
+
+def test_stream_products_against_python_complex():
+    """The written-out complex products agree with Python's own complex arithmetic
+    (an independent implementation) element by element, and the identities
+    conj(x) x = |x|^2, x i = (-Im x, Re x) hold."""
+    rng = np.random.default_rng(51)
+    n = 257
+    x = rng.standard_normal(2 * n)
+    y = rng.standard_normal(2 * n)
+    z = rng.standard_normal(2 * n)
+    cx = [complex(x[2 * k], x[2 * k + 1]) for k in range(n)]
+    cy = [complex(y[2 * k], y[2 * k + 1]) for k in range(n)]
+    cz = [complex(z[2 * k], z[2 * k + 1]) for k in range(n)]
+    expect = {
+        oracle.STREAM_CPLX_MUL: [a * b for a, b in zip(cx, cy)],
+        oracle.STREAM_CPLX_CONJ_MUL: [a.conjugate() * b for a, b in zip(cx, cy)],
+        oracle.STREAM_CPLX_MADD: [c + a * b for a, b, c in zip(cx, cy, cz)],
+        oracle.STREAM_CPLX_CONJ_MADD: [c + a.conjugate() * b for a, b, c in zip(cx, cy, cz)],
+    }
+    for kind, ref in expect.items():
+        got = oracle.stream_mul(kind, x, y, z)
+        ref = np.array([[v.real, v.imag] for v in ref]).reshape(-1)
+        assert np.max(np.abs(got - ref)) <= 1e-15 * np.max(np.abs(ref)), kind
+    assert np.array_equal(oracle.stream_mul(oracle.STREAM_REAL_MUL, x, y), np.array([a * b for a, b in zip(x, y)]))
+    xx = oracle.stream_mul(oracle.STREAM_CPLX_CONJ_MUL, x, x)
+    assert np.all(xx[1::2] == 0) and np.allclose(xx[0::2], x[0::2] ** 2 + x[1::2] ** 2, rtol=1e-15)
+    i_unit = np.tile([0.0, 1.0], n)
+    xi = oracle.stream_mul(oracle.STREAM_CPLX_MUL, x, i_unit)
+    assert np.array_equal(xi[0::2], -x[1::2]) and np.array_equal(xi[1::2], x[0::2])
