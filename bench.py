@@ -328,12 +328,16 @@ def run_gpu(args):
         variants["device_peaks"] = device_peaks
     mrhs = None
     blas = None
+    streams = None
     if not args.no_variants:
         _log("multi_rhs")
         mrhs = _mrhs_section(wd, torch, ctx, U, psi, peak)
         _log("blas")
         blas = _blas_section(wd, torch, ctx, psi, peak, stream,
                              fp64_tflops=variants.get("device_peaks", {}).get("fp64_tflops"))
+        _log("stream")
+        streams = _stream_section(wd, torch, ctx, peak, stream,
+                                  fp64_tflops=variants.get("device_peaks", {}).get("fp64_tflops"))
     batch = None
     if not args.no_cg:
         _log("batch")
@@ -379,6 +383,7 @@ def run_gpu(args):
         "variants": variants,
         "multi_rhs": mrhs,
         "blas": blas,
+        "stream": streams,
         "cg": cg,
         "solve": solve,
         "batch": batch,
@@ -529,6 +534,42 @@ def _blas_section(wd, torch, ctx, psi, peak, stream, fp64_tflops=None, reps=30):
               lambda st, pi=pi, po=po: wd.convert(ctx, dims, full, po, st[1], pi, st[0], stream=stream))
     timed("norm2_noalloc_f64", fb[wd.F64], lambda k: packed(wd.F64, k),
           lambda f: wd.norm2_noalloc(dims, full, wd.F64, f, res, stream=stream))
+    return out
+
+
+def _stream_section(wd, torch, ctx, peak, stream, fp64_tflops=None, reps=20):
+    """Element-wise products of Sec. IV on 2^26 complex numbers (1 GiB per FP64 array; 2^27 reals
+    for the real product), inputs N(0,1) generated on the device: GB/s of the algorithmic bytes
+    (inputs read once, output written once) and the binding floor: HBM bytes over the measured
+    copy bandwidth or FP64 instructions (1 per real product, 4 per complex one) over the measured
+    FP64 FMA rate."""
+    n = 1 << 26
+    gen = torch.Generator(device="cuda").manual_seed(6001)
+    x = torch.randn(2 * n, dtype=torch.float64, device="cuda", generator=gen)
+    y = torch.randn(2 * n, dtype=torch.float64, device="cuda", generator=gen)
+    z = torch.randn(2 * n, dtype=torch.float64, device="cuda", generator=gen)
+    kinds = [("real_mul", wd.STREAM_REAL_MUL, 2 * n, 24, 1), ("cplx_mul", wd.STREAM_CPLX_MUL, n, 48, 4),
+             ("cplx_conj_mul", wd.STREAM_CPLX_CONJ_MUL, n, 48, 4), ("cplx_madd", wd.STREAM_CPLX_MADD, n, 64, 4),
+             ("cplx_conj_madd", wd.STREAM_CPLX_CONJ_MADD, n, 64, 4)]
+    out = {"elements_complex": n, "array_bytes": 16 * n}
+    for name, kind, count, bpe, dp in kinds:
+        for _ in range(3):
+            wd.stream_mul(ctx, kind, count, x, y, z, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            wd.stream_mul(ctx, kind, count, x, y, z, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        nbytes = count * bpe
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        t_hbm = nbytes / (peak * 1e9)
+        t_alu = count * dp / (fp64_tflops * 1e12 / 2) if fp64_tflops else 0.0
+        out[name] = {"ms": round(ms, 5), "bytes": nbytes, "gbs": round(gbs, 1), "frac_hbm": round(gbs / peak, 4),
+                     "fp64_instr_per_element": dp, "bound": "fp64_alu" if t_alu > t_hbm else "hbm",
+                     "frac_bound": round(max(t_hbm, t_alu) / (ms * 1e-3), 4)}
+    del x, y, z
     return out
 
 

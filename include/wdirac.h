@@ -142,6 +142,15 @@ int dslash_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, doub
                  int nrhs, int prec, int recon, void *stream);
 
 /*
+ * out = D^dagger in = gamma5 D gamma5 in = (m+4) in - (gamma5 H gamma5) in / 2.
+ * gamma5 H gamma5 is the hopping term of Sec. II-A, Eq. (1) exactly as printed
+ * (projector 1 + gamma forward, 1 - gamma backward), so this is also the
+ * operator in the paper's sign convention.  Arguments as for dslash_apply.
+ */
+int dslash_apply_dagger(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, double mass,
+                        int nrhs, int prec, int recon, void *stream);
+
+/*
  * Even-odd hopping block with fused axpby:
  *     out_p = a * x_p + b * H^(d)_{p,1-p} in_{1-p},   p = out_parity,
  * where H_{p,1-p} is H restricted to output sites of parity p (its inputs
@@ -223,6 +232,28 @@ int wd_convert(wd_ctx *ctx, const int dims[4], int sites, int prec_out, void *ou
  * equal wd_norm2's up to FP64 summation order.  `result` is device memory. */
 int wd_norm2_noalloc(const int dims[4], int sites, int prec, const void *x, double *result,
                      void *stream);
+
+/* ---- Element-wise products (Sec. IV examples; Sec. III-D complex forms) ----
+ * z_i = f(x_i, y_i[, z_i]) for i < n on device arrays of FP64:
+ *   WD_STREAM_REAL_MUL        z = x y        n reals (Sec. IV, real arithmetic)
+ *   WD_STREAM_CPLX_MUL        z = x y        n complex numbers stored as
+ *   WD_STREAM_CPLX_CONJ_MUL   z = conj(x) y  interleaved (re, im) pairs
+ *   WD_STREAM_CPLX_MADD       z = z + x y    (Sec. IV, complex arithmetic; the
+ *   WD_STREAM_CPLX_CONJ_MADD  z = z + conj(x) y  FCMLA rotation pairs of III-D)
+ * Complex products use FMA: re = fma(xr, yr, -(xi yi)), im = fma(xr, yi, xi yr)
+ * (the conjugate forms with -xi), so results can differ from a plain
+ * multiply-then-add in the last bit.  Arrays must be 16-byte aligned; z may
+ * equal x or y (element-wise in place).  Asynchronous on `stream`; n = 0 is a
+ * no-op.  HBM stream kernels: also the calibration of the memory roofline. */
+typedef enum {
+    WD_STREAM_REAL_MUL = 0,
+    WD_STREAM_CPLX_MUL = 1,
+    WD_STREAM_CPLX_CONJ_MUL = 2,
+    WD_STREAM_CPLX_MADD = 3,
+    WD_STREAM_CPLX_CONJ_MADD = 4
+} wd_stream_kind;
+
+int wd_stream_mul(wd_ctx *ctx, int kind, size_t n, const double *x, const double *y, double *z, void *stream);
 
 /* ---- Conjugate gradient (Sec. II-A: CG solves the Dirac system) ------------
  * Solves  Mhat^dagger Mhat x = b  on the even sites, where

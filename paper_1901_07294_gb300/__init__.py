@@ -49,10 +49,12 @@ _SIGS = {
     "wd_unpack": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _vp, _vp]),
     "wd_gauge_create": (_ip, [_vp, _DIMS, _vp, _ip, ctypes.POINTER(_vp)]),
     "wd_gauge_prepare": (_ip, [_vp, _ip, _ip]),
+    "wd_stream_mul": (_ip, [_vp, _ip, _sz, _vp, _vp, _vp, _vp]),
     "wd_gauge_set_boundary": (_ip, [_vp, _ip]),
     "wd_gauge_bytes": (_ip, [_vp, _ip, _ip, ctypes.POINTER(_sz)]),
     "wd_gauge_destroy": (_ip, [_vp]),
     "dslash_apply": (_ip, [_vp, _vp, _vp, _vp, _dp, _ip, _ip, _ip, _vp]),
+"dslash_apply_dagger": (_ip, [_vp, _vp, _vp, _vp, _dp, _ip, _ip, _ip, _vp]),
     "dslash_eo_apply": (_ip, [_vp, _vp, _vp, _vp, _vp, _ip, _dp, _dp, _ip, _ip, _ip, _ip, _vp]),
     "wd_norm2": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _vp, _vp]),
     "wd_dot": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _vp, _vp, _vp]),
@@ -254,6 +256,13 @@ def dslash_apply(ctx: Context, gauge: Gauge, out, inp, mass: float, nrhs: int = 
                                int(prec), int(recon), _stream(stream)))
 
 
+def dslash_apply_dagger(ctx: Context, gauge: Gauge, out, inp, mass: float, nrhs: int = 1, prec: int = F32,
+                        recon: int = 18, stream=None) -> None:
+    """out = D^dagger in = gamma5 D gamma5 in (the paper's Eq. (1) sign convention); asynchronous."""
+    _check(load().dslash_apply_dagger(ctx.handle, gauge.handle, _ptr(out), _ptr(inp), float(mass), int(nrhs),
+                                      int(prec), int(recon), _stream(stream)))
+
+
 def dslash_eo_apply(ctx: Context, gauge: Gauge, out, inp, x, out_parity: int, a: float, b: float,
                     dagger: bool = False, nrhs: int = 1, prec: int = F32, recon: int = 18, stream=None) -> None:
     """out_p = a x_p + b H^(dagger)_{p,1-p} in_{1-p} on half fields (asynchronous)."""
@@ -343,6 +352,15 @@ def wilson_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-
     out = st.as_dict()
     out["status"] = rc
     return out
+
+
+STREAM_REAL_MUL, STREAM_CPLX_MUL, STREAM_CPLX_CONJ_MUL, STREAM_CPLX_MADD, STREAM_CPLX_CONJ_MADD = range(5)
+
+
+def stream_mul(ctx: Context, kind: int, n: int, x, y, z, stream=None) -> None:
+    """z = x y (real, n doubles) or z = x y, conj(x) y, z + x y, z + conj(x) y (n complex numbers as
+    interleaved float64 pairs), element-wise on device arrays (asynchronous)."""
+    _check(load().wd_stream_mul(ctx.handle, int(kind), int(n), _ptr(x), _ptr(y), _ptr(z), _stream(stream)))
 
 
 def norm2_noalloc(dims, sites: int, prec: int, x, result, stream=None) -> None:

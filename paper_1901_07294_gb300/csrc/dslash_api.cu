@@ -113,8 +113,8 @@ using namespace wd;
 
 extern "C" {
 
-int dslash_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, double mass, int nrhs, int prec,
-                 int recon, void *stream)
+static int full_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, double mass, int dagger, int nrhs,
+                      int prec, int recon, void *stream)
 {
     clear_error();
     if (!ctx) return set_error(WD_EINVAL, "ctx is NULL");
@@ -137,7 +137,19 @@ int dslash_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, doub
     A.parity0 = 0;
     A.a = mass + 4.0;
     A.b = -0.5;
-    return hop_launch(ctx, A, prec, recon, 0, nrhs, (cudaStream_t)stream);
+    return hop_launch(ctx, A, prec, recon, dagger, nrhs, (cudaStream_t)stream);
+}
+
+int dslash_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, double mass, int nrhs, int prec,
+                 int recon, void *stream)
+{
+    return full_apply(ctx, g, out, in, mass, 0, nrhs, prec, recon, stream);
+}
+
+int dslash_apply_dagger(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, double mass, int nrhs, int prec,
+                        int recon, void *stream)
+{
+    return full_apply(ctx, g, out, in, mass, 1, nrhs, prec, recon, stream);
 }
 
 int dslash_eo_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, const void *x, int out_parity,

@@ -281,3 +281,27 @@ def test_degenerate_extents_and_ragged_tails(dims, prec, threads, variant):
         wd.dslash_apply(ctx, g, fout, fin, 0.3, prec=prec, recon=recon)
         check_dslash(unpack_field(ctx, dims, wd.SITES_FULL, prec, fout), oracle.dirac(dims, U, psi, 0.3), prec,
                      dims, U, psi, recon, lambda u, p: oracle.dirac(dims, u, p, 0.3))
+
+
+@pytest.mark.parametrize("prec", ALL_PREC)
+@pytest.mark.parametrize("recon", [18, 12])
+def test_dagger_is_paper_convention(ctx, prec, recon):
+    """D^dagger = (m+4) - D_h / 2 with D_h the hopping term of Eq. (1) as printed
+    (the oracle's convention 1, pinned against gamma5 H gamma5 on the CPU)."""
+    dims = (4, 6, 8, 10)
+    U = synth.gauge(dims, seed=1501)
+    psi = synth.spinor(dims, seed=3501)
+    g = wd.Gauge(ctx, dims, U)
+    out = wd.alloc_field(dims, wd.SITES_FULL, prec)
+    wd.dslash_apply_dagger(ctx, g, out, pack_field(ctx, dims, wd.SITES_FULL, prec, psi), 0.1, prec=prec, recon=recon)
+    got = unpack_field(ctx, dims, wd.SITES_FULL, prec, out)
+    fn = lambda u, p: 4.1 * p - 0.5 * oracle.hop(dims, u, p, convention=1)
+    check_dslash(got, fn(U, psi), prec, dims, U, psi, recon, fn)
+    # <x, D y> = <D^dagger x, y> with the GPU operators (FP64)
+    if prec == wd.F64:
+        y = synth.spinor(dims, seed=3502)
+        dy = wd.alloc_field(dims, wd.SITES_FULL, prec)
+        wd.dslash_apply(ctx, g, dy, pack_field(ctx, dims, wd.SITES_FULL, prec, y), 0.1, prec=prec, recon=recon)
+        lhs = np.vdot(psi, unpack_field(ctx, dims, wd.SITES_FULL, prec, dy))
+        rhs = np.vdot(got, y)
+        assert abs(lhs - rhs) / abs(lhs) < 1e-13
