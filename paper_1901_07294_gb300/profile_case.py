@@ -3,13 +3,15 @@
     python -m paper_1901_07294_gb300.profile_case --op eo --prec f32 --dims 32,32,32,32 --nrhs 12 \
         --launches 4 [--threads 128 --variant 3]
     python -m paper_1901_07294_gb300.profile_case --op cg --prec f16 --dims 24,24,24,48 --launches 1
+    python -m paper_1901_07294_gb300.profile_case --op stream --kind 1 --n 16777216 --launches 3
 
 Inputs are the seeded synthetic gauge field and source of the benchmark.  With
 --threads/--variant the launch shape is pinned; otherwise the library default
 is used (no tuning, so few launches precede the profiled ones).  --op cg runs
 `launches` mixed-precision CG solves (inner precision --prec, reliable updates,
 delta 0.01, tol 1e-10, mass 0.1) on an even Gaussian source; --graph drives
-them with CUDA graphs.
+them with CUDA graphs.  --op stream runs `launches` element-wise products of
+kind --kind (wd_stream_mul) on --n elements of N(0,1) arrays.
 """
 from __future__ import annotations
 
@@ -20,7 +22,9 @@ import sys
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["full", "eo", "cg"], default="full")
+    ap.add_argument("--op", choices=["full", "eo", "cg", "stream"], default="full")
+    ap.add_argument("--kind", type=int, default=1)
+    ap.add_argument("--n", type=int, default=1 << 24)
     ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16"], default="f32")
     ap.add_argument("--recon", type=int, default=18)
     ap.add_argument("--dims", default="32,32,32,32")
@@ -42,6 +46,14 @@ def main(argv=None) -> int:
     prec = {"f64": wd.F64, "f32": wd.F32, "f16": wd.F16, "bf16": wd.BF16}[a.prec]
     dims = tuple(int(t) for t in a.dims.split(","))
     ctx = wd.Context(0)
+    if a.op == "stream":
+        gen = torch.Generator(device="cuda").manual_seed(6001)
+        x, y, z = (torch.randn(2 * a.n, dtype=torch.float64, device="cuda", generator=gen) for _ in range(3))
+        for _ in range(a.launches):
+            wd.stream_mul(ctx, a.kind, a.n, x, y, z)
+        torch.cuda.synchronize()
+        print(f"profile_case: stream kind={a.kind} n={a.n} launches={a.launches} ok")
+        return 0
     g = wd.Gauge(ctx, dims, synth.gauge(dims, seed=1001))
     if a.op == "cg":
         b = synth.even_spinor(dims, seed=3001)
