@@ -329,12 +329,15 @@ def run_gpu(args):
     mrhs = None
     blas = None
     streams = None
+    dd = None
     if not args.no_variants:
         _log("multi_rhs")
         mrhs = _mrhs_section(wd, torch, ctx, U, psi, peak)
         _log("blas")
         blas = _blas_section(wd, torch, ctx, psi, peak, stream,
                              fp64_tflops=variants.get("device_peaks", {}).get("fp64_tflops"))
+        _log("dd")
+        dd = _dd_section(wd, torch, ctx, U, psi, peak, mean_launch)
         _log("stream")
         streams = _stream_section(wd, torch, ctx, peak, stream,
                                   fp64_tflops=variants.get("device_peaks", {}).get("fp64_tflops"))
@@ -384,6 +387,7 @@ def run_gpu(args):
         "multi_rhs": mrhs,
         "blas": blas,
         "stream": streams,
+        "domain_decomposition": dd,
         "cg": cg,
         "solve": solve,
         "batch": batch,
@@ -570,6 +574,43 @@ def _stream_section(wd, torch, ctx, peak, stream, fp64_tflops=None, reps=20):
                      "fp64_instr_per_element": dp, "bound": "fp64_alu" if t_alu > t_hbm else "hbm",
                      "frac_bound": round(max(t_hbm, t_alu) / (ms * 1e-3), 4)}
     del x, y, z
+    return out
+
+
+def _dd_section(wd, torch, ctx, U, psi, peak, single_ms, reps=30):
+    """The 32^4 FP32 Dslash split along t into nsub slabs with a halo exchange (all slabs on this
+    GPU; the exchange is a device copy into each receiver's halo buffer): time per application of
+    all slabs, GB/s of the same 480 B/site, and the bytes exchanged, with FP32 and FP16 halos."""
+    import numpy as np
+    dims = DIMS
+    v = int(np.prod(dims))
+    aos = torch.from_numpy(psi.view(np.float64).reshape(-1).copy()).cuda()
+    out = {"lattice": list(dims), "single_domain_ms": round(single_ms, 5)}
+    for nsub in (1, 2, 4, 8):
+        dd = wd.DomainDecomposition(ctx, dims, nsub, U)
+        ld = dd.local_dims()
+        vloc = int(np.prod(ld))
+        ins, outs = [], []
+        for k in range(nsub):
+            f = wd.alloc_field(ld, wd.SITES_FULL, wd.F32)
+            wd.pack(ctx, ld, wd.SITES_FULL, wd.F32, aos[k * vloc * 24:(k + 1) * vloc * 24], f)
+            ins.append(f)
+            outs.append(wd.alloc_field(ld, wd.SITES_FULL, wd.F32))
+        for hp in (wd.F32, wd.F16):
+            for _ in range(3):
+                dd.dslash(outs, ins, MASS, prec=wd.F32, halo_prec=hp)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                dd.dslash(outs, ins, MASS, prec=wd.F32, halo_prec=hp)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = 480 * v / (ms * 1e-3) / 1e9
+            out[f"nsub{nsub}/{wd.PREC_NAMES[hp]}_halo"] = {
+                "ms": round(ms, 5), "gbs": round(gbs, 1), "frac_hbm": round(gbs / peak, 4),
+                "vs_single_domain": round(single_ms / ms, 3), "halo_bytes": dd.halo_bytes(hp)}
+        dd.close()
     return out
 
 

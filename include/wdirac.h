@@ -233,6 +233,40 @@ int wd_convert(wd_ctx *ctx, const int dims[4], int sites, int prec_out, void *ou
 int wd_norm2_noalloc(const int dims[4], int sites, int prec, const void *x, double *result,
                      void *stream);
 
+/* ---- Domain decomposition with a halo exchange (Sec. II-A) ----------------
+ * Sec. II-A parallelises the hopping term by decomposing the lattice into
+ * sub-lattices, one per process; Sec. V uses 16-bit floats only to compress
+ * the data exchanged between them.  A wd_dd splits the lattice `dims` along t
+ * into nsub slabs of L_t/nsub slices (nsub must divide L_t; the slab extent
+ * must be even and >= 2).  Slab k holds its own gauge (the k-th contiguous
+ * slice of the canonical links, whose site order has t slowest) and works on
+ * its own full fields of the local dimensions (wd_dd_local_dims); pack slab
+ * k's field with wd_pack from the k-th slice of a canonical global array.
+ * All slabs live on this GPU; the exchange is a device copy into each
+ * receiver's own halo buffer, the step that a multi-GPU build replaces by
+ * NCCL send/recv.
+ *
+ * wd_dd_dslash: out[k] = D in[k] for every slab k (D = (m+4) - H/2 of the
+ * global lattice): the faces (12-real spin-projected half spinors; backward
+ * faces already multiplied by the sender's link) are gathered and exchanged
+ * on an internal stream while the interior pass (hops that stay inside a
+ * slab) runs on `stream`; the boundary sites then add the halo terms.
+ * halo_prec: WD_F64, WD_F32 or WD_F16 (with a per-site FP32 scale) for the
+ * exchanged faces, independent of the field precision `prec`.  Asynchronous
+ * on `stream`.  out[k] must not alias in[k].  wd_dd_set_boundary: +1
+ * periodic, -1 antiperiodic in t (the sign goes on the faces that cross the
+ * global boundary).  wd_dd_halo_bytes: bytes of faces exchanged per
+ * application (all slabs, both directions and parities). */
+typedef struct wd_dd wd_dd;
+
+int wd_dd_create(wd_ctx *ctx, const int dims[4], int nsub, const double *links, int links_on_host, wd_dd **out);
+int wd_dd_local_dims(const wd_dd *dd, int dims_out[4]);
+int wd_dd_set_boundary(wd_dd *dd, int t_sign);
+int wd_dd_halo_bytes(const wd_dd *dd, int halo_prec, size_t *out);
+int wd_dd_dslash(wd_dd *dd, void *const *out, const void *const *in, double mass, int prec, int recon,
+                 int halo_prec, void *stream);
+int wd_dd_destroy(wd_dd *dd);
+
 /* ---- Element-wise products (Sec. IV examples; Sec. III-D complex forms) ----
  * z_i = f(x_i, y_i[, z_i]) for i < n on device arrays of FP64:
  *   WD_STREAM_REAL_MUL        z = x y        n reals (Sec. IV, real arithmetic)

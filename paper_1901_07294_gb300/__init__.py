@@ -50,6 +50,12 @@ _SIGS = {
     "wd_gauge_create": (_ip, [_vp, _DIMS, _vp, _ip, ctypes.POINTER(_vp)]),
     "wd_gauge_prepare": (_ip, [_vp, _ip, _ip]),
     "wd_stream_mul": (_ip, [_vp, _ip, _sz, _vp, _vp, _vp, _vp]),
+    "wd_dd_create": (_ip, [_vp, _DIMS, _ip, _vp, _ip, ctypes.POINTER(_vp)]),
+    "wd_dd_local_dims": (_ip, [_vp, _DIMS]),
+    "wd_dd_set_boundary": (_ip, [_vp, _ip]),
+    "wd_dd_halo_bytes": (_ip, [_vp, _ip, ctypes.POINTER(_sz)]),
+    "wd_dd_dslash": (_ip, [_vp, _vp, _vp, _dp, _ip, _ip, _ip, _vp]),
+    "wd_dd_destroy": (_ip, [_vp]),
     "wd_gauge_set_boundary": (_ip, [_vp, _ip]),
     "wd_gauge_bytes": (_ip, [_vp, _ip, _ip, ctypes.POINTER(_sz)]),
     "wd_gauge_destroy": (_ip, [_vp]),
@@ -352,6 +358,62 @@ def wilson_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-
     out = st.as_dict()
     out["status"] = rc
     return out
+
+
+class DomainDecomposition:
+    """The lattice `dims` split along t into `nsub` slabs, each with its own gauge and fields,
+    and the Wilson-Dirac operator applied with a halo exchange between slabs."""
+
+    def __init__(self, ctx: Context, dims, nsub: int, links):
+        import numpy as np
+        self.ctx = ctx
+        self.dims = tuple(int(d) for d in dims)
+        self.nsub = int(nsub)
+        self._h = _vp()
+        if hasattr(links, "data_ptr"):
+            if not links.is_cuda or not links.is_contiguous():
+                raise ValueError("torch links must be a contiguous CUDA tensor (or pass a numpy array)")
+            ptr, on_host = links.data_ptr(), 0
+        else:
+            arr = np.ascontiguousarray(links, dtype=np.complex128)
+            ptr, on_host = arr.ctypes.data, 1
+        _check(load().wd_dd_create(ctx.handle, _dims(self.dims), self.nsub, ptr, on_host, ctypes.byref(self._h)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def local_dims(self) -> tuple:
+        d = _DIMS()
+        _check(load().wd_dd_local_dims(self._h, d))
+        return tuple(d)
+
+    def set_boundary(self, t_sign: int) -> None:
+        _check(load().wd_dd_set_boundary(self._h, int(t_sign)))
+
+    def halo_bytes(self, halo_prec: int) -> int:
+        out = _sz()
+        _check(load().wd_dd_halo_bytes(self._h, int(halo_prec), ctypes.byref(out)))
+        return int(out.value)
+
+    def dslash(self, outs, ins, mass: float, prec: int = F32, recon: int = 18, halo_prec: int = F32,
+               stream=None) -> None:
+        n = self.nsub
+        po = (_vp * n)(*[_ptr(t) for t in outs])
+        pi = (_vp * n)(*[_ptr(t) for t in ins])
+        _check(load().wd_dd_dslash(self._h, po, pi, float(mass), int(prec), int(recon), int(halo_prec),
+                                   _stream(stream)))
+
+    def close(self):
+        if self._h:
+            load().wd_dd_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 STREAM_REAL_MUL, STREAM_CPLX_MUL, STREAM_CPLX_CONJ_MUL, STREAM_CPLX_MADD, STREAM_CPLX_CONJ_MADD = range(5)

@@ -29,6 +29,7 @@ struct HopArgs {
     int nparity;          // 2: blocks alternate parity (full operator); 1: parity0 only
     int parity0;
     int tneg;             // 1: antiperiodic in t (hops across the t boundary change sign)
+    int topen;            // 1: open t boundary (a sub-domain): no hop crosses it; halo terms come separately
     double a, b;
 };
 
@@ -178,6 +179,7 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
     const int tf = (t == Lt - 1) ? i - (Lt - 1) * st : i + st;
     const int tb = (t == 0) ? i + (Lt - 1) * st : i - st;
     const bool ntf = A.tneg && t == Lt - 1, ntb = A.tneg && t == 0;
+    const bool dtf = !(A.topen && t == Lt - 1), dtb = !(A.topen && t == 0);   // t hops taken here
 
     constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF gamma
     constexpr int SB = -SF;             // backward projector
@@ -197,8 +199,8 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
         hop_dir<P, RECON, 1, SB, false>(in, gb + 1 * lb, vh, yb, yb, false, acc);
         hop_dir<P, RECON, 2, SF, true>(in, gf + 2 * lb, vh, zf, i, false, acc);
         hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, false, acc);
-        hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
-        hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
+        if (dtf) hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
+        if (dtb) hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
     } else {
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) LK::prefetch(gf + mu * lb, vh, i);
@@ -212,11 +214,11 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
         hop_dir<P, RECON, 0, SB, false>(in, gb + 0 * lb, vh, xb, xb, false, acc);
         hop_dir<P, RECON, 1, SB, false>(in, gb + 1 * lb, vh, yb, yb, false, acc);
         hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, false, acc);
-        hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
+        if (dtb) hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
         hop_dir<P, RECON, 0, SF, true>(in, gf + 0 * lb, vh, xf, i, false, acc);
         hop_dir<P, RECON, 1, SF, true>(in, gf + 1 * lb, vh, yf, i, false, acc);
         hop_dir<P, RECON, 2, SF, true>(in, gf + 2 * lb, vh, zf, i, false, acc);
-        hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
+        if (dtf) hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
     }
 
     const T a = (T)A.a, b = (T)A.b;
