@@ -548,6 +548,9 @@ extern "C" int cg_solve_batch(wd_ctx *ctx, int n, const wd_solve_desc *descs, in
     if (mode == WD_BATCH_PERSISTENT) {
         rc = run_persistent(ctx, n, descs, stats, s);
     } else {
+        // the solves run on their own streams: first let the work queued on the
+        // caller's stream (which may still be writing the sources) finish
+        WD_CUDA_TRY(cudaStreamSynchronize(s));
         rc = run_graph(ctx, n, descs, stats);
     }
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -205,7 +205,12 @@ int cg_run_graph(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const cha
 int cg_dispatch(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, double tol,
                 const wd_cg_opts &o, wd_cg_stats &st, cudaStream_t s)
 {
-    if (o.use_graph && o.inner_prec != WD_F64 && o.reliable) return cg_run_graph(ctx, g, mass, x, b, tol, o, st);
+    if (o.use_graph && o.inner_prec != WD_F64 && o.reliable) {
+        // the graph runs on the solve's own stream: first let the work queued on
+        // the caller's stream (which may still be writing b) finish
+        WD_CUDA_TRY(cudaStreamSynchronize(s));
+        return cg_run_graph(ctx, g, mass, x, b, tol, o, st);
+    }
     switch (o.inner_prec) {
     case WD_F64: return cg_run<PREC_F64, PREC_F64>(ctx, g, mass, x, b, tol, o, st, s);
     case WD_F32: return cg_run<PREC_F32, PREC_F32>(ctx, g, mass, x, b, tol, o, st, s);

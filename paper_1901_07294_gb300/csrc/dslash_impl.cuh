@@ -29,7 +29,7 @@ struct HopArgs {
     int nparity;          // 2: blocks alternate parity (full operator); 1: parity0 only
     int parity0;
     int tneg;             // 1: antiperiodic in t (hops across the t boundary change sign)
-    int topen;            // 1: open t boundary (a sub-domain): no hop crosses it; halo terms come separately
+    int topen;            // 1: open t boundary (a sub-domain): no hop crosses it (selects the TOPEN kernel)
     double a, b;
 };
 
@@ -147,7 +147,9 @@ __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh
 //      every link once, so all of them come from DRAM).
 // One output site: checkerboard index i < A.vh of parity p, right-hand side
 // at byte offset roff.  Shared by hop_kernel and the persistent solver.
-template <int P, int RECON, bool DAG, bool HAS_X, int PF>
+// TOPEN: the t boundary is open (a sub-domain of a decomposed lattice): the
+// hops across it are skipped; their halo terms are added separately.
+template <int P, int RECON, bool DAG, bool HAS_X, int PF, bool TOPEN = false>
 __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const int i, const size_t roff)
 {
     using T = typename Prec<P>::real;
@@ -179,7 +181,7 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
     const int tf = (t == Lt - 1) ? i - (Lt - 1) * st : i + st;
     const int tb = (t == 0) ? i + (Lt - 1) * st : i - st;
     const bool ntf = A.tneg && t == Lt - 1, ntb = A.tneg && t == 0;
-    const bool dtf = !(A.topen && t == Lt - 1), dtb = !(A.topen && t == 0);   // t hops taken here
+    const bool dtf = !TOPEN || t != Lt - 1, dtb = !TOPEN || t != 0;   // t hops taken here
 
     constexpr int SF = DAG ? +1 : -1;   // forward projector 1 + SF gamma
     constexpr int SB = -SF;             // backward projector
@@ -247,7 +249,7 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
 // PF 4 is schedule 1 compiled for 3 resident blocks of 256 threads per SM
 // (at most 85 registers): more warps to hide latency, at the price of
 // registers the compiler would otherwise use to hoist loads.
-template <int P, int RECON, bool DAG, bool HAS_X, int PF>
+template <int P, int RECON, bool DAG, bool HAS_X, int PF, bool TOPEN = false>
 __global__ void __launch_bounds__(256, PF == 4 ? 3 : 2) hop_kernel(const HopArgs A)
 {
     int p, blk;
@@ -255,7 +257,7 @@ __global__ void __launch_bounds__(256, PF == 4 ? 3 : 2) hop_kernel(const HopArgs
     else { p = A.parity0; blk = blockIdx.x; }
     const int i = blk * blockDim.x + threadIdx.x;
     if (i >= A.vh) return;
-    hop_site<P, RECON, DAG, HAS_X, PF>(A, p, i, (size_t)blockIdx.y * A.rhs_stride);
+    hop_site<P, RECON, DAG, HAS_X, PF, TOPEN>(A, p, i, (size_t)blockIdx.y * A.rhs_stride);
 }
 
 constexpr int HOP_VARIANTS = 3;       // memory schedules 0..2 (one site per thread, linear blocks)
@@ -272,6 +274,10 @@ __host__ __device__ constexpr int hop_mrhs_strip(int v)
 template <int P, int RECON, bool DAG, bool HX>
 void launch_hop_pf(const HopArgs &A, dim3 grid, int threads, int pf, cudaStream_t s)
 {
+    if (A.topen) {   // sub-domain interior pass: schedule 1 with the open t boundary
+        wd_launch(hop_kernel<P, RECON, DAG, HX, 1, true>, grid, dim3(threads), 0, s, A);
+        return;
+    }
     switch (pf) {
     case 0: wd_launch(hop_kernel<P, RECON, DAG, HX, 0>, grid, dim3(threads), 0, s, A); break;
     case 1: wd_launch(hop_kernel<P, RECON, DAG, HX, 1>, grid, dim3(threads), 0, s, A); break;

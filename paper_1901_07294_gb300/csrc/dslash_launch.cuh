@@ -14,7 +14,7 @@ namespace wd {
 template <int P>
 cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int threads, int pf, cudaStream_t s)
 {
-    const int zs = hop_mrhs_strip(pf);
+    const int zs = A.topen ? -1 : hop_mrhs_strip(pf);   // open-boundary passes use the single-field kernel
     if (zs >= 0) {
         const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
         const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
