@@ -1,11 +1,18 @@
-// One mixed-precision reliable-update CG solve driven by a captured CUDA graph.
+// One mixed-precision reliable-update CG solve driven by a CUDA graph with a
+// device-side loop.
 //
 // Shared by the graph batch mode and the request queue.  A solve owns its
-// workspace, a stream, per-solve reduction scratch and a graph holding
-// GS_ITERS iterations (4 hop launches and 3 BLAS kernels each, with every CG
-// scalar kept in device memory).  The host replays the graph, reads the
-// scalars, and does the FP64 reliable updates (x += x_lo, r = b - A x) and
-// the convergence test between replays.
+// workspace, a stream, per-solve reduction scratch and a graph whose only
+// top-level node is a conditional WHILE node.  Its body is one CG iteration
+// (4 hop launches and 3 BLAS kernels, every CG scalar in device memory)
+// followed by a one-thread control kernel that tracks max |r| and the
+// iteration counts and keeps the loop going until a reliable update is due
+// (|r| < delta max|r|, |r|^2 <= tol^2 |b|^2, a breakdown, RELIABLE_MAX_GAP
+// iterations without an update, maxiter) or GS_LAUNCH_CAP iterations have run
+// in this launch.  The host then reads the scalars and does the FP64 reliable
+// update (x += x_lo, r = b - A x) and the convergence test: one host round
+// trip per update instead of one per fixed number of iterations, and no
+// iterations past the point where an update was due.
 #pragma once
 
 #include <cmath>
@@ -15,7 +22,34 @@
 
 namespace wd {
 
-constexpr int GS_ITERS = 8;   // CG iterations per graph replay
+constexpr int GS_LAUNCH_CAP = 32;   // iterations at most per graph launch
+
+// Device scalar slots of a graph-driven solve (see also OpDotAlphaDev):
+// s[0] |r|^2, s[1] pAp, s[2] alpha, s[3] true |r|^2, s[4] previous |r|^2,
+// s[6] breakdown flag, s[8] max |r| since the last update, s[9] iterations in
+// this launch, s[10] iterations since the last update, s[11] iterations in
+// total, s[12] tol^2 |b|^2, s[13] delta, s[14] maxiter, s[15] GS_LAUNCH_CAP.
+constexpr int GS_NSCAL = 16;
+
+// The loop condition of the WHILE node, evaluated after each iteration.
+template <int UNUSED = 0>
+__global__ void gs_control_kernel(double *s, cudaGraphConditionalHandle cond)
+{
+    if (threadIdx.x != 0) return;
+    const double r2 = s[0];
+    const double rn = sqrt(r2);
+    double maxr = s[8];
+    if (rn > maxr) maxr = rn;
+    s[8] = maxr;
+    const double n_launch = s[9] + 1.0, n_gap = s[10] + 1.0, n_total = s[11] + 1.0;
+    s[9] = n_launch;
+    s[10] = n_gap;
+    s[11] = n_total;
+    const bool finite = r2 == r2 && r2 < 1e300;
+    const bool stop = s[6] != 0.0 || !finite || rn < s[13] * maxr || r2 <= s[12] || n_total >= s[14] ||
+                      n_gap >= (double)RELIABLE_MAX_GAP || n_launch >= s[15];
+    cudaGraphSetConditional(cond, stop ? 0u : 1u);
+}
 
 struct GSolve {
     // problem
@@ -28,6 +62,7 @@ struct GSolve {
     // resources
     cudaStream_t s = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond = 0;
     void *mem = nullptr;
     double *h = nullptr;   // pinned host copy of the scalars
     char *r = nullptr, *ax = nullptr, *t_o = nullptr, *t_e = nullptr;
@@ -115,14 +150,28 @@ template <int PS> int init(const wd_ctx *ctx, GSolve &q)
     static const double inf = INFINITY;   // s[4] = inf: the first direction update gives p = r
     WD_CUDA_TRY(cudaMemcpyAsync(q.scal + 4, &inf, sizeof(double), cudaMemcpyHostToDevice, q.s));
     WD_CUDA_TRY(cudaMemcpyAsync(q.h, q.scal, sizeof(double), cudaMemcpyDeviceToHost, q.s));
-    // build a graph of GS_ITERS iterations node by node (no stream capture)
+    // build the graph node by node (no stream capture): a WHILE node whose
+    // body is one iteration and the control kernel
     cudaGraph_t graph;
     WD_CUDA_TRY(cudaGraphCreate(&graph, 0));
+    cudaError_t ge = cudaGraphConditionalHandleCreate(&q.cond, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = q.cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if (ge == cudaSuccess) ge = cudaGraphAddNode(&loop, graph, nullptr, nullptr, 0, &cp);
+    if (ge != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return set_error(WD_ECUDA, "creating the solve loop failed: %s", cudaGetErrorString(ge));
+    }
     GraphSink sink;
-    sink.graph = graph;
+    sink.graph = cp.conditional.phGraph_out[0];
     graph_sink() = &sink;
-    int rc = WD_OK;
-    for (int it = 0; it < GS_ITERS && rc == WD_OK; ++it) rc = iteration<PS>(ctx, q);
+    int rc = iteration<PS>(ctx, q);
+    if (rc == WD_OK && wd_launch(gs_control_kernel<0>, dim3(1), dim3(32), 0, q.s, q.scal, q.cond) != cudaSuccess)
+        rc = set_error(WD_ECUDA, "adding the loop control failed");
     graph_sink() = nullptr;
     if (rc == WD_OK && sink.err != cudaSuccess)
         rc = set_error(WD_ECUDA, "building the solve graph failed: %s", cudaGetErrorString(sink.err));
@@ -157,7 +206,7 @@ inline int gs_alloc(GSolve &q)
         q.mem = nullptr;
         return set_error(WD_ENOMEM, "cudaMalloc of %zu bytes of solve workspace failed", bytes);
     }
-    WD_CUDA_TRY(cudaMallocHost(&q.h, 8 * sizeof(double)));
+    WD_CUDA_TRY(cudaMallocHost(&q.h, GS_NSCAL * sizeof(double)));
     WD_CUDA_TRY(cudaStreamCreateWithFlags(&q.s, cudaStreamNonBlocking));
     return WD_OK;
 }
@@ -173,7 +222,7 @@ inline int gs_bind(const wd_ctx *ctx, GSolve &q)
     q.status = WD_OK;
     q.active = true;
     q.rel = 1.0;
-    std::memset(q.h, 0, 8 * sizeof(double));
+    std::memset(q.h, 0, GS_NSCAL * sizeof(double));
     char *p = (char *)q.mem;
     auto take = [&p](size_t n) {
         char *r = p;
@@ -197,7 +246,8 @@ inline int gs_setup(const wd_ctx *ctx, GSolve &q)
     return gs_bind(ctx, q);
 }
 
-// After gs_bind's work has finished: reads |b|^2 and prepares the test.
+// After gs_bind's work has finished: reads |b|^2, prepares the test and
+// enqueues the loop's constants (s[8..15]).
 inline void gs_start(GSolve &q)
 {
     q.b2 = q.h[0];
@@ -207,27 +257,44 @@ inline void gs_start(GSolve &q)
         q.active = false;
         q.rel = 0.0;
         if (!std::isfinite(q.b2)) q.status = WD_EINVAL;   // poisoned source
+        return;
+    }
+    double *c = q.h + 8;
+    c[0] = q.maxr;
+    c[1] = c[2] = c[3] = 0.0;
+    c[4] = q.stop2;
+    c[5] = q.opts.delta;
+    c[6] = (double)q.opts.maxiter;
+    c[7] = (double)GS_LAUNCH_CAP;
+    if (cudaMemcpyAsync(q.scal + 8, c, 8 * sizeof(double), cudaMemcpyHostToDevice, q.s) != cudaSuccess ||
+        cudaStreamSynchronize(q.s) != cudaSuccess) {
+        cudaGetLastError();
+        q.active = false;
+        q.status = WD_ECUDA;
     }
 }
 
-// Enqueues one replay (GS_ITERS iterations) and the scalar read-back.
+// Enqueues one launch (the device loop runs until an update is due or
+// GS_LAUNCH_CAP iterations) and the scalar read-back.
 inline int gs_launch(GSolve &q)
 {
+    WD_CUDA_TRY(cudaMemsetAsync(q.scal + 9, 0, sizeof(double), q.s));
     WD_CUDA_TRY(cudaGraphLaunch(q.exec, q.s));
-    WD_CUDA_TRY(cudaMemcpyAsync(q.h, q.scal, 7 * sizeof(double), cudaMemcpyDeviceToHost, q.s));
+    WD_CUDA_TRY(cudaMemcpyAsync(q.h, q.scal, GS_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, q.s));
     return WD_OK;
 }
 
-// After a replay has finished: residual test, reliable update, convergence.
+// After a launch has finished: reliable update and convergence test when
+// the loop stopped for one of them (not merely at the per-launch cap).
 inline int gs_after(const wd_ctx *ctx, GSolve &q)
 {
-    q.iters += GS_ITERS;
+    q.iters = (int)q.h[11];
     const double r2 = q.h[0];
     const bool broke = q.h[6] != 0.0 || !std::isfinite(r2);
     const double rn = std::sqrt(r2);
-    if (rn > q.maxr) q.maxr = rn;
+    q.maxr = q.h[8];
     if (!(broke || rn < q.opts.delta * q.maxr || r2 <= q.stop2 || q.iters >= q.opts.maxiter ||
-          q.iters - q.iters_at_update >= RELIABLE_MAX_GAP))
+          (int)q.h[10] >= RELIABLE_MAX_GAP))
         return WD_OK;
     q.iters_at_update = q.iters;
     int rc;
@@ -258,8 +325,12 @@ inline int gs_after(const wd_ctx *ctx, GSolve &q)
         static const double restart[3] = {INFINITY, 0.0, 0.0};   // s[4], s[5], s[6]
         WD_CUDA_TRY(cudaMemcpyAsync(q.scal + 4, restart, sizeof(restart), cudaMemcpyHostToDevice, q.s));
     }
-    WD_CUDA_TRY(cudaStreamSynchronize(q.s));
     q.maxr = std::sqrt(r2t);
+    q.h[8] = q.maxr;   // s[8] = max |r| = the true |r|, s[10] = 0 iterations since the update
+    q.h[10] = 0.0;
+    WD_CUDA_TRY(cudaMemcpyAsync(q.scal + 8, q.h + 8, sizeof(double), cudaMemcpyHostToDevice, q.s));
+    WD_CUDA_TRY(cudaMemcpyAsync(q.scal + 10, q.h + 10, sizeof(double), cudaMemcpyHostToDevice, q.s));
+    WD_CUDA_TRY(cudaStreamSynchronize(q.s));
     return WD_OK;
 }
 
