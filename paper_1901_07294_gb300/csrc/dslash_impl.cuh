@@ -260,17 +260,6 @@ __global__ void __launch_bounds__(256, PF == 4 ? 3 : 2) hop_kernel(const HopArgs
     hop_site<P, RECON, DAG, HAS_X, PF, TOPEN>(A, p, i, (size_t)blockIdx.y * A.rhs_stride);
 }
 
-constexpr int HOP_VARIANTS = 3;       // memory schedules 0..2 (one site per thread, linear blocks)
-constexpr int HOP_MRHS_VARIANT = 3;   // variant index of the shared-link multi-RHS kernel
-constexpr int HOP_OCC_VARIANT = 4;    // schedule 1 compiled for 3 blocks of 256 threads per SM
-constexpr int HOP_MAX_VARIANT = 7;    // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
-
-// Multi-RHS variants and their z-strip width (0: natural order); -1 if v is not one.
-__host__ __device__ constexpr int hop_mrhs_strip(int v)
-{
-    return v == HOP_MRHS_VARIANT ? 0 : v == 5 ? 16 : v == 6 ? 8 : v == 7 ? 4 : -1;
-}
-
 template <int P, int RECON, bool DAG, bool HX>
 void launch_hop_pf(const HopArgs &A, dim3 grid, int threads, int pf, cudaStream_t s)
 {

@@ -7,6 +7,17 @@
 
 namespace wd {
 
+constexpr int HOP_VARIANTS = 3;       // memory schedules 0..2 (one site per thread, linear blocks)
+constexpr int HOP_MRHS_VARIANT = 3;   // variant index of the shared-link multi-RHS kernel
+constexpr int HOP_OCC_VARIANT = 4;    // schedule 1 compiled for 3 blocks of 256 threads per SM
+constexpr int HOP_MAX_VARIANT = 7;    // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
+
+// Multi-RHS variants and their z-strip width (0: natural order); -1 if v is not one.
+__host__ __device__ constexpr int hop_mrhs_strip(int v)
+{
+    return v == HOP_MRHS_VARIANT ? 0 : v == 5 ? 16 : v == 6 ? 8 : v == 7 ? 4 : -1;
+}
+
 // Launches the hop kernel of precision P for the runtime (recon, dagger,
 // has_x) with `threads` per block (at most 256) and memory schedule `pf`
 // (pf = HOP_MRHS_VARIANT and 5..7: the shared-link multi-RHS kernel, threads/32
