@@ -318,6 +318,25 @@ def run_gpu(args):
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
     e2e_value = bytes_step * ws / (e2e_ms * 1e-3) / 1e9
 
+    # the host-link floor of that loop: the same H2D and D2H copies alone, concurrently
+    def copies_only(k):
+        b = sets[k % 2]
+        with torch.cuda.stream(b["s"]):
+            b["aos"].copy_(psi_host, non_blocking=True)
+            b["out_host"].copy_(b["aos_out"], non_blocking=True)
+
+    for k in range(4):
+        copies_only(k)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sets[1]["s"].wait_event(e0)
+    for k in range(e2e_steps):
+        copies_only(k)
+    stream.wait_stream(sets[1]["s"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    copy_floor_ms = e0.elapsed_time(e1) / e2e_steps
+
     variants = {}
     if not args.no_variants:
         _log("variants")
@@ -375,6 +394,7 @@ def run_gpu(args):
                      "mean_launch_ms": mean_launch},
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": v * 24 * 8,
                 "d2h_bytes_per_step": v * 24 * 8, "ms_per_step": e2e_ms,
+                "copy_floor_ms_per_step": copy_floor_ms, "frac_of_copy_floor": copy_floor_ms / e2e_ms,
                 "path": "pinned H2D FP64 canonical -> wd.pack -> wd.dslash_apply -> wd.unpack -> D2H, "
                         "steps alternating over two streams"},
         "autotune": {"chosen": {"threads": best["threads"], "variant": best["variant"]},

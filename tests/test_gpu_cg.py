@@ -59,6 +59,7 @@ CASES = [
     dict(inner_prec=wd.BF16, reliable=True, delta=0.01, use_graph=True),
     dict(inner_prec=wd.F32, reliable=True, delta=0.1, use_graph=True),
     dict(inner_prec=wd.F16, reliable=False, delta=1e-3),
+    dict(inner_prec=wd.F32, reliable=True, delta=1e-6, use_graph=True),
 ]
 
 
@@ -128,3 +129,16 @@ def test_cg_free_field_closed_form(ctx):
     wd.cg_solve(ctx, g, m, fx, fb, tol=1e-12, inner_prec=wd.F32, reliable=True, delta=0.1)
     x = unpack_field(ctx, dims, wd.SITES_EVEN, wd.F64, fx)
     assert rel_max_err(x, xs) < 1e-10
+
+
+def test_graph_loop_relaunches_between_updates(ctx):
+    """delta = 1e-6: more iterations pass between reliable updates than one graph launch
+    runs (32), so the host relaunches without an update; the device-side loop then takes
+    the same iterations as the host-driven solver, up to rounding."""
+    dims, mass = (8, 8, 8, 8), 0.1
+    kw = dict(inner_prec=wd.F32, reliable=True, delta=1e-6)
+    st_h = _solve(ctx, dims, mass, 1e-10, **kw)[0]
+    st_g = _solve(ctx, dims, mass, 1e-10, use_graph=True, **kw)[0]
+    assert st_h["iters"] > 32 and st_g["iters"] > 32
+    assert abs(st_g["iters"] - st_h["iters"]) <= 3, (st_g["iters"], st_h["iters"])
+    assert st_g["reliable_updates"] <= st_h["reliable_updates"] + 1

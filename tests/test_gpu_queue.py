@@ -134,14 +134,16 @@ def test_request_larger_than_budget_is_refused():
 def test_cancel_wait_timeout_and_poisoned_request():
     ctx = _ctx()
     q = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=1)
-    first, _ = _request(ctx, 0, dims=(8, 8, 8, 16), tol=1e-12)
+    # a solve long enough (tens of ms) to still run while the others are submitted
+    first, _ = _request(ctx, 0, dims=(16, 16, 16, 32), tol=1e-12)
     first["mass"] = 0.02
+    later_reqs = [_request(ctx, k, dims=(4, 4, 4, 4))[0] for k in range(1, 4)]
     t0 = q.submit(first)
-    later = [q.submit(_request(ctx, k, dims=(4, 4, 4, 4))[0]) for k in range(1, 4)]
-    q.cancel(later[1])                                     # still waiting: cancelled at once
     with pytest.raises(wd.WdError) as e:
         q.wait(t0, timeout_ms=0)                           # host-side wait gives up; the request goes on
     assert e.value.status == wd.WD_ETIMEOUT
+    later = [q.submit(r) for r in later_reqs]
+    q.cancel(later[1])                                     # still waiting (one slot, busy): cancelled at once
     poisoned, _ = _request(ctx, 7, dims=(4, 4, 4, 4))
     nan = np.full((volume((4, 4, 4, 4)), 4, 3), np.nan, np.complex128)
     poisoned["b"] = pack_field(ctx, (4, 4, 4, 4), wd.SITES_EVEN, wd.F64, nan)
