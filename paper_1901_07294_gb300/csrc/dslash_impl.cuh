@@ -30,8 +30,25 @@ struct HopArgs {
     int parity0;
     int tneg;             // 1: antiperiodic in t (hops across the t boundary change sign)
     int topen;            // 1: open t boundary (a sub-domain): no hop crosses it (selects the TOPEN kernel)
+    unsigned div_m[3];    // n / d for d = L[0]/2, L[1], L[2] as (n * m) >> s (set by hop_setup)
+    int div_s[3];
     double a, b;
 };
+
+// Division by an invariant integer (Granlund and Montgomery, 1994): for
+// 0 <= n < 2^31, m = ceil(2^s / d) and s = 31 + ceil(log2 d) give
+// floor(n m / 2^s) = floor(n / d) exactly (n (m d - 2^s) / (d 2^s) < 1/d).
+__host__ __device__ __forceinline__ int div_inv(int n, unsigned m, int s)
+{
+    return (int)(((unsigned long long)(unsigned)n * m) >> s);
+}
+inline void div_magic(unsigned d, unsigned &m, int &s)
+{
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    s = 31 + l;
+    m = (unsigned)((((unsigned long long)1 << s) + d - 1) / d);
+}
 
 // h0, h1 = upper two spin components of (1 + S gamma_MU) psi, chiral basis.
 template <int MU, int S, typename T>
@@ -163,12 +180,12 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
     // checkerboard index -> coordinates; x-parity bit from the site parity
     const int Lx = A.L[0], Ly = A.L[1], Lz = A.L[2], Lt = A.L[3];
     const int lxh = Lx >> 1;
-    int r = i / lxh;
+    const int r = div_inv(i, A.div_m[0], A.div_s[0]);
     const int xh = i - r * lxh;
-    const int y = r % Ly;
-    r /= Ly;
-    const int z = r % Lz;
-    const int t = r / Lz;
+    const int r2 = div_inv(r, A.div_m[1], A.div_s[1]);
+    const int y = r - r2 * Ly;
+    const int t = div_inv(r2, A.div_m[2], A.div_s[2]);
+    const int z = r2 - t * Lz;
     const int x = 2 * xh + ((p + y + z + t) & 1);
     const int sy = lxh, sz = lxh * Ly, st = sz * Lz;
     const int row = i - xh;

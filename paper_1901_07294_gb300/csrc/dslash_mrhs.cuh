@@ -13,12 +13,12 @@ __device__ __forceinline__ void site_neighbours(const HopArgs &A, int p, int i, 
 {
     const int Lx = A.L[0], Ly = A.L[1], Lz = A.L[2], Lt = A.L[3];
     const int lxh = Lx >> 1;
-    int r = i / lxh;
+    const int r = div_inv(i, A.div_m[0], A.div_s[0]);
     const int xh = i - r * lxh;
-    const int y = r % Ly;
-    r /= Ly;
-    const int z = r % Lz;
-    const int t = r / Lz;
+    const int r2 = div_inv(r, A.div_m[1], A.div_s[1]);
+    const int y = r - r2 * Ly;
+    const int t = div_inv(r2, A.div_m[2], A.div_s[2]);
+    const int z = r2 - t * Lz;
     const int x = 2 * xh + ((p + y + z + t) & 1);
     const int sy = lxh, sz = lxh * Ly, st = sz * Lz;
     const int row = i - xh;
