@@ -178,7 +178,10 @@ int wd_probe_fma(wd_ctx *ctx, int prec, double *tflops);
  * 4: as 1 compiled for 3 resident blocks of 256 threads per SM; for nrhs > 1
  * also 3: links of 32 sites staged once in shared memory for all nrhs fields,
  * and 5, 6, 7: as 3 with the (z, t) slices visited in z-strips of width 16,
- * 8, 4, which shortens the reuse distance of t-neighbours in L2).
+ * 8, 4, which shortens the reuse distance of t-neighbours in L2); and the
+ * search's other two dimensions: 8: as 1 with each block's window of nearby
+ * neighbour spinors staged in shared memory (tiling on), 9: as 1 with two
+ * sites per thread.
  * wd_tune_dslash times every candidate for one problem shape (full = 1: the
  * dslash_apply shape; full = 0: dslash_eo_apply with (with_x = 1) or without
  * the x term) on private scratch fields (allocated and freed by the call),

@@ -4,13 +4,16 @@
 
 #include "dslash_impl.cuh"
 #include "dslash_mrhs.cuh"
+#include "dslash_variants.cuh"
 
 namespace wd {
 
 constexpr int HOP_VARIANTS = 3;       // memory schedules 0..2 (one site per thread, linear blocks)
 constexpr int HOP_MRHS_VARIANT = 3;   // variant index of the shared-link multi-RHS kernel
 constexpr int HOP_OCC_VARIANT = 4;    // schedule 1 compiled for 3 blocks of 256 threads per SM
-constexpr int HOP_MAX_VARIANT = 7;    // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
+constexpr int HOP_TILE_VARIANT = 8;   // schedule 1 with the neighbour window staged in shared memory
+constexpr int HOP_2SITE_VARIANT = 9;  // schedule 1 with two sites per thread
+constexpr int HOP_MAX_VARIANT = 9;    // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
 
 // Multi-RHS variants and their z-strip width (0: natural order); -1 if v is not one.
 __host__ __device__ constexpr int hop_mrhs_strip(int v)
@@ -21,7 +24,8 @@ __host__ __device__ constexpr int hop_mrhs_strip(int v)
 // Launches the hop kernel of precision P for the runtime (recon, dagger,
 // has_x) with `threads` per block (at most 256) and memory schedule `pf`
 // (pf = HOP_MRHS_VARIANT and 5..7: the shared-link multi-RHS kernel, threads/32
-// fields at a time, in the site order hop_mrhs_strip(pf) names).
+// fields at a time, in the site order hop_mrhs_strip(pf) names;
+// HOP_TILE_VARIANT and HOP_2SITE_VARIANT: the kernels of dslash_variants.cuh).
 template <int P>
 cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int threads, int pf, cudaStream_t s)
 {
@@ -46,6 +50,37 @@ cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int th
     const dim3 grid((unsigned)(per * A.nparity), (unsigned)nrhs);
     const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
     const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
+    if (pf == HOP_2SITE_VARIANT && !A.topen) {
+        switch (key) {
+        case 0: launch_hop_2site<P, 18, false, false>(B, nrhs, threads, s); break;
+        case 1: launch_hop_2site<P, 18, false, true>(B, nrhs, threads, s); break;
+        case 2: launch_hop_2site<P, 18, true, false>(B, nrhs, threads, s); break;
+        case 3: launch_hop_2site<P, 18, true, true>(B, nrhs, threads, s); break;
+        case 4: launch_hop_2site<P, 12, false, false>(B, nrhs, threads, s); break;
+        case 5: launch_hop_2site<P, 12, false, true>(B, nrhs, threads, s); break;
+        case 6: launch_hop_2site<P, 12, true, false>(B, nrhs, threads, s); break;
+        case 7: launch_hop_2site<P, 12, true, true>(B, nrhs, threads, s); break;
+        }
+        return cudaGetLastError();
+    }
+    if (pf == HOP_TILE_VARIANT) {
+        bool ok = false;
+        if (!A.topen) {
+            switch (key) {
+            case 0: ok = launch_hop_window<P, 18, false, false>(B, grid, threads, s); break;
+            case 1: ok = launch_hop_window<P, 18, false, true>(B, grid, threads, s); break;
+            case 2: ok = launch_hop_window<P, 18, true, false>(B, grid, threads, s); break;
+            case 3: ok = launch_hop_window<P, 18, true, true>(B, grid, threads, s); break;
+            case 4: ok = launch_hop_window<P, 12, false, false>(B, grid, threads, s); break;
+            case 5: ok = launch_hop_window<P, 12, false, true>(B, grid, threads, s); break;
+            case 6: ok = launch_hop_window<P, 12, true, false>(B, grid, threads, s); break;
+            case 7: ok = launch_hop_window<P, 12, true, true>(B, grid, threads, s); break;
+            }
+        }
+        if (ok) return cudaGetLastError();
+        pf = 1;   // window larger than 48 KB, or an open-boundary pass: schedule 1
+    }
+    if (pf == HOP_2SITE_VARIANT) pf = 1;   // open-boundary pass
     switch (key) {
     case 0: launch_hop_pf<P, 18, false, false>(B, grid, threads, pf, s); break;
     case 1: launch_hop_pf<P, 18, false, true>(B, grid, threads, pf, s); break;
