@@ -181,7 +181,7 @@ int wd_probe_fma(wd_ctx *ctx, int prec, double *tflops);
  * 8, 4, which shortens the reuse distance of t-neighbours in L2); and the
  * search's other two dimensions: 8: as 1 with each block's window of nearby
  * neighbour spinors staged in shared memory (tiling on), 9: as 1 with two
- * sites per thread.
+ * sites per thread).
  * wd_tune_dslash times every candidate for one problem shape (full = 1: the
  * dslash_apply shape; full = 0: dslash_eo_apply with (with_x = 1) or without
  * the x term) on private scratch fields (allocated and freed by the call),

@@ -97,6 +97,35 @@ __device__ __forceinline__ void hop_dir_smem(const char *in, int vh, int nb,
     accumulate<MU, S>(acc, w0, w1);
 }
 
+// out = a x + b acc at site i of parity p for the field at byte offset roff
+template <int P, bool HAS_X>
+__device__ __forceinline__ void mrhs_store(const HopArgs &A, int p, int i, size_t roff,
+                                           const cpx<typename Prec<P>::real> (&acc)[4][3])
+{
+    using T = typename Prec<P>::real;
+    const T a = (T)A.a, b = (T)A.b;
+    T o[24];
+    if constexpr (HAS_X) {
+        Spinor<P>::load((p ? A.x[1] : A.x[0]) + roff, A.vh, i, o);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o[6 * sp + 2 * c] = a * o[6 * sp + 2 * c] + b * acc[sp][c].re;
+                o[6 * sp + 2 * c + 1] = a * o[6 * sp + 2 * c + 1] + b * acc[sp][c].im;
+            }
+    } else {
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o[6 * sp + 2 * c] = b * acc[sp][c].re;
+                o[6 * sp + 2 * c + 1] = b * acc[sp][c].im;
+            }
+    }
+    Spinor<P>::store((p ? A.out[1] : A.out[0]) + roff, A.vh, i, o);
+}
+
 // Multi right-hand-side hop: a block owns 32 consecutive checkerboard sites
 // and all nrhs fields.  The 8 links of each site are loaded once (row 3
 // rebuilt once for 12-real storage) into shared memory, then warp y of the
@@ -175,15 +204,13 @@ __global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 3) hop_mrhs_kernel(co
     }
     __syncthreads();
     if (!active) return;
-    int nb[8];
-#pragma unroll
-    for (int d = 0; d < 8; ++d) nb[d] = nbs[d][s];
+    // the neighbour indices stay in shared memory and are read where used,
+    // which keeps eight registers free across the field loop
+    const int *nb = &nbs[0][s];   // nb[32 d] = neighbour in direction d; a t hop wraps
+                                  // (t = Lt-1 forward, t = 0 backward) exactly when that
+                                  // neighbour's checkerboard index falls below / above i
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
-    // a t hop wraps (t = Lt-1 forward, t = 0 backward) exactly when the
-    // neighbour's checkerboard index falls below / above the site's
-    const bool ntf = A.tneg && nb[3] < i, ntb = A.tneg && nb[7] > i;
-    const T a = (T)A.a, b = (T)A.b;
     for (int rhs = threadIdx.y; rhs < nrhs; rhs += blockDim.y) {
         const size_t roff = (size_t)rhs * A.rhs_stride;
         const char *in = (p ? A.in[1] : A.in[0]) + roff;
@@ -192,34 +219,15 @@ __global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 3) hop_mrhs_kernel(co
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc[sp][c] = {T(0), T(0)};
-        hop_dir_smem<P, 0, SB, false>(in, vh, nb[4], &lk[4][0][s], false, acc);
-        hop_dir_smem<P, 1, SB, false>(in, vh, nb[5], &lk[5][0][s], false, acc);
-        hop_dir_smem<P, 2, SB, false>(in, vh, nb[6], &lk[6][0][s], false, acc);
-        hop_dir_smem<P, 3, SB, false>(in, vh, nb[7], &lk[7][0][s], ntb, acc);
+        hop_dir_smem<P, 0, SB, false>(in, vh, nb[128], &lk[4][0][s], false, acc);
+        hop_dir_smem<P, 1, SB, false>(in, vh, nb[160], &lk[5][0][s], false, acc);
+        hop_dir_smem<P, 2, SB, false>(in, vh, nb[192], &lk[6][0][s], false, acc);
+        hop_dir_smem<P, 3, SB, false>(in, vh, nb[224], &lk[7][0][s], A.tneg && nb[224] > i, acc);
         hop_dir_smem<P, 0, SF, true>(in, vh, nb[0], &lk[0][0][s], false, acc);
-        hop_dir_smem<P, 1, SF, true>(in, vh, nb[1], &lk[1][0][s], false, acc);
-        hop_dir_smem<P, 2, SF, true>(in, vh, nb[2], &lk[2][0][s], false, acc);
-        hop_dir_smem<P, 3, SF, true>(in, vh, nb[3], &lk[3][0][s], ntf, acc);
-        T o[24];
-        if constexpr (HAS_X) {
-            Spinor<P>::load((p ? A.x[1] : A.x[0]) + roff, vh, i, o);
-#pragma unroll
-            for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    o[6 * sp + 2 * c] = a * o[6 * sp + 2 * c] + b * acc[sp][c].re;
-                    o[6 * sp + 2 * c + 1] = a * o[6 * sp + 2 * c + 1] + b * acc[sp][c].im;
-                }
-        } else {
-#pragma unroll
-            for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    o[6 * sp + 2 * c] = b * acc[sp][c].re;
-                    o[6 * sp + 2 * c + 1] = b * acc[sp][c].im;
-                }
-        }
-        Spinor<P>::store((p ? A.out[1] : A.out[0]) + roff, vh, i, o);
+        hop_dir_smem<P, 1, SF, true>(in, vh, nb[32], &lk[1][0][s], false, acc);
+        hop_dir_smem<P, 2, SF, true>(in, vh, nb[64], &lk[2][0][s], false, acc);
+        hop_dir_smem<P, 3, SF, true>(in, vh, nb[96], &lk[3][0][s], A.tneg && nb[96] < i, acc);
+        mrhs_store<P, HAS_X>(A, p, i, roff, acc);
     }
 }
 
