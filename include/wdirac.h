@@ -316,9 +316,10 @@ typedef struct {
     double delta;      /* see above; ignored for inner_prec = WD_F64 */
     int maxiter;       /* limit on inner iterations */
     int autotune;      /* 1: tune the hop launches the solve uses (once per context) */
-    int use_graph;     /* 1 (mixed precision, reliable = 1): run 8 iterations per CUDA-graph
-                          replay with the CG scalars on the device; the host checks the
-                          residual and does reliable updates between replays */
+    int use_graph;     /* 1 (mixed precision, reliable = 1): a CUDA graph whose device-side
+                          loop runs iterations (CG scalars on the device) until a reliable
+                          update is due, or 32 of them; the host does the FP64 updates
+                          between launches */
 } wd_cg_opts;
 
 typedef struct {
@@ -373,10 +374,10 @@ int wilson_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x, const voi
  * Modes:
  *   WD_BATCH_SEQUENTIAL  cg_solve on each descriptor in turn (any options);
  *   WD_BATCH_GRAPH       mixed-precision reliable-update solves (inner_prec
- *                        WD_F32/WD_F16/WD_BF16, the same for all), 8
- *                        iterations of each solve captured into a CUDA graph
- *                        and replayed on a stream per solve; residual checks
- *                        and FP64 reliable updates on the host between replays;
+ *                        WD_F32/WD_F16/WD_BF16, the same for all), each a
+ *                        CUDA graph with a device-side iteration loop on a
+ *                        stream per solve; FP64 reliable updates and the
+ *                        convergence test on the host between launches;
  *   WD_BATCH_PERSISTENT  one cooperative kernel: each solve runs on its own
  *                        group of thread blocks (sized by volume), steps
  *                        separated by group barriers whose waits are bounded

@@ -5,11 +5,11 @@
 // solution, true residual and inner products):
 //   WD_BATCH_SEQUENTIAL  one cg_solve after another;
 //   WD_BATCH_GRAPH       each solve's iteration (4 hop launches and 3 BLAS
-//                        kernels whose scalars stay in device memory)
-//                        captured K times into a CUDA graph per solve; the
-//                        graphs of all active solves are replayed on their own
-//                        streams, and the host checks residuals and does the
-//                        FP64 reliable updates between replays;
+//                        kernels whose scalars stay in device memory) is the
+//                        body of a device-side WHILE loop in a CUDA graph per
+//                        solve; the graphs of all active solves run on their
+//                        own streams until a reliable update is due, and the
+//                        host does the FP64 updates between launches;
 //   WD_BATCH_PERSISTENT  one cooperative launch: each solve owns a group of
 //                        thread blocks (sized in proportion to its volume)
 //                        that runs the whole solve, separated by group-local

@@ -168,8 +168,8 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
     return status;
 }
 
-// The same solve driven by a CUDA graph of GS_ITERS iterations (gsolve.cuh):
-// one host synchronisation per replay instead of one per iteration.  Runs on
+// The same solve driven by a CUDA graph with a device-side loop (gsolve.cuh):
+// one host synchronisation per reliable update instead of one per iteration.  Runs on
 // the solve's own stream; the call is synchronous either way.
 int cg_run_graph(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, double tol,
                  const wd_cg_opts &o, wd_cg_stats &st)

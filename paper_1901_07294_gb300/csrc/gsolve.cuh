@@ -102,9 +102,9 @@ template <typename Op> inline int launch(const wd_ctx *ctx, const Op &op, int ns
 }
 
 // One iteration, starting with the direction update p = r + beta p
-// (beta = s[0]/s[4]; s[4] = +inf gives p = r).  A replay therefore ends right
-// after the residual update, and a host-side reliable update that replaces r
-// and s[0] between replays is picked up by the next direction update, as in
+// (beta = s[0]/s[4]; s[4] = +inf gives p = r).  A launch therefore ends right
+// after a residual update, and a host-side reliable update that replaces r
+// and s[0] between launches is picked up by the next direction update, as in
 // the sequential solver.
 template <int PS> int iteration(const wd_ctx *ctx, GSolve &q)
 {

@@ -4,9 +4,10 @@
 // host thread and run by one scheduler thread.  Each scheduler step admits
 // waiting requests while free slots and the HBM budget allow (first come
 // first served, but a request that fits may pass one that does not), sets up
-// the admitted ones (workspace, stream, captured CUDA graph), replays the
-// graph of every running request on its own stream (so their work overlaps on
-// the GPU), then does each request's residual test and FP64 reliable update,
+// the admitted ones (workspace, stream, a CUDA graph whose device-side loop
+// runs CG iterations until a reliable update is due), launches the graph of
+// every running request on its own stream (so their work overlaps on the
+// GPU), then does each request's FP64 reliable update and convergence test,
 // retires the finished ones and frees their memory.  Requests therefore join
 // and leave the running batch between steps.
 #include <algorithm>
