@@ -363,7 +363,7 @@ def run_gpu(args):
     batch = None
     if not args.no_cg:
         _log("batch")
-        batch = _batch_section(wd, torch, ctx)
+        batch = _batch_section(wd, torch, ctx, peak)
     serving = None
     if not args.no_cg and not args.no_serving:
         _log("serving")
@@ -371,7 +371,7 @@ def run_gpu(args):
     solve = None
     if not args.no_cg:
         _log("solve")
-        solve = _solve_section(wd, torch, ctx)
+        solve = _solve_section(wd, torch, ctx, peak)
     cg = None
     if not args.no_cg:
         _log("cg")
@@ -701,7 +701,7 @@ def _mrhs_section(wd, torch, ctx, U, psi, peak, reps=20):
     return out
 
 
-def _batch_section(wd, torch, ctx):
+def _batch_section(wd, torch, ctx, peak):
     """24 solves of uneven volumes (8 each of 8^4, 16^4, 24^3x48), masses U[0.05, 0.5] (seed 4001),
     tol 1e-10, mixed FP32 reliable-update CG: one persistent launch vs per-solve CUDA graphs vs
     24 sequential cg_solve calls."""
@@ -744,10 +744,14 @@ def _batch_section(wd, torch, ctx):
             if best is None or ms < best[0]:
                 best = (ms, st)
         ms, st = best
+        it_bytes = sum(s_["iters"] * int(np.prod(p["gauge"].dims)) // 2 * _cg_iteration_bytes(wd.F32, 18)
+                       for s_, p in zip(st, probs))
         out[name] = {"seconds": round(ms / 1e3, 4), "solves_per_s": round(24 / (ms / 1e3), 1),
                      "iters_total": int(sum(s["iters"] for s in st)),
                      "max_true_rel_resid": max(s["true_rel_resid"] for s in st),
-                     "all_converged": all(s["status"] == 0 for s in st)}
+                     "all_converged": all(s["status"] == 0 for s in st),
+                     "iter_model_bytes": it_bytes,
+                     "iter_frac_hbm_incl_updates": round(it_bytes / (ms / 1e3) / 1e9 / peak, 4)}
     for g in gauges.values():
         g.close()
     return out
@@ -841,6 +845,19 @@ def _serving_section(wd, torch, ctx, n_main=600, n_sweep=150, warm=60):
     return out
 
 
+def _bicgstab_iteration_bytes(inner_prec, recon):
+    """Bytes per even site that one BiCGStab iteration on Mhat moves by design: four
+    even-odd hops (two Mhat applications; their second hops read the axpy term),
+    p = r + beta (p - omega v) (r, p, v read, p written), <r^, v> (2 fields),
+    s = r - alpha v (2 read, 1 written), <t, s> and |t|^2 (2), and the fused update
+    (p, s, t, r^ read, r written, x read and written): 26 inner-precision passes, two
+    over the x accumulator and four link sets.  Reliable updates come on top."""
+    fb = {0: 192, 1: 96, 2: 52, 3: 52}[inner_prec]
+    link_b = {0: 8, 1: 4, 2: 2, 3: 2}[inner_prec] * recon * 8
+    fx = 192 if inner_prec == 0 else 96
+    return 26 * fb + 4 * link_b + 2 * fx
+
+
 def _cg_iteration_bytes(inner_prec, recon):
     """Bytes per even site that one CG iteration on Mhat^dagger Mhat moves by design
     (every kernel's inputs read once, outputs written once): four even-odd hops
@@ -856,7 +873,7 @@ def _cg_iteration_bytes(inner_prec, recon):
     return 19 * fb + 4 * link_b + 2 * fx
 
 
-def _solve_section(wd, torch, ctx):
+def _solve_section(wd, torch, ctx, peak):
     """Full-system solve D x = b on 24^3x48 (Gaussian source on all sites, seed 3201), tol 1e-10:
     BiCGStab on Mhat vs CG on the normal equations, FP64 and mixed FP16 (reliable updates,
     delta 0.01).  Best of 2 after one warm solve."""
@@ -870,7 +887,10 @@ def _solve_section(wd, torch, ctx):
     fb = wd.alloc_field(dims, wd.SITES_FULL, wd.F64)
     wd.pack(ctx, dims, wd.SITES_FULL, wd.F64, torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
     fx = wd.alloc_field(dims, wd.SITES_FULL, wd.F64)
-    out = {"lattice": list(dims), "tol": 1e-10, "mass": 0.1, "runs": {}}
+    vh = int(np.prod(dims)) // 2
+    out = {"lattice": list(dims), "tol": 1e-10, "mass": 0.1, "runs": {},
+           "iter_model": "per-iteration bytes of the Schur solver's kernels (reliable updates and the "
+                         "source and reconstruction hops excluded) over the whole solve time per iteration"}
     runs = [("bicgstab_fp64", wd.SOLVER_BICGSTAB, dict(inner_prec=wd.F64)),
             ("bicgstab_fp16", wd.SOLVER_BICGSTAB, dict(inner_prec=wd.F16, reliable=True, delta=0.01)),
             ("bicgstab_fp32", wd.SOLVER_BICGSTAB, dict(inner_prec=wd.F32, reliable=True, delta=0.01)),
@@ -890,8 +910,15 @@ def _solve_section(wd, torch, ctx):
             if best is None or ms < best[0]:
                 best = (ms, st)
         ms, st = best
-        out["runs"][name] = {"seconds": round(ms / 1e3, 5), "iters": st["iters"],
-                             "reliable_updates": st["reliable_updates"], "true_rel_resid": st["true_rel_resid"]}
+        rec = {"seconds": round(ms / 1e3, 5), "iters": st["iters"],
+               "reliable_updates": st["reliable_updates"], "true_rel_resid": st["true_rel_resid"]}
+        if st["iters"] > 0:
+            model = _bicgstab_iteration_bytes if solver == wd.SOLVER_BICGSTAB else _cg_iteration_bytes
+            it_bytes = model(kw["inner_prec"], kw.get("inner_recon", 18)) * vh
+            per_it = ms / 1e3 / st["iters"]
+            rec.update({"ms_per_iter_incl_updates": round(per_it * 1e3, 5), "iter_model_bytes": it_bytes,
+                        "iter_frac_hbm_incl_updates": round(it_bytes / per_it / 1e9 / peak, 4)})
+        out["runs"][name] = rec
     g.close()
     return out
 

@@ -4,6 +4,8 @@
         --launches 4 [--threads 128 --variant 3]
     python -m paper_1901_07294_gb300.profile_case --op cg --prec f16 --dims 24,24,24,48 --launches 1
     python -m paper_1901_07294_gb300.profile_case --op stream --kind 1 --n 16777216 --launches 3
+    python -m paper_1901_07294_gb300.profile_case --op dd --nsub 4 --halo f16 --launches 3
+    python -m paper_1901_07294_gb300.profile_case --op solve --prec f16 --dims 24,24,24,48 --launches 1
 
 Inputs are the seeded synthetic gauge field and source of the benchmark.  With
 --threads/--variant the launch shape is pinned; otherwise the library default
@@ -11,7 +13,10 @@ is used (no tuning, so few launches precede the profiled ones).  --op cg runs
 `launches` mixed-precision CG solves (inner precision --prec, reliable updates,
 delta 0.01, tol 1e-10, mass 0.1) on an even Gaussian source; --graph drives
 them with CUDA graphs.  --op stream runs `launches` element-wise products of
-kind --kind (wd_stream_mul) on --n elements of N(0,1) arrays.
+kind --kind (wd_stream_mul) on --n elements of N(0,1) arrays.  --op dd applies
+the operator `launches` times to the lattice split into --nsub slabs (field
+precision --prec, halos --halo).  --op solve runs `launches` full-system solves
+D x = b by BiCGStab (inner precision --prec, delta 0.01, tol 1e-10, mass 0.1).
 """
 from __future__ import annotations
 
@@ -22,7 +27,9 @@ import sys
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["full", "eo", "cg", "stream"], default="full")
+    ap.add_argument("--op", choices=["full", "eo", "cg", "stream", "dd", "solve"], default="full")
+    ap.add_argument("--nsub", type=int, default=2)
+    ap.add_argument("--halo", choices=["f64", "f32", "f16"], default="f32")
     ap.add_argument("--kind", type=int, default=1)
     ap.add_argument("--n", type=int, default=1 << 24)
     ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16"], default="f32")
@@ -54,7 +61,36 @@ def main(argv=None) -> int:
         torch.cuda.synchronize()
         print(f"profile_case: stream kind={a.kind} n={a.n} launches={a.launches} ok")
         return 0
+    if a.op == "dd":
+        hp = {"f64": wd.F64, "f32": wd.F32, "f16": wd.F16}[a.halo]
+        dd = wd.DomainDecomposition(ctx, dims, a.nsub, synth.gauge(dims, seed=1001))
+        ld = dd.local_dims()
+        vloc = int(np.prod(ld))
+        aos = torch.from_numpy(synth.spinor(dims, seed=2001).view(np.float64).reshape(-1).copy()).cuda()
+        ins, outs = [], []
+        for k in range(a.nsub):
+            f = wd.alloc_field(ld, wd.SITES_FULL, prec)
+            wd.pack(ctx, ld, wd.SITES_FULL, prec, aos[k * vloc * 24:(k + 1) * vloc * 24], f)
+            ins.append(f)
+            outs.append(wd.alloc_field(ld, wd.SITES_FULL, prec))
+        for _ in range(a.launches):
+            dd.dslash(outs, ins, 0.1, prec=prec, recon=a.recon, halo_prec=hp)
+        torch.cuda.synchronize()
+        print(f"profile_case: dd {a.prec} halo {a.halo} {a.dims} nsub={a.nsub} launches={a.launches} ok")
+        return 0
     g = wd.Gauge(ctx, dims, synth.gauge(dims, seed=1001))
+    if a.op == "solve":
+        b = synth.spinor(dims, seed=3201)
+        fb = wd.alloc_field(dims, wd.SITES_FULL, wd.F64)
+        wd.pack(ctx, dims, wd.SITES_FULL, wd.F64, torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
+        fx = wd.alloc_field(dims, wd.SITES_FULL, wd.F64)
+        for _ in range(a.launches):
+            st = wd.wilson_solve(ctx, g, 0.1, fx, fb, tol=1e-10, solver=wd.SOLVER_BICGSTAB, inner_prec=prec,
+                                 inner_recon=a.recon, reliable=True, delta=0.01)
+        torch.cuda.synchronize()
+        print(f"profile_case: solve bicgstab {a.prec} {a.dims} solves={a.launches} iters={st['iters']} "
+              f"updates={st['reliable_updates']} seconds={st['seconds']:.4f} ok")
+        return 0
     if a.op == "cg":
         b = synth.even_spinor(dims, seed=3001)
         fb = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
