@@ -378,6 +378,8 @@ def run_gpu(args):
         cg = _cg_section(wd, torch, ctx, with_cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline), peak=peak)
     _log("done")
 
+    traffic = _traffic_from_profile()
+    props = wd.device_info(ctx)
     line = {
         "metric": "dslash_hbm_gbs", "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -390,8 +392,11 @@ def run_gpu(args):
         "gflops": FLOPS_PER_SITE * v * args.steps * ws / (total_ms * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "kernel": HEADLINE_KERNEL, "achieved": achieved, "peak": peak,
                      "peak_kind": f"{peak_kind} copy bandwidth (burst)", "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": _traffic_from_profile(), "algorithmic_bytes_per_launch": bytes_step,
-                     "mean_launch_ms": mean_launch},
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_step,
+                     "mean_launch_ms": mean_launch, "median_launch_ms": statistics.median(launch_ms),
+                     "traffic_gbs": (traffic / (mean_launch * 1e-3) / 1e9) if traffic else None,
+                     "nominal_peak": props["nominal_hbm_gbs"], "frac_of_nominal": achieved / props["nominal_hbm_gbs"],
+                     "nominal_from": f"2 x {props['mem_clock_khz'] / 1e3:.0f} MHz x {props['mem_bus_bits']} bit / 8"},
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": v * 24 * 8,
                 "d2h_bytes_per_step": v * 24 * 8, "ms_per_step": e2e_ms,
                 "copy_floor_ms_per_step": copy_floor_ms, "frac_of_copy_floor": copy_floor_ms / e2e_ms,
@@ -422,12 +427,37 @@ def run_gpu(args):
     return 0
 
 
+def _per_launch_ms(torch, fn, stream, reps, flush=None):
+    """Mean and median of `reps` launches, each between its own CUDA events on `stream`
+    (torch's current stream); with `flush` (a buffer larger than L2) that buffer is
+    written before every launch."""
+    import statistics
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    # hold the stream for about 100 us per launch so that every launch is queued before the
+    # first runs: a launch shorter than the host's submission time is then still timed alone
+    torch.cuda._sleep(200_000 * reps)
+    for a, b in evs:
+        if flush is not None:
+            flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ts = [a.elapsed_time(b) for a, b in evs]
+    return sum(ts) / len(ts), statistics.median(ts)
+
+
 def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, fp64_tflops=None, reps=50):
-    """Per-launch GB/s of every operator variant of the 32^4 / 16^3x32 configuration."""
+    """Per-launch times and GB/s of every operator variant of the 32^4 / 16^3x32 configuration:
+    mean and median over `reps` launches timed one by one, warm (the inputs of consecutive
+    launches may still be in L2: 16^3x32 FP32 is about 63 MB) and with L2 flushed (a buffer of
+    twice the L2 size written before each launch)."""
     import numpy as np
 
     import synth
-    out = {}
+    l2 = wd.device_info(ctx)["l2_bytes"] or (128 << 20)
+    flush = torch.empty(2 * l2 // 4, dtype=torch.float32, device="cuda")
+    out = {"timing": f"{reps} launches each, CUDA events per launch; L2 flush: {2 * l2 >> 20} MB written before each"}
     for dims in ((32, 32, 32, 32), (16, 16, 16, 32)):
         if dims == base_dims:
             U, psi = U_base, psi_base
@@ -460,18 +490,16 @@ def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, fp64_tf
                         nsite = v // 2
                     for _ in range(5):
                         fn()
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    for _ in range(reps):
-                        fn()
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                    ms = e0.elapsed_time(e1) / reps
+                    ms, med = _per_launch_ms(torch, fn, stream, reps)
+                    ms_fl, med_fl = _per_launch_ms(torch, fn, stream, reps, flush=flush)
                     b = BYTES_PER_SITE[(pn, kind, recon)] * nsite
                     gbs = b / (ms * 1e-3) / 1e9
                     key = f"{'x'.join(map(str, dims))}/{pn}/{kind}/r{recon}"
-                    out[key] = {"ms": round(ms, 5), "gbs": round(gbs, 1), "frac_hbm": round(gbs / peak, 4),
-                                "gflops": round(FLOPS_PER_SITE * nsite / (ms * 1e-3) / 1e9, 1)}
+                    out[key] = {"ms": round(ms, 5), "ms_median": round(med, 5), "gbs": round(gbs, 1),
+                                "frac_hbm": round(gbs / peak, 4),
+                                "gflops": round(FLOPS_PER_SITE * nsite / (ms * 1e-3) / 1e9, 1),
+                                "ms_l2_flushed": round(ms_fl, 5), "ms_l2_flushed_median": round(med_fl, 5),
+                                "frac_hbm_l2_flushed": round(b / (ms_fl * 1e-3) / 1e9 / peak, 4)}
                     if pn == "f64" and fp64_tflops:
                         # FP64 is bounded by the FP64 units: the useful 1320 flops/site
                         # against the measured FP64 FMA rate

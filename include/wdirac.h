@@ -170,6 +170,21 @@ int dslash_eo_apply(wd_ctx *ctx, const wd_gauge *g, void *out, const void *in, c
  * counterpart; this is measurement support.  Synchronous, about 0.1 s. */
 int wd_probe_fma(wd_ctx *ctx, int prec, double *tflops);
 
+/* Device attributes of the context's GPU, for rooflines: SM count, memory
+ * clock (kHz), memory bus width (bits), L2 size (bytes), compute capability,
+ * and the nominal HBM bandwidth 2 x clock x width / 8 (GB/s; two transfers
+ * per clock).  Measurement support; the paper has no counterpart. */
+typedef struct {
+    int sm_count;
+    int mem_clock_khz;
+    int mem_bus_bits;
+    int l2_bytes;
+    int cc_major, cc_minor;
+    double nominal_hbm_gbs;
+} wd_device_props;
+
+int wd_device_info(const wd_ctx *ctx, wd_device_props *out);
+
 /* ---- Autotuning of the operator launches ------------------------------------
  * The hop kernel has tunable launch parameters: threads per block (32..256,
  * multiple of 32) and a memory-schedule variant (0: directions x+,x-,..,t-

@@ -50,6 +50,7 @@ _SIGS = {
     "wd_gauge_create": (_ip, [_vp, _DIMS, _vp, _ip, ctypes.POINTER(_vp)]),
     "wd_gauge_prepare": (_ip, [_vp, _ip, _ip]),
     "wd_stream_mul": (_ip, [_vp, _ip, _sz, _vp, _vp, _vp, _vp]),
+    "wd_device_info": (_ip, [_vp, _vp]),
     "wd_dd_create": (_ip, [_vp, _DIMS, _ip, _vp, _ip, ctypes.POINTER(_vp)]),
     "wd_dd_local_dims": (_ip, [_vp, _DIMS]),
     "wd_dd_set_boundary": (_ip, [_vp, _ip]),
@@ -562,6 +563,19 @@ def solve_workspace_bytes(dims, inner_prec: int) -> int:
     out = _sz()
     _check(load().wd_solve_workspace_bytes(_dims(dims), int(inner_prec), ctypes.byref(out)))
     return int(out.value)
+
+
+class DeviceProps(ctypes.Structure):
+    """wd_device_props"""
+    _fields_ = [("sm_count", _ip), ("mem_clock_khz", _ip), ("mem_bus_bits", _ip), ("l2_bytes", _ip),
+                ("cc_major", _ip), ("cc_minor", _ip), ("nominal_hbm_gbs", _dp)]
+
+
+def device_info(ctx: Context) -> dict:
+    """SM count, memory clock and bus width, L2 size, compute capability and the nominal HBM GB/s."""
+    p = DeviceProps()
+    _check(load().wd_device_info(ctx.handle, ctypes.byref(p)))
+    return {f: getattr(p, f) for f, _ in DeviceProps._fields_}
 
 
 def probe_fma_tflops(ctx: Context, prec: int) -> float:

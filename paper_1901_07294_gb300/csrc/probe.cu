@@ -67,3 +67,23 @@ extern "C" int wd_probe_fma(wd_ctx *ctx, int prec, double *tflops)
     if (prec == WD_F32) return run_probe<float>(ctx, tflops);
     return set_error(WD_EINVAL, "the FMA probe measures WD_F64 or WD_F32");
 }
+
+extern "C" int wd_device_info(const wd_ctx *ctx, wd_device_props *out)
+{
+    clear_error();
+    if (!ctx || !out) return set_error(WD_EINVAL, "NULL argument");
+    int v[6] = {0, 0, 0, 0, 0, 0};
+    const cudaDeviceAttr attrs[6] = {cudaDevAttrMultiProcessorCount, cudaDevAttrMemoryClockRate,
+                                     cudaDevAttrGlobalMemoryBusWidth, cudaDevAttrL2CacheSize,
+                                     cudaDevAttrComputeCapabilityMajor, cudaDevAttrComputeCapabilityMinor};
+    for (int k = 0; k < 6; ++k) WD_CUDA_TRY(cudaDeviceGetAttribute(&v[k], attrs[k], ctx->device));
+    out->sm_count = v[0];
+    out->mem_clock_khz = v[1];
+    out->mem_bus_bits = v[2];
+    out->l2_bytes = v[3];
+    out->cc_major = v[4];
+    out->cc_minor = v[5];
+    // double data rate: two transfers per memory clock
+    out->nominal_hbm_gbs = 2.0 * (double)v[1] * 1e3 * (double)v[2] / 8.0 / 1e9;
+    return WD_OK;
+}
