@@ -185,6 +185,14 @@ typedef struct {
 
 int wd_device_info(const wd_ctx *ctx, wd_device_props *out);
 
+/* Asynchronous device-side status of the context: a kernel whose bounded wait
+ * gave up (the bulk-copy staged operator kernel waits at most about a second
+ * for its copies) records WD_ETIMEOUT in a context-owned word and skips its
+ * output.  wd_device_status waits for all work on the context's device,
+ * stores that word (WD_OK if nothing was recorded) in *code and clears it.
+ * Returns WD_OK, or WD_ECUDA if the device could not be synchronised. */
+int wd_device_status(wd_ctx *ctx, int *code);
+
 /* ---- Autotuning of the operator launches ------------------------------------
  * The hop kernel has tunable launch parameters: threads per block (32..256,
  * multiple of 32) and a memory-schedule variant (0: directions x+,x-,..,t-
@@ -196,7 +204,11 @@ int wd_device_info(const wd_ctx *ctx, wd_device_props *out);
  * 8, 4, which shortens the reuse distance of t-neighbours in L2); and the
  * search's other two dimensions: 8: as 1 with each block's window of nearby
  * neighbour spinors staged in shared memory (tiling on), 9: as 1 with two
- * sites per thread).
+ * sites per thread, 10: as 1 with each block's forward links, t-forward
+ * neighbours and x term copied into shared memory by bulk (TMA) copies that
+ * complete on an mbarrier while the backward directions run; 10 applies when
+ * the block size divides Lx/2*Ly*Lz and every plane is 16-byte aligned, and
+ * is schedule 1 otherwise).
  * wd_tune_dslash times every candidate for one problem shape (full = 1: the
  * dslash_apply shape; full = 0: dslash_eo_apply with (with_x = 1) or without
  * the x term) on private scratch fields (allocated and freed by the call),

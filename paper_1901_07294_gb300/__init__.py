@@ -51,6 +51,7 @@ _SIGS = {
     "wd_gauge_prepare": (_ip, [_vp, _ip, _ip]),
     "wd_stream_mul": (_ip, [_vp, _ip, _sz, _vp, _vp, _vp, _vp]),
     "wd_device_info": (_ip, [_vp, _vp]),
+    "wd_device_status": (_ip, [_vp, _vp]),
     "wd_dd_create": (_ip, [_vp, _DIMS, _ip, _vp, _ip, ctypes.POINTER(_vp)]),
     "wd_dd_local_dims": (_ip, [_vp, _DIMS]),
     "wd_dd_set_boundary": (_ip, [_vp, _ip]),
@@ -576,6 +577,14 @@ def device_info(ctx: Context) -> dict:
     p = DeviceProps()
     _check(load().wd_device_info(ctx.handle, ctypes.byref(p)))
     return {f: getattr(p, f) for f, _ in DeviceProps._fields_}
+
+
+def device_status(ctx: Context) -> int:
+    """Waits for the device, then returns and clears the context's asynchronous status
+    word (0, or a WD_E* code a kernel's bounded wait recorded)."""
+    out = _ip(0)
+    _check(load().wd_device_status(ctx.handle, ctypes.byref(out)))
+    return int(out.value)
 
 
 def probe_fma_tflops(ctx: Context, prec: int) -> float:

@@ -70,6 +70,7 @@ int hop_setup(const wd_gauge *g, int prec, int recon, HopArgs &A)
     for (int mu = 0; mu < 4; ++mu) A.L[mu] = g->geo.L[mu];
     A.vh = vh;
     A.tneg = g->t_sign < 0 ? 1 : 0;
+    A.status = ctx_status_word(g->ctx);
     div_magic((unsigned)(A.L[0] >> 1), A.div_m[0], A.div_s[0]);
     div_magic((unsigned)A.L[1], A.div_m[1], A.div_s[1]);
     div_magic((unsigned)A.L[2], A.div_m[2], A.div_s[2]);

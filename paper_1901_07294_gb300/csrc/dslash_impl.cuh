@@ -32,6 +32,7 @@ struct HopArgs {
     int topen;            // 1: open t boundary (a sub-domain): no hop crosses it (selects the TOPEN kernel)
     unsigned div_m[3];    // n / d for d = L[0]/2, L[1], L[2] as (n * m) >> s (set by hop_setup)
     int div_s[3];
+    int *status;          // device status word for asynchronous errors (bounded waits); may be NULL
     double a, b;
 };
 
@@ -278,17 +279,15 @@ __global__ void __launch_bounds__(256, PF == 4 ? 3 : 2) hop_kernel(const HopArgs
 }
 
 template <int P, int RECON, bool DAG, bool HX>
-void launch_hop_pf(const HopArgs &A, dim3 grid, int threads, int pf, cudaStream_t s)
+cudaError_t launch_hop_pf(const HopArgs &A, dim3 grid, int threads, int pf, cudaStream_t s)
 {
-    if (A.topen) {   // sub-domain interior pass: schedule 1 with the open t boundary
-        wd_launch(hop_kernel<P, RECON, DAG, HX, 1, true>, grid, dim3(threads), 0, s, A);
-        return;
-    }
+    if (A.topen)   // sub-domain interior pass: schedule 1 with the open t boundary
+        return wd_launch(hop_kernel<P, RECON, DAG, HX, 1, true>, grid, dim3(threads), 0, s, A);
     switch (pf) {
-    case 0: wd_launch(hop_kernel<P, RECON, DAG, HX, 0>, grid, dim3(threads), 0, s, A); break;
-    case 1: wd_launch(hop_kernel<P, RECON, DAG, HX, 1>, grid, dim3(threads), 0, s, A); break;
-    case 2: wd_launch(hop_kernel<P, RECON, DAG, HX, 2>, grid, dim3(threads), 0, s, A); break;
-    default: wd_launch(hop_kernel<P, RECON, DAG, HX, 4>, grid, dim3(threads), 0, s, A); break;
+    case 0: return wd_launch(hop_kernel<P, RECON, DAG, HX, 0>, grid, dim3(threads), 0, s, A);
+    case 1: return wd_launch(hop_kernel<P, RECON, DAG, HX, 1>, grid, dim3(threads), 0, s, A);
+    case 2: return wd_launch(hop_kernel<P, RECON, DAG, HX, 2>, grid, dim3(threads), 0, s, A);
+    default: return wd_launch(hop_kernel<P, RECON, DAG, HX, 4>, grid, dim3(threads), 0, s, A);
     }
 }
 

@@ -2,6 +2,7 @@
 // variant) to the single-field kernel or the multi right-hand-side kernel.
 #pragma once
 
+#include "dslash_bulk.cuh"
 #include "dslash_impl.cuh"
 #include "dslash_mrhs.cuh"
 #include "dslash_variants.cuh"
@@ -13,7 +14,8 @@ constexpr int HOP_MRHS_VARIANT = 3;   // variant index of the shared-link multi-
 constexpr int HOP_OCC_VARIANT = 4;    // schedule 1 compiled for 3 blocks of 256 threads per SM
 constexpr int HOP_TILE_VARIANT = 8;   // schedule 1 with the neighbour window staged in shared memory
 constexpr int HOP_2SITE_VARIANT = 9;  // schedule 1 with two sites per thread
-constexpr int HOP_MAX_VARIANT = 9;    // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
+constexpr int HOP_BULK_VARIANT = 10;  // schedule 1 with the block's contiguous data staged by bulk copies
+constexpr int HOP_MAX_VARIANT = 10;   // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
 
 // Multi-RHS variants and their z-strip width (0: natural order); -1 if v is not one.
 __host__ __device__ constexpr int hop_mrhs_strip(int v)
@@ -25,73 +27,85 @@ __host__ __device__ constexpr int hop_mrhs_strip(int v)
 // has_x) with `threads` per block (at most 256) and memory schedule `pf`
 // (pf = HOP_MRHS_VARIANT and 5..7: the shared-link multi-RHS kernel, threads/32
 // fields at a time, in the site order hop_mrhs_strip(pf) names;
-// HOP_TILE_VARIANT and HOP_2SITE_VARIANT: the kernels of dslash_variants.cuh).
+// HOP_TILE_VARIANT and HOP_2SITE_VARIANT: the kernels of dslash_variants.cuh;
+// HOP_BULK_VARIANT: the kernel of dslash_bulk.cuh).
 template <int P>
 cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int threads, int pf, cudaStream_t s)
 {
+    const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
+    const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
     const int zs = A.topen ? -1 : hop_mrhs_strip(pf);   // open-boundary passes use the single-field kernel
     if (zs >= 0) {
-        const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
-        const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
         switch (key) {
-        case 0: launch_hop_mrhs<P, 18, false, false>(A, nrhs, threads, zs, s); break;
-        case 1: launch_hop_mrhs<P, 18, false, true>(A, nrhs, threads, zs, s); break;
-        case 2: launch_hop_mrhs<P, 18, true, false>(A, nrhs, threads, zs, s); break;
-        case 3: launch_hop_mrhs<P, 18, true, true>(A, nrhs, threads, zs, s); break;
-        case 4: launch_hop_mrhs<P, 12, false, false>(A, nrhs, threads, zs, s); break;
-        case 5: launch_hop_mrhs<P, 12, false, true>(A, nrhs, threads, zs, s); break;
-        case 6: launch_hop_mrhs<P, 12, true, false>(A, nrhs, threads, zs, s); break;
-        case 7: launch_hop_mrhs<P, 12, true, true>(A, nrhs, threads, zs, s); break;
+        case 0: return launch_hop_mrhs<P, 18, false, false>(A, nrhs, threads, zs, s);
+        case 1: return launch_hop_mrhs<P, 18, false, true>(A, nrhs, threads, zs, s);
+        case 2: return launch_hop_mrhs<P, 18, true, false>(A, nrhs, threads, zs, s);
+        case 3: return launch_hop_mrhs<P, 18, true, true>(A, nrhs, threads, zs, s);
+        case 4: return launch_hop_mrhs<P, 12, false, false>(A, nrhs, threads, zs, s);
+        case 5: return launch_hop_mrhs<P, 12, false, true>(A, nrhs, threads, zs, s);
+        case 6: return launch_hop_mrhs<P, 12, true, false>(A, nrhs, threads, zs, s);
+        default: return launch_hop_mrhs<P, 12, true, true>(A, nrhs, threads, zs, s);
         }
-        return cudaGetLastError();
     }
     const HopArgs &B = A;
     const int per = (A.vh + threads - 1) / threads;
     const dim3 grid((unsigned)(per * A.nparity), (unsigned)nrhs);
-    const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
-    const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
     if (pf == HOP_2SITE_VARIANT && !A.topen) {
         switch (key) {
-        case 0: launch_hop_2site<P, 18, false, false>(B, nrhs, threads, s); break;
-        case 1: launch_hop_2site<P, 18, false, true>(B, nrhs, threads, s); break;
-        case 2: launch_hop_2site<P, 18, true, false>(B, nrhs, threads, s); break;
-        case 3: launch_hop_2site<P, 18, true, true>(B, nrhs, threads, s); break;
-        case 4: launch_hop_2site<P, 12, false, false>(B, nrhs, threads, s); break;
-        case 5: launch_hop_2site<P, 12, false, true>(B, nrhs, threads, s); break;
-        case 6: launch_hop_2site<P, 12, true, false>(B, nrhs, threads, s); break;
-        case 7: launch_hop_2site<P, 12, true, true>(B, nrhs, threads, s); break;
+        case 0: return launch_hop_2site<P, 18, false, false>(B, nrhs, threads, s);
+        case 1: return launch_hop_2site<P, 18, false, true>(B, nrhs, threads, s);
+        case 2: return launch_hop_2site<P, 18, true, false>(B, nrhs, threads, s);
+        case 3: return launch_hop_2site<P, 18, true, true>(B, nrhs, threads, s);
+        case 4: return launch_hop_2site<P, 12, false, false>(B, nrhs, threads, s);
+        case 5: return launch_hop_2site<P, 12, false, true>(B, nrhs, threads, s);
+        case 6: return launch_hop_2site<P, 12, true, false>(B, nrhs, threads, s);
+        default: return launch_hop_2site<P, 12, true, true>(B, nrhs, threads, s);
         }
-        return cudaGetLastError();
+    }
+    cudaError_t e = cudaSuccess;
+    if (pf == HOP_BULK_VARIANT) {
+        bool ok = false;
+        switch (key) {
+        case 0: ok = launch_hop_bulk<P, 18, false, false>(B, grid, threads, s, e); break;
+        case 1: ok = launch_hop_bulk<P, 18, false, true>(B, grid, threads, s, e); break;
+        case 2: ok = launch_hop_bulk<P, 18, true, false>(B, grid, threads, s, e); break;
+        case 3: ok = launch_hop_bulk<P, 18, true, true>(B, grid, threads, s, e); break;
+        case 4: ok = launch_hop_bulk<P, 12, false, false>(B, grid, threads, s, e); break;
+        case 5: ok = launch_hop_bulk<P, 12, false, true>(B, grid, threads, s, e); break;
+        case 6: ok = launch_hop_bulk<P, 12, true, false>(B, grid, threads, s, e); break;
+        case 7: ok = launch_hop_bulk<P, 12, true, true>(B, grid, threads, s, e); break;
+        }
+        if (ok) return e;
+        pf = 1;   // a block would straddle a t-slice, an address is misaligned, or an open-boundary pass
     }
     if (pf == HOP_TILE_VARIANT) {
         bool ok = false;
         if (!A.topen) {
             switch (key) {
-            case 0: ok = launch_hop_window<P, 18, false, false>(B, grid, threads, s); break;
-            case 1: ok = launch_hop_window<P, 18, false, true>(B, grid, threads, s); break;
-            case 2: ok = launch_hop_window<P, 18, true, false>(B, grid, threads, s); break;
-            case 3: ok = launch_hop_window<P, 18, true, true>(B, grid, threads, s); break;
-            case 4: ok = launch_hop_window<P, 12, false, false>(B, grid, threads, s); break;
-            case 5: ok = launch_hop_window<P, 12, false, true>(B, grid, threads, s); break;
-            case 6: ok = launch_hop_window<P, 12, true, false>(B, grid, threads, s); break;
-            case 7: ok = launch_hop_window<P, 12, true, true>(B, grid, threads, s); break;
+            case 0: ok = launch_hop_window<P, 18, false, false>(B, grid, threads, s, e); break;
+            case 1: ok = launch_hop_window<P, 18, false, true>(B, grid, threads, s, e); break;
+            case 2: ok = launch_hop_window<P, 18, true, false>(B, grid, threads, s, e); break;
+            case 3: ok = launch_hop_window<P, 18, true, true>(B, grid, threads, s, e); break;
+            case 4: ok = launch_hop_window<P, 12, false, false>(B, grid, threads, s, e); break;
+            case 5: ok = launch_hop_window<P, 12, false, true>(B, grid, threads, s, e); break;
+            case 6: ok = launch_hop_window<P, 12, true, false>(B, grid, threads, s, e); break;
+            case 7: ok = launch_hop_window<P, 12, true, true>(B, grid, threads, s, e); break;
             }
         }
-        if (ok) return cudaGetLastError();
+        if (ok) return e;
         pf = 1;   // window larger than 48 KB, or an open-boundary pass: schedule 1
     }
     if (pf == HOP_2SITE_VARIANT) pf = 1;   // open-boundary pass
     switch (key) {
-    case 0: launch_hop_pf<P, 18, false, false>(B, grid, threads, pf, s); break;
-    case 1: launch_hop_pf<P, 18, false, true>(B, grid, threads, pf, s); break;
-    case 2: launch_hop_pf<P, 18, true, false>(B, grid, threads, pf, s); break;
-    case 3: launch_hop_pf<P, 18, true, true>(B, grid, threads, pf, s); break;
-    case 4: launch_hop_pf<P, 12, false, false>(B, grid, threads, pf, s); break;
-    case 5: launch_hop_pf<P, 12, false, true>(B, grid, threads, pf, s); break;
-    case 6: launch_hop_pf<P, 12, true, false>(B, grid, threads, pf, s); break;
-    case 7: launch_hop_pf<P, 12, true, true>(B, grid, threads, pf, s); break;
+    case 0: return launch_hop_pf<P, 18, false, false>(B, grid, threads, pf, s);
+    case 1: return launch_hop_pf<P, 18, false, true>(B, grid, threads, pf, s);
+    case 2: return launch_hop_pf<P, 18, true, false>(B, grid, threads, pf, s);
+    case 3: return launch_hop_pf<P, 18, true, true>(B, grid, threads, pf, s);
+    case 4: return launch_hop_pf<P, 12, false, false>(B, grid, threads, pf, s);
+    case 5: return launch_hop_pf<P, 12, false, true>(B, grid, threads, pf, s);
+    case 6: return launch_hop_pf<P, 12, true, false>(B, grid, threads, pf, s);
+    default: return launch_hop_pf<P, 12, true, true>(B, grid, threads, pf, s);
     }
-    return cudaGetLastError();
 }
 
 } // namespace wd

@@ -232,12 +232,12 @@ __global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 3) hop_mrhs_kernel(co
 }
 
 template <int P, int RECON, bool DAG, bool HX>
-void launch_hop_mrhs(const HopArgs &A, int nrhs, int threads, int zs, cudaStream_t s)
+cudaError_t launch_hop_mrhs(const HopArgs &A, int nrhs, int threads, int zs, cudaStream_t s)
 {
     const int ry = threads / 32;
     const int per = (A.vh + 31) / 32;
     if (zs <= 0 || zs >= A.L[2]) zs = 0;
-    wd_launch(hop_mrhs_kernel<P, RECON, DAG, HX>, dim3((unsigned)(per * A.nparity)), dim3(32, ry), 0, s, A, nrhs, zs);
+    return wd_launch(hop_mrhs_kernel<P, RECON, DAG, HX>, dim3((unsigned)(per * A.nparity)), dim3(32, ry), 0, s, A, nrhs, zs);
 }
 
 } // namespace wd

@@ -182,11 +182,11 @@ __global__ void __launch_bounds__(256, 2) hop_window_kernel(const HopArgs A)
 // Launches the windowed kernel; false (nothing launched) if its shared memory
 // would exceed the default 48 KB per block.
 template <int P, int RECON, bool DAG, bool HX>
-bool launch_hop_window(const HopArgs &A, dim3 grid, int threads, cudaStream_t s)
+bool launch_hop_window(const HopArgs &A, dim3 grid, int threads, cudaStream_t s, cudaError_t &err)
 {
     const size_t smem = window_bytes<P>(threads, A.L[0] >> 1);
     if (smem > 48 * 1024) return false;
-    wd_launch(hop_window_kernel<P, RECON, DAG, HX>, grid, dim3(threads), smem, s, A);
+    err = wd_launch(hop_window_kernel<P, RECON, DAG, HX>, grid, dim3(threads), smem, s, A);
     return true;
 }
 
@@ -209,10 +209,10 @@ __global__ void __launch_bounds__(256, 2) hop_2site_kernel(const HopArgs A)
 }
 
 template <int P, int RECON, bool DAG, bool HX>
-void launch_hop_2site(const HopArgs &A, int nrhs, int threads, cudaStream_t s)
+cudaError_t launch_hop_2site(const HopArgs &A, int nrhs, int threads, cudaStream_t s)
 {
     const int per = (A.vh + 2 * threads - 1) / (2 * threads);
-    wd_launch(hop_2site_kernel<P, RECON, DAG, HX>, dim3((unsigned)(per * A.nparity), (unsigned)nrhs), dim3(threads),
+    return wd_launch(hop_2site_kernel<P, RECON, DAG, HX>, dim3((unsigned)(per * A.nparity), (unsigned)nrhs), dim3(threads),
               0, s, A);
 }
 

@@ -87,3 +87,17 @@ extern "C" int wd_device_info(const wd_ctx *ctx, wd_device_props *out)
     out->nominal_hbm_gbs = 2.0 * (double)v[1] * 1e3 * (double)v[2] / 8.0 / 1e9;
     return WD_OK;
 }
+
+extern "C" int wd_device_status(wd_ctx *ctx, int *code)
+{
+    clear_error();
+    if (!ctx || !code) return set_error(WD_EINVAL, "NULL argument");
+    DeviceGuard dg(ctx->device);
+    WD_CUDA_TRY(cudaDeviceSynchronize());
+    int *w = ctx_status_word(ctx);
+    int v = 0;
+    WD_CUDA_TRY(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v != 0) WD_CUDA_TRY(cudaMemset(w, 0, sizeof(int)));
+    *code = v;
+    return WD_OK;
+}

@@ -99,6 +99,10 @@ struct wd_gauge {
 
 namespace wd {
 constexpr int NSCAL = 64;
+// Device status word of a context: word 32 of the 64-word ticket buffer (word
+// 0 is the reduction ticket).  Kernels with bounded waits write their error
+// code here; wd_device_status reads and clears it.
+inline int *ctx_status_word(const wd_ctx *c) { return c ? reinterpret_cast<int *>(c->d_ticket + 32) : nullptr; }
 // Even-odd hop on half fields: out_p = a x_p + b H^(d)_{p,1-p} in (see dslash_eo_apply).
 int eo_hop(const wd_gauge *g, int prec, int recon, void *out, const void *in, const void *x, int p, double a,
            double b, int dagger, cudaStream_t s);
