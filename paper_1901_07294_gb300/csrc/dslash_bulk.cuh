@@ -17,10 +17,17 @@
 // with their links, the t neighbour and x read from shared memory.  The
 // copies take no registers and no load instructions of the computing warps.
 //
-// The wait is bounded (about one second of clock cycles); on expiry the block
-// writes WD_ETIMEOUT to the context's status word, waits once more (bounded)
-// for its copies, and returns without writing its output.
+// The wait is bounded (one second of clock cycles by default,
+// WD_BULK_TIMEOUT_S); on expiry the block writes WD_ETIMEOUT to the context's
+// status word, waits once more (bounded) for its copies, and returns without
+// writing its output.  Tests make the wait run out with a host-side switch
+// (WD_FAULT=bulk_tx) that makes the barrier expect 16 bytes more than are
+// copied.
 #pragma once
+
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
 
 #include "dslash_impl.cuh"
 #include "wdirac.h"
@@ -72,7 +79,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  : "memory");
 }
 
-constexpr long long BULK_WAIT_CYCLES = 2000000000LL;   // about one second at GB300 clocks
 
 // Shared-memory image of the staged data for B sites: per mu the link planes
 // (main planes, then the tail plane) of the forward links, then the t-forward
@@ -182,12 +188,13 @@ __device__ __forceinline__ void hop_dir_loaded(const typename Prec<P>::real (&ps
 // Issues the block's bulk copies (called by all 32 lanes of one warp).
 template <int P, int RECON, bool HAS_X>
 __device__ __forceinline__ void bulk_issue(unsigned char *tile, int b, const char *gf, size_t lb, int vh, int i0,
-                                           const char *in, int j0, const char *x, unsigned long long *bar, int lane)
+                                           const char *in, int j0, const char *x, unsigned long long *bar, int lane,
+                                           unsigned extra_tx)
 {
     using BT = BulkTile<P, RECON>;
     constexpr int nl = 4 * BT::lcopies;
     constexpr int nc = nl + BT::scopies * (HAS_X ? 2 : 1);
-    if (lane == 0) mbar_arrive_expect_tx(bar, (unsigned)BT::bytes(b, HAS_X));
+    if (lane == 0) mbar_arrive_expect_tx(bar, (unsigned)BT::bytes(b, HAS_X) + extra_tx);
     __syncwarp();
     for (int c = lane; c < nc; c += 32) {
         unsigned char *dst;
@@ -226,7 +233,8 @@ __device__ __forceinline__ void bulk_issue(unsigned char *tile, int b, const cha
 }
 
 template <int P, int RECON, bool DAG, bool HAS_X>
-__global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 2) hop_bulk_kernel(const HopArgs A)
+__global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 2) hop_bulk_kernel(const HopArgs A, const unsigned extra_tx,
+                                                                            const long long limit)
 {
     using T = typename Prec<P>::real;
     using BT = BulkTile<P, RECON>;
@@ -254,7 +262,7 @@ __global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 2) hop_bulk_kernel(co
     __syncthreads();
     if (s < 32)
         bulk_issue<P, RECON, HAS_X>(bulk_smem, b, gf, lb, vh, i0, in, j0,
-                                    HAS_X ? (p ? A.x[1] : A.x[0]) + roff : nullptr, &bar, s);
+                                    HAS_X ? (p ? A.x[1] : A.x[0]) + roff : nullptr, &bar, s, extra_tx);
 
     // site coordinates (as in hop_site)
     const int r = div_inv(i, A.div_m[0], A.div_s[0]);
@@ -287,9 +295,9 @@ __global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 2) hop_bulk_kernel(co
     hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, false, acc);
     hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
 
-    if (!mbar_wait_bounded(&bar, 0, BULK_WAIT_CYCLES)) {
+    if (!mbar_wait_bounded(&bar, 0, limit)) {
         if (A.status) atomicExch(A.status, WD_ETIMEOUT);
-        mbar_wait_bounded(&bar, 0, BULK_WAIT_CYCLES);   // let the copies land before the block exits
+        mbar_wait_bounded(&bar, 0, limit);   // let the copies land before the block exits
         return;
     }
     const unsigned char *lt = bulk_smem;
@@ -336,6 +344,24 @@ __global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 2) hop_bulk_kernel(co
     Spinor<P>::store((p ? A.out[1] : A.out[0]) + roff, vh, i, o);
 }
 
+// SM clock of the current device in kHz, queried once per device (the query
+// takes hundreds of microseconds, far longer than the launch it serves).
+inline int device_clock_khz()
+{
+    static std::atomic<int> cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 2000000;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrClockRate, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 2000000;
+        }
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
 // Launches the staged kernel if the problem allows it (every block inside one
 // t-slice, all bases and plane offsets 16-byte aligned, no open boundary);
 // returns false otherwise and the caller uses schedule 1.
@@ -358,7 +384,13 @@ bool launch_hop_bulk(const HopArgs &A, dim3 grid, int threads, cudaStream_t s, c
         cudaGetLastError();
         return false;
     }
-    err = wd_launch(hop_bulk_kernel<P, RECON, DAG, HX>, grid, dim3(threads), smem, s, A);
+    // host-side fault injection for tests (WD_FAULT=bulk_tx) and the wait limit
+    const char *fault = std::getenv("WD_FAULT");
+    const unsigned extra_tx = (fault && std::strstr(fault, "bulk_tx")) ? 16u : 0u;
+    double limit_s = 1.0;
+    if (const char *ls = std::getenv("WD_BULK_TIMEOUT_S")) limit_s = std::atof(ls);
+    const long long limit = (long long)(limit_s * device_clock_khz() * 1e3);
+    err = wd_launch(hop_bulk_kernel<P, RECON, DAG, HX>, grid, dim3(threads), smem, s, A, extra_tx, limit);
     return true;
 }
 

@@ -133,3 +133,29 @@ def test_autotuner_includes_staged_kernel(ctx):
     table = wd.tune_dslash(ctx, g, wd.F32, 18, full=True)
     assert {t["variant"] for t in table} == {0, 1, 2, 4, 8, 9, BULK}
     assert all(np.isfinite(t["ms"]) and t["ms"] > 0 for t in table)
+
+
+def test_bounded_wait_reports_timeout_and_context_recovers(monkeypatch):
+    """The barrier is made to expect 16 bytes more than the copies bring (a host-side switch),
+    so its phase never completes: every block gives up after its bounded wait (0.1 s here),
+    records WD_ETIMEOUT in the context's status word and returns.  The next launch on the
+    same context is correct and reports nothing."""
+    ctx = wd.Context(0)
+    dims = (8, 8, 8, 8)   # 64 blocks of 64 threads: all resident at once
+    U = synth.gauge(dims, seed=1605)
+    psi = synth.spinor(dims, seed=3605)
+    g = wd.Gauge(ctx, dims, U)
+    wd.tune_set_dslash(ctx, g, wd.F32, 18, True, True, 1, 64, BULK)
+    fin = pack_field(ctx, dims, wd.SITES_FULL, wd.F32, psi)
+    fout = wd.alloc_field(dims, wd.SITES_FULL, wd.F32)
+    assert wd.device_status(ctx) == 0
+    monkeypatch.setenv("WD_FAULT", "bulk_tx")
+    monkeypatch.setenv("WD_BULK_TIMEOUT_S", "0.1")
+    wd.dslash_apply(ctx, g, fout, fin, 0.1, prec=wd.F32)
+    assert wd.device_status(ctx) == wd.WD_ETIMEOUT
+    assert wd.device_status(ctx) == 0   # read and cleared
+    monkeypatch.delenv("WD_FAULT")
+    wd.dslash_apply(ctx, g, fout, fin, 0.1, prec=wd.F32)
+    check_dslash(unpack_field(ctx, dims, wd.SITES_FULL, wd.F32, fout), oracle.dirac(dims, U, psi, 0.1), wd.F32,
+                 dims, U, psi, 18, lambda u, p: oracle.dirac(dims, u, p, 0.1))
+    assert wd.device_status(ctx) == 0
