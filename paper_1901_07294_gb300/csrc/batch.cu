@@ -336,9 +336,7 @@ int run_persistent(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stat
     const int extra = (fault && std::strstr(fault, "barrier_missing")) ? 1 : 0;
     double limit_s = 1.0;
     if (const char *ls = std::getenv("WD_BARRIER_TIMEOUT_S")) limit_s = std::atof(ls);
-    int clock_khz = 0;
-    cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, ctx->device);
-    const long long limit = (long long)(limit_s * (clock_khz > 0 ? clock_khz : 2000000) * 1e3);
+    const long long limit = (long long)(limit_s * device_clock_khz(ctx->device) * 1e3);
 
     int done = 0;
     while (done < n) {

@@ -25,7 +25,6 @@
 // copied.
 #pragma once
 
-#include <atomic>
 #include <cstdlib>
 #include <cstring>
 
@@ -342,24 +341,6 @@ __global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 2) hop_bulk_kernel(co
             }
     }
     Spinor<P>::store((p ? A.out[1] : A.out[0]) + roff, vh, i, o);
-}
-
-// SM clock of the current device in kHz, queried once per device (the query
-// takes hundreds of microseconds, far longer than the launch it serves).
-inline int device_clock_khz()
-{
-    static std::atomic<int> cache[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 2000000;
-    int v = cache[dev].load(std::memory_order_relaxed);
-    if (v == 0) {
-        if (cudaDeviceGetAttribute(&v, cudaDevAttrClockRate, dev) != cudaSuccess || v <= 0) {
-            cudaGetLastError();
-            v = 2000000;
-        }
-        cache[dev].store(v, std::memory_order_relaxed);
-    }
-    return v;
 }
 
 // Launches the staged kernel if the problem allows it (every block inside one

@@ -11,6 +11,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <tuple>
 #include <type_traits>
@@ -58,6 +59,25 @@ cudaError_t wd_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sm
     if (e == cudaSuccess) g->last = node;
     else if (g->err == cudaSuccess) g->err = e;
     return e;
+}
+
+// SM clock of device `dev` (-1: the current one) in kHz, queried once per
+// device: the query takes hundreds of microseconds, far longer than a launch.
+// Used to turn the bounded waits' limits from seconds into clock cycles.
+inline int device_clock_khz(int dev = -1)
+{
+    static std::atomic<int> cache[64] = {};
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return 2000000;
+    if (dev < 0 || dev >= 64) return 2000000;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrClockRate, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 2000000;
+        }
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
 }
 
 } // namespace wd
