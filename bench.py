@@ -447,7 +447,7 @@ def _per_launch_ms(torch, fn, stream, reps, flush=None):
     return sum(ts) / len(ts), statistics.median(ts)
 
 
-def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, fp64_tflops=None, reps=50):
+def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, fp64_tflops=None, reps=100):
     """Per-launch times and GB/s of every operator variant of the 32^4 / 16^3x32 configuration:
     mean and median over `reps` launches timed one by one, warm (the inputs of consecutive
     launches may still be in L2: 16^3x32 FP32 is about 63 MB) and with L2 flushed (a buffer of
@@ -488,7 +488,7 @@ def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, fp64_tf
                         fn = lambda: wd.dslash_eo_apply(ctx, g, eo_out, eo_in, None, wd.EVEN, 0.0, 1.0,
                                                         prec=prec, recon=recon, stream=stream)
                         nsite = v // 2
-                    for _ in range(5):
+                    for _ in range(10):
                         fn()
                     ms, med = _per_launch_ms(torch, fn, stream, reps)
                     ms_fl, med_fl = _per_launch_ms(torch, fn, stream, reps, flush=flush)
@@ -785,7 +785,7 @@ def _batch_section(wd, torch, ctx, peak):
     return out
 
 
-def _serving_section(wd, torch, ctx, n_main=600, n_sweep=150, warm=60):
+def _serving_section(wd, torch, ctx, n_main=2000, n_sweep=150, warm=100):
     """Serving: Poisson arrivals of CG solve requests (volumes uniform over 8^4, 16^4, 24^3x48,
     32^3x64; masses log-uniform in [0.02, 0.5]; tolerances in {1e-8, 1e-10, 1e-12}) on resident
     smoothed-SU(3) configurations, continuous batching with HBM admission.  Headline at 200 req/s
@@ -861,7 +861,8 @@ def _serving_section(wd, torch, ctx, n_main=600, n_sweep=150, warm=60):
                 "max_true_resid_over_tol": round(max(r["cg_true_rel_resid"] / t for t, r in zip(tols, res)), 4)}
 
     out = {"volumes": [list(v) for v in vols], "inner": "fp16 storage, fp32 compute, fp64 reliable updates",
-           "queue": {"hbm_budget_gb": 48, "max_slots": 32, "iterations_per_step": 8}}
+           "queue": {"hbm_budget_gb": 48, "max_slots": 32, "max_iterations_per_launch": 32,
+                     "scheduling": "each request advanced when its own stream is idle"}}
     results, st = run(200.0, n_main + warm, 5001)
     out["rate_200"] = summarise(results, st, 200.0, warm)
     out["sweep"] = []
@@ -978,7 +979,7 @@ def _cg_section(wd, torch, ctx, with_cpu: bool, peak: float):
         for name, kw in runs:
             wd.cg_solve(ctx, g, mass, fx, fb, tol=1e-10, maxiter=20000, autotune=True, **kw)   # warm: layouts, workspace, tuning
             best = None
-            for _ in range(2):
+            for _ in range(3):   # best of 3
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 st = wd.cg_solve(ctx, g, mass, fx, fb, tol=1e-10, maxiter=20000, **kw)

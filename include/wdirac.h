@@ -434,12 +434,15 @@ int cg_solve_batch(wd_ctx *ctx, int n, const wd_solve_desc *descs, int mode, wd_
  * wd_solve_desc problems (mixed-precision reliable-update CG: inner_prec
  * WD_F32, WD_F16 or WD_BF16) whose gauge and fields stay resident; x_e and b_e
  * are the caller's device buffers and must stay valid until the request's
- * result has been taken.  Each scheduler step admits waiting requests while
- * fewer than max_slots run and their workspace fits hbm_budget_bytes (first
- * come first served, a request that fits may pass one that does not), runs 8
- * CG iterations of every running request (each on its own stream, so they
- * overlap), then checks residuals, does FP64 reliable updates and retires
- * finished requests.  Requests join and leave between steps.
+ * result has been taken.  The scheduler admits waiting requests while fewer
+ * than max_slots run and their workspace fits hbm_budget_bytes (first come
+ * first served, a request that fits may pass one that does not).  Each running
+ * request has its own stream and a graph whose device-side loop runs CG
+ * iterations until a reliable update is due (at most 32 per launch).  The
+ * scheduler polls the streams and advances each idle request on its own:
+ * it enqueues the FP64 reliable update, or relaunches the loop, or retires
+ * the converged request.  No request waits for another, and requests join
+ * and leave at any time.
  *   rq_submit: non-blocking, thread-safe; copies the descriptor; WD_ENOMEM if
  *              the request alone exceeds the budget.
  *   rq_poll:   WD_EBUSY while running; otherwise fills the result and forgets
@@ -447,7 +450,7 @@ int cg_solve_batch(wd_ctx *ctx, int n, const wd_solve_desc *descs, int mode, wd_
  *   rq_wait:   blocks up to timeout_ms (< 0: forever); WD_ETIMEOUT if still
  *              running (the request keeps running).
  *   rq_cancel: a waiting request ends at once with WD_ECANCELLED; a running one
- *              at the end of the current step.
+ *              when its current launch or reliable update has finished.
  *   rq_destroy: finishes every submitted request, then stops and frees.
  * Times in wd_solve_result are seconds since rq_create.  A request whose
  * source is not finite ends with WD_EINVAL without affecting the others. */
@@ -460,8 +463,8 @@ typedef struct {
 } wd_solve_result;
 
 typedef struct {
-    uint64_t submitted, completed, admission_stalls, steps;
-    double mean_running;     /* running requests per scheduler step, averaged */
+    uint64_t submitted, completed, admission_stalls, steps;   /* steps: device-loop launches */
+    double mean_running;     /* running requests, averaged over the time any request runs */
     int waiting, running;
     size_t hbm_in_use;
 } rq_counters;

@@ -73,6 +73,7 @@ struct GSolve {
     double b2 = 0, stop2 = 0, maxr = 0;
     int iters = 0, updates = 0, status = WD_OK, iters_at_update = 0;
     bool active = true;
+    bool broke = false;   // the last launch stopped on a breakdown (set by gs_after_begin)
     double rel = 1.0;
 };
 
@@ -284,16 +285,19 @@ inline int gs_launch(GSolve &q)
     return WD_OK;
 }
 
-// After a launch has finished: reliable update and convergence test when
-// the loop stopped for one of them (not merely at the per-launch cap).
-inline int gs_after(const wd_ctx *ctx, GSolve &q)
+// First half of the work after a launch has finished: if the loop stopped
+// for a reliable update or the convergence test (not merely at the
+// per-launch cap), enqueues the FP64 update on the solve's stream and sets
+// *pending; the caller then waits for the stream and calls gs_after_update.
+inline int gs_after_begin(const wd_ctx *ctx, GSolve &q, bool &pending)
 {
+    pending = false;
     q.iters = (int)q.h[11];
     const double r2 = q.h[0];
-    const bool broke = q.h[6] != 0.0 || !std::isfinite(r2);
+    q.broke = q.h[6] != 0.0 || !std::isfinite(r2);
     const double rn = std::sqrt(r2);
     q.maxr = q.h[8];
-    if (!(broke || rn < q.opts.delta * q.maxr || r2 <= q.stop2 || q.iters >= q.opts.maxiter ||
+    if (!(q.broke || rn < q.opts.delta * q.maxr || r2 <= q.stop2 || q.iters >= q.opts.maxiter ||
           (int)q.h[10] >= RELIABLE_MAX_GAP))
         return WD_OK;
     q.iters_at_update = q.iters;
@@ -304,7 +308,16 @@ inline int gs_after(const wd_ctx *ctx, GSolve &q)
     default: rc = gs_detail::reliable_update<PREC_F32>(ctx, q); break;
     }
     if (rc) return rc;
-    WD_CUDA_TRY(cudaStreamSynchronize(q.s));
+    pending = true;
+    return WD_OK;
+}
+
+// Second half, once the update's work has finished: reads the true residual,
+// ends the solve or enqueues the restart scalars on the stream.  It does not
+// wait for them: the next launch on the same stream runs after them, and the
+// host writes the scalar buffer again only after that launch has finished.
+inline int gs_after_update(GSolve &q)
+{
     const double r2t = q.h[7];
     q.updates++;
     q.rel = std::sqrt(r2t / q.b2);
@@ -321,7 +334,7 @@ inline int gs_after(const wd_ctx *ctx, GSolve &q)
     // s[0] = true |r|^2, so the next direction update uses beta = |r_true|^2 / |r_old|^2
     // (s[4] still holds |r_old|^2); after a breakdown restart with p = r (s[4] = inf)
     WD_CUDA_TRY(cudaMemcpyAsync(q.scal, &q.h[7], sizeof(double), cudaMemcpyHostToDevice, q.s));
-    if (broke) {
+    if (q.broke) {
         static const double restart[3] = {INFINITY, 0.0, 0.0};   // s[4], s[5], s[6]
         WD_CUDA_TRY(cudaMemcpyAsync(q.scal + 4, restart, sizeof(restart), cudaMemcpyHostToDevice, q.s));
     }
@@ -330,6 +343,18 @@ inline int gs_after(const wd_ctx *ctx, GSolve &q)
     q.h[10] = 0.0;
     WD_CUDA_TRY(cudaMemcpyAsync(q.scal + 8, q.h + 8, sizeof(double), cudaMemcpyHostToDevice, q.s));
     WD_CUDA_TRY(cudaMemcpyAsync(q.scal + 10, q.h + 10, sizeof(double), cudaMemcpyHostToDevice, q.s));
+    return WD_OK;
+}
+
+// After a launch has finished: reliable update and convergence test when the
+// loop stopped for one of them (both halves above, waiting for each).
+inline int gs_after(const wd_ctx *ctx, GSolve &q)
+{
+    bool pending = false;
+    WD_TRY(gs_after_begin(ctx, q, pending));
+    if (!pending) return WD_OK;
+    WD_CUDA_TRY(cudaStreamSynchronize(q.s));
+    WD_TRY(gs_after_update(q));
     WD_CUDA_TRY(cudaStreamSynchronize(q.s));
     return WD_OK;
 }

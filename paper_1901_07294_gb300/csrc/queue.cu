@@ -1,15 +1,18 @@
 // Solve-request queue with continuous batching.
 //
 // Requests (cg_solve problems on resident gauge fields) are submitted from any
-// host thread and run by one scheduler thread.  Each scheduler step admits
-// waiting requests while free slots and the HBM budget allow (first come
-// first served, but a request that fits may pass one that does not), sets up
-// the admitted ones (workspace, stream, a CUDA graph whose device-side loop
-// runs CG iterations until a reliable update is due), launches the graph of
-// every running request on its own stream (so their work overlaps on the
-// GPU), then does each request's FP64 reliable update and convergence test,
-// retires the finished ones and frees their memory.  Requests therefore join
-// and leave the running batch between steps.
+// host thread and run by one scheduler thread.  In each pass the scheduler
+// admits waiting requests while free slots and the HBM budget allow (first
+// come first served, but a request that fits may pass one that does not),
+// sets up the admitted ones (workspace, stream, a CUDA graph whose
+// device-side loop runs CG iterations until a reliable update is due) and
+// launches their loops, each on its own stream so that all running requests'
+// work overlaps on the GPU.  It then polls the running requests' streams and
+// advances only those that are idle: after a loop has stopped it enqueues the
+// FP64 reliable update (or relaunches the loop); after an update has finished
+// it tests convergence and relaunches or retires the request.  No request
+// waits for another's loop or update, so small and large volumes proceed at
+// their own pace and requests join and leave at any time.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -32,6 +35,7 @@ struct Req {
     wd_solve_desc d{};
     size_t foot = 0;
     bool cancel = false, done = false;
+    bool updating = false;   // its FP64 reliable update is in flight (scheduler thread only)
     wd_solve_result res{};
     wd::GSolve gs;
 };
@@ -54,7 +58,8 @@ struct rq_queue {
     clk::time_point t0;
     // counters
     uint64_t submitted = 0, completed = 0, stalls = 0, steps = 0, admitted = 0;
-    double occupancy_sum = 0.0;
+    double occupancy_sum = 0.0;   // integral of the running count over time (seconds)
+    double busy_s = 0.0;          // time with at least one request running
     int fault_alloc_at = 0;   // WD_FAULT=alloc:N -> the N-th admission fails
     // idle workspaces of finished requests, reused by requests of the same
     // footprint (scheduler thread only); they count against the budget
@@ -138,9 +143,55 @@ void park(rq_queue *q, Req *r)
     r->gs.s = nullptr;
 }
 
+// Ends a running request whose stream is idle: returns its workspace to the
+// pool (or frees it after a CUDA error) and publishes the result.
+void retire(rq_queue *q, Req *r, int rc)
+{
+    if (rc == WD_ECUDA) gs_release(r->gs);
+    else park(q, r);
+    finish(q, r, rc != WD_OK ? rc : r->gs.status);
+}
+
+// Advances one running request whose stream has gone idle.  Returns true if it
+// keeps running (a new launch or its reliable update is in flight).
+bool advance(rq_queue *q, Req *r)
+{
+    bool cancel;
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        cancel = r->cancel;
+    }
+    int rc = WD_OK;
+    if (cancel) rc = WD_ECANCELLED;
+    else if (r->gs.status == WD_OK) {
+        if (r->updating) {           // its FP64 reliable update has finished
+            r->updating = false;
+            rc = gs_after_update(r->gs);
+        } else {                     // its device loop has stopped
+            bool pending = false;
+            rc = gs_after_begin(q->ctx, r->gs, pending);
+            if (rc == WD_OK && pending) {
+                r->updating = true;
+                return true;
+            }
+        }
+    }
+    if (rc == WD_OK && r->gs.active && r->gs.status == WD_OK) {
+        if (gs_launch(r->gs) == WD_OK) {
+            std::lock_guard<std::mutex> lk(q->mu);
+            q->steps++;
+            return true;
+        }
+        rc = WD_ECUDA;
+    }
+    retire(q, r, rc);
+    return false;
+}
+
 void scheduler(rq_queue *q)
 {
     cudaSetDevice(q->ctx->device);
+    auto last = clk::now();
     for (;;) {
         std::vector<Req *> admit;
         {
@@ -162,7 +213,7 @@ void scheduler(rq_queue *q)
             }
             if (stalled) q->stalls++;
         }
-        // set up the admitted requests outside the lock
+        // set up the admitted requests outside the lock and start their loops
         for (Req *r : admit) {
             r->res.t_admit = now_s(q);
             q->admitted++;
@@ -182,45 +233,57 @@ void scheduler(rq_queue *q)
                 finish(q, r, r->gs.status);
                 continue;
             }
-            std::lock_guard<std::mutex> lk(q->mu);
-            q->running.push_back(r);
-        }
-        if (q->running.empty()) continue;
-        // one step of every running request
-        {
+            if (gs_launch(r->gs) != WD_OK) {
+                gs_release(r->gs);
+                finish(q, r, WD_ECUDA);
+                continue;
+            }
             std::lock_guard<std::mutex> lk(q->mu);
             q->steps++;
-            q->occupancy_sum += (double)q->running.size();
+            q->running.push_back(r);
         }
-        for (Req *r : q->running) {
-            bool cancel;
-            {
-                std::lock_guard<std::mutex> lk(q->mu);
-                cancel = r->cancel;
-            }
-            if (!cancel && gs_launch(r->gs) != WD_OK) r->gs.status = WD_ECUDA;
+        std::vector<Req *> running;
+        {
+            std::lock_guard<std::mutex> lk(q->mu);
+            running = q->running;
         }
+        // time-weighted occupancy while requests run
+        const auto t = clk::now();
+        const double dt = std::chrono::duration<double>(t - last).count();
+        last = t;
+        if (running.empty()) continue;
+        {
+            std::lock_guard<std::mutex> lk(q->mu);
+            q->busy_s += dt;
+            q->occupancy_sum += dt * (double)running.size();
+        }
+        // advance every request whose stream is idle; the others keep running
+        bool progress = !admit.empty();
         std::vector<Req *> keep;
-        for (Req *r : q->running) {
-            bool cancel;
-            {
-                std::lock_guard<std::mutex> lk(q->mu);
-                cancel = r->cancel;
-            }
-            int rc = WD_OK;
-            if (cudaStreamSynchronize(r->gs.s) != cudaSuccess) rc = WD_ECUDA;
-            else if (cancel) rc = WD_ECANCELLED;
-            else if (r->gs.status == WD_OK) rc = gs_after(q->ctx, r->gs);
-            if (rc == WD_OK && r->gs.active && r->gs.status == WD_OK) {
+        for (Req *r : running) {
+            const cudaError_t qe = cudaStreamQuery(r->gs.s);
+            if (qe == cudaErrorNotReady) {
                 keep.push_back(r);
                 continue;
             }
-            if (rc == WD_ECUDA) gs_release(r->gs);
-            else park(q, r);
-            finish(q, r, rc != WD_OK ? rc : r->gs.status);
+            progress = true;
+            if (qe != cudaSuccess) {
+                cudaGetLastError();
+                retire(q, r, WD_ECUDA);
+                continue;
+            }
+            if (advance(q, r)) keep.push_back(r);
         }
-        std::lock_guard<std::mutex> lk(q->mu);
-        q->running.swap(keep);
+        {
+            std::lock_guard<std::mutex> lk(q->mu);
+            q->running.swap(keep);
+        }
+        // nothing finished: wait briefly, or until a new request arrives
+        if (!progress) {
+            std::unique_lock<std::mutex> lk(q->mu);
+            q->cv_work.wait_for(lk, std::chrono::microseconds(20),
+                                [q] { return q->stop || (!q->waiting.empty() && (int)q->running.size() < q->max_slots); });
+        }
     }
     for (auto &e : q->pool) free_idle(e);
     q->pool.clear();
@@ -363,7 +426,7 @@ int rq_cancel(rq_queue *q, uint64_t ticket)
         q->completed++;
         q->cv_done.notify_all();
     } else {
-        r->cancel = true;   // retired by the scheduler at the end of its current step
+        r->cancel = true;   // retired by the scheduler once its stream is idle
     }
     return WD_OK;
 }
@@ -377,7 +440,7 @@ int rq_stats(rq_queue *q, rq_counters *out)
     out->completed = q->completed;
     out->admission_stalls = q->stalls;
     out->steps = q->steps;
-    out->mean_running = q->steps ? q->occupancy_sum / (double)q->steps : 0.0;
+    out->mean_running = q->busy_s > 0.0 ? q->occupancy_sum / q->busy_s : 0.0;
     out->waiting = (int)q->waiting.size();
     out->running = (int)q->running.size();
     out->hbm_in_use = q->in_use;
