@@ -208,7 +208,9 @@ int wd_device_status(wd_ctx *ctx, int *code);
  * neighbours and x term copied into shared memory by bulk (TMA) copies that
  * complete on an mbarrier while the backward directions run; 10 applies when
  * the block size divides Lx/2*Ly*Lz and every plane is 16-byte aligned, and
- * is schedule 1 otherwise).
+ * is schedule 1 otherwise; 11, 12: schedules 0 and 1 with the links loaded
+ * without L1 allocation, which suits even-odd hops, where each link is read
+ * once per call).
  * wd_tune_dslash times every candidate for one problem shape (full = 1: the
  * dslash_apply shape; full = 0: dslash_eo_apply with (with_x = 1) or without
  * the x term) on private scratch fields (allocated and freed by the call),

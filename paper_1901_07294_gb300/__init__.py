@@ -441,10 +441,10 @@ def norm2_noalloc(dims, sites: int, prec: int, x, result, stream=None) -> None:
 def tune_dslash(ctx: Context, gauge: Gauge, prec: int, recon: int, full: bool, with_x: bool = False,
                 nrhs: int = 1) -> list[dict]:
     """Time every launch candidate of one operator shape; the fastest is kept in ctx."""
-    table = (TuneEntry * 32)()
+    table = (TuneEntry * 64)()
     n = _ip(0)
     _check(load().wd_tune_dslash(ctx.handle, gauge.handle, int(prec), int(recon), int(bool(full)),
-                                 int(bool(with_x)), int(nrhs), table, 32, ctypes.byref(n)))
+                                 int(bool(with_x)), int(nrhs), table, 64, ctypes.byref(n)))
     return [{"threads": table[k].threads, "variant": table[k].variant, "ms": table[k].ms} for k in range(n.value)]
 
 

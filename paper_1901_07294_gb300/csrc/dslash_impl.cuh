@@ -123,7 +123,7 @@ __device__ __forceinline__ void su3_mul(const cpx<T> (&U)[3][3], const cpx<T> (&
 // stored reals.  neg: the hop crosses an antiperiodic boundary, U h changes
 // sign (done here rather than in the stored links, whose 12-real form
 // rebuilds row 3 assuming det U = 1).
-template <int P, int RECON, int MU, int S, bool FWD>
+template <int P, int RECON, int MU, int S, bool FWD, bool LNA = false>
 __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh, int nb, int li, bool neg,
                                         cpx<typename Prec<P>::real> (&acc)[4][3])
 {
@@ -133,7 +133,7 @@ __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh
     cpx<T> h0[3], h1[3];
     project<MU, S>(psi, h0, h1);
     cpx<T> U[3][3];
-    Link<link_prec(P), RECON>::load(lblk, vh, li, U);
+    Link<link_prec(P), RECON>::template load<LNA>(lblk, vh, li, U);
     cpx<T> w0[3], w1[3];
     su3_mul<FWD>(U, h0, w0);
     su3_mul<FWD>(U, h1, w1);
@@ -167,7 +167,7 @@ __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh
 // at byte offset roff.  Shared by hop_kernel and the persistent solver.
 // TOPEN: the t boundary is open (a sub-domain of a decomposed lattice): the
 // hops across it are skipped; their halo terms are added separately.
-template <int P, int RECON, bool DAG, bool HAS_X, int PF, bool TOPEN = false>
+template <int P, int RECON, bool DAG, bool HAS_X, int PF, bool TOPEN = false, bool LNA = false>
 __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const int i, const size_t roff)
 {
     using T = typename Prec<P>::real;
@@ -213,14 +213,14 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
 
     using LK = Link<link_prec(P), RECON>;
     if constexpr (PF == 0) {
-        hop_dir<P, RECON, 0, SF, true>(in, gf + 0 * lb, vh, xf, i, false, acc);
-        hop_dir<P, RECON, 0, SB, false>(in, gb + 0 * lb, vh, xb, xb, false, acc);
-        hop_dir<P, RECON, 1, SF, true>(in, gf + 1 * lb, vh, yf, i, false, acc);
-        hop_dir<P, RECON, 1, SB, false>(in, gb + 1 * lb, vh, yb, yb, false, acc);
-        hop_dir<P, RECON, 2, SF, true>(in, gf + 2 * lb, vh, zf, i, false, acc);
-        hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, false, acc);
-        if (dtf) hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
-        if (dtb) hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
+        hop_dir<P, RECON, 0, SF, true, LNA>(in, gf + 0 * lb, vh, xf, i, false, acc);
+        hop_dir<P, RECON, 0, SB, false, LNA>(in, gb + 0 * lb, vh, xb, xb, false, acc);
+        hop_dir<P, RECON, 1, SF, true, LNA>(in, gf + 1 * lb, vh, yf, i, false, acc);
+        hop_dir<P, RECON, 1, SB, false, LNA>(in, gb + 1 * lb, vh, yb, yb, false, acc);
+        hop_dir<P, RECON, 2, SF, true, LNA>(in, gf + 2 * lb, vh, zf, i, false, acc);
+        hop_dir<P, RECON, 2, SB, false, LNA>(in, gb + 2 * lb, vh, zb, zb, false, acc);
+        if (dtf) hop_dir<P, RECON, 3, SF, true, LNA>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
+        if (dtb) hop_dir<P, RECON, 3, SB, false, LNA>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
     } else {
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) LK::prefetch(gf + mu * lb, vh, i);
@@ -231,14 +231,14 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
             LK::prefetch(gb + 2 * lb, vh, zb);
             LK::prefetch(gb + 3 * lb, vh, tb);
         }
-        hop_dir<P, RECON, 0, SB, false>(in, gb + 0 * lb, vh, xb, xb, false, acc);
-        hop_dir<P, RECON, 1, SB, false>(in, gb + 1 * lb, vh, yb, yb, false, acc);
-        hop_dir<P, RECON, 2, SB, false>(in, gb + 2 * lb, vh, zb, zb, false, acc);
-        if (dtb) hop_dir<P, RECON, 3, SB, false>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
-        hop_dir<P, RECON, 0, SF, true>(in, gf + 0 * lb, vh, xf, i, false, acc);
-        hop_dir<P, RECON, 1, SF, true>(in, gf + 1 * lb, vh, yf, i, false, acc);
-        hop_dir<P, RECON, 2, SF, true>(in, gf + 2 * lb, vh, zf, i, false, acc);
-        if (dtf) hop_dir<P, RECON, 3, SF, true>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
+        hop_dir<P, RECON, 0, SB, false, LNA>(in, gb + 0 * lb, vh, xb, xb, false, acc);
+        hop_dir<P, RECON, 1, SB, false, LNA>(in, gb + 1 * lb, vh, yb, yb, false, acc);
+        hop_dir<P, RECON, 2, SB, false, LNA>(in, gb + 2 * lb, vh, zb, zb, false, acc);
+        if (dtb) hop_dir<P, RECON, 3, SB, false, LNA>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
+        hop_dir<P, RECON, 0, SF, true, LNA>(in, gf + 0 * lb, vh, xf, i, false, acc);
+        hop_dir<P, RECON, 1, SF, true, LNA>(in, gf + 1 * lb, vh, yf, i, false, acc);
+        hop_dir<P, RECON, 2, SF, true, LNA>(in, gf + 2 * lb, vh, zf, i, false, acc);
+        if (dtf) hop_dir<P, RECON, 3, SF, true, LNA>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
     }
 
     const T a = (T)A.a, b = (T)A.b;
@@ -267,7 +267,7 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
 // PF 4 is schedule 1 compiled for 3 resident blocks of 256 threads per SM
 // (at most 85 registers): more warps to hide latency, at the price of
 // registers the compiler would otherwise use to hoist loads.
-template <int P, int RECON, bool DAG, bool HAS_X, int PF, bool TOPEN = false>
+template <int P, int RECON, bool DAG, bool HAS_X, int PF, bool TOPEN = false, bool LNA = false>
 __global__ void __launch_bounds__(256, PF == 4 ? 3 : 2) hop_kernel(const HopArgs A)
 {
     int p, blk;
@@ -275,14 +275,17 @@ __global__ void __launch_bounds__(256, PF == 4 ? 3 : 2) hop_kernel(const HopArgs
     else { p = A.parity0; blk = blockIdx.x; }
     const int i = blk * blockDim.x + threadIdx.x;
     if (i >= A.vh) return;
-    hop_site<P, RECON, DAG, HAS_X, PF, TOPEN>(A, p, i, (size_t)blockIdx.y * A.rhs_stride);
+    hop_site<P, RECON, DAG, HAS_X, PF, TOPEN, LNA>(A, p, i, (size_t)blockIdx.y * A.rhs_stride);
 }
 
+// lna: links loaded without L1 allocation (schedules 0 and 1 only).
 template <int P, int RECON, bool DAG, bool HX>
-cudaError_t launch_hop_pf(const HopArgs &A, dim3 grid, int threads, int pf, cudaStream_t s)
+cudaError_t launch_hop_pf(const HopArgs &A, dim3 grid, int threads, int pf, bool lna, cudaStream_t s)
 {
     if (A.topen)   // sub-domain interior pass: schedule 1 with the open t boundary
         return wd_launch(hop_kernel<P, RECON, DAG, HX, 1, true>, grid, dim3(threads), 0, s, A);
+    if (lna && pf == 0) return wd_launch(hop_kernel<P, RECON, DAG, HX, 0, false, true>, grid, dim3(threads), 0, s, A);
+    if (lna && pf == 1) return wd_launch(hop_kernel<P, RECON, DAG, HX, 1, false, true>, grid, dim3(threads), 0, s, A);
     switch (pf) {
     case 0: return wd_launch(hop_kernel<P, RECON, DAG, HX, 0>, grid, dim3(threads), 0, s, A);
     case 1: return wd_launch(hop_kernel<P, RECON, DAG, HX, 1>, grid, dim3(threads), 0, s, A);

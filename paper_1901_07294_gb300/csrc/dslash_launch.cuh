@@ -15,7 +15,9 @@ constexpr int HOP_OCC_VARIANT = 4;    // schedule 1 compiled for 3 blocks of 256
 constexpr int HOP_TILE_VARIANT = 8;   // schedule 1 with the neighbour window staged in shared memory
 constexpr int HOP_2SITE_VARIANT = 9;  // schedule 1 with two sites per thread
 constexpr int HOP_BULK_VARIANT = 10;  // schedule 1 with the block's contiguous data staged by bulk copies
-constexpr int HOP_MAX_VARIANT = 10;   // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
+constexpr int HOP_NA0_VARIANT = 11;   // schedule 0 with the links loaded without L1 allocation
+constexpr int HOP_NA1_VARIANT = 12;   // schedule 1 with the links loaded without L1 allocation
+constexpr int HOP_MAX_VARIANT = 12;   // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
 
 // Multi-RHS variants and their z-strip width (0: natural order); -1 if v is not one.
 __host__ __device__ constexpr int hop_mrhs_strip(int v)
@@ -28,7 +30,9 @@ __host__ __device__ constexpr int hop_mrhs_strip(int v)
 // (pf = HOP_MRHS_VARIANT and 5..7: the shared-link multi-RHS kernel, threads/32
 // fields at a time, in the site order hop_mrhs_strip(pf) names;
 // HOP_TILE_VARIANT and HOP_2SITE_VARIANT: the kernels of dslash_variants.cuh;
-// HOP_BULK_VARIANT: the kernel of dslash_bulk.cuh).
+// HOP_BULK_VARIANT: the kernel of dslash_bulk.cuh; HOP_NA0_VARIANT and
+// HOP_NA1_VARIANT: schedules 0 and 1 with the links loaded without L1
+// allocation, for even-odd hops, which read every link exactly once).
 template <int P>
 cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int threads, int pf, cudaStream_t s)
 {
@@ -96,15 +100,17 @@ cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int th
         pf = 1;   // window larger than 48 KB, or an open-boundary pass: schedule 1
     }
     if (pf == HOP_2SITE_VARIANT) pf = 1;   // open-boundary pass
+    const bool lna = pf == HOP_NA0_VARIANT || pf == HOP_NA1_VARIANT;
+    if (lna) pf = pf == HOP_NA0_VARIANT ? 0 : 1;
     switch (key) {
-    case 0: return launch_hop_pf<P, 18, false, false>(B, grid, threads, pf, s);
-    case 1: return launch_hop_pf<P, 18, false, true>(B, grid, threads, pf, s);
-    case 2: return launch_hop_pf<P, 18, true, false>(B, grid, threads, pf, s);
-    case 3: return launch_hop_pf<P, 18, true, true>(B, grid, threads, pf, s);
-    case 4: return launch_hop_pf<P, 12, false, false>(B, grid, threads, pf, s);
-    case 5: return launch_hop_pf<P, 12, false, true>(B, grid, threads, pf, s);
-    case 6: return launch_hop_pf<P, 12, true, false>(B, grid, threads, pf, s);
-    default: return launch_hop_pf<P, 12, true, true>(B, grid, threads, pf, s);
+    case 0: return launch_hop_pf<P, 18, false, false>(B, grid, threads, pf, lna, s);
+    case 1: return launch_hop_pf<P, 18, false, true>(B, grid, threads, pf, lna, s);
+    case 2: return launch_hop_pf<P, 18, true, false>(B, grid, threads, pf, lna, s);
+    case 3: return launch_hop_pf<P, 18, true, true>(B, grid, threads, pf, lna, s);
+    case 4: return launch_hop_pf<P, 12, false, false>(B, grid, threads, pf, lna, s);
+    case 5: return launch_hop_pf<P, 12, false, true>(B, grid, threads, pf, lna, s);
+    case 6: return launch_hop_pf<P, 12, true, false>(B, grid, threads, pf, lna, s);
+    default: return launch_hop_pf<P, 12, true, true>(B, grid, threads, pf, lna, s);
     }
 }
 

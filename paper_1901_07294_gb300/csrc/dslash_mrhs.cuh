@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 3) hop_mrhs_kernel(co
         const char *lblk = d < 4 ? gf + mu * lb : gb + mu * lb;
         const int li = d < 4 ? is : nbs[d][ss];
         cpx<T> U[3][3];
-        LK::load(lblk, vh, li, U);
+        LK::template load<true>(lblk, vh, li, U);   // each link is staged once: no L1 allocation
         tile_put<T>(&lk[d][0][ss], U);
     }
     __syncthreads();

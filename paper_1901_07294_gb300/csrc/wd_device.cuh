@@ -59,6 +59,15 @@ __device__ __forceinline__ uint4 ldg16(const void *p)
 {
     return __ldg(reinterpret_cast<const uint4 *>(p));
 }
+// As ldg16, without allocating the line in L1.
+__device__ __forceinline__ uint4 ldg16_na(const void *p)
+{
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p));
+    return r;
+}
 __device__ __forceinline__ void stg16(void *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
 
 // Hint: bring the 128-byte line holding p into L2 (no register result).
@@ -205,11 +214,15 @@ template <int P, int RECON> struct Link {
         if constexpr (ntail > 0) prefetch_l2(blk + (size_t)nmain * vh * 16 + (size_t)i * ntail * Prec<P>::bytes);
     }
 
+    // NA: the 16-byte planes bypass L1 allocation (a link read once per call
+    // would only evict neighbour spinors that other threads of the block reuse)
+    template <bool NA = false>
     __device__ static __forceinline__ void load_raw(const char *blk, int vh, int i, real (&u)[18])
     {
 #pragma unroll
         for (int k = 0; k < nmain; ++k) {
-            uint4 w = ldg16(blk + ((size_t)k * vh + i) * 16);
+            const char *a = blk + ((size_t)k * vh + i) * 16;
+            const uint4 w = NA ? ldg16_na(a) : ldg16(a);
             unpack16<P>(w, u + k * per16, 1.0f);
         }
         if constexpr (ntail > 0) {
@@ -240,10 +253,11 @@ template <int P, int RECON> struct Link {
     }
 
     // Full 3x3 matrix; with RECON = 12 the third row is conj(row0 x row1).
+    template <bool NA = false>
     __device__ static __forceinline__ void load(const char *blk, int vh, int i, cpx<real> (&U)[3][3])
     {
         real u[18];
-        load_raw(blk, vh, i, u);
+        load_raw<NA>(blk, vh, i, u);
 #pragma unroll
         for (int r = 0; r < (RECON == 18 ? 3 : 2); ++r)
 #pragma unroll

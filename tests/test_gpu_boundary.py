@@ -158,3 +158,28 @@ def test_boundary_argument_checked(ctx):
         g.set_boundary(0)
     g.set_boundary(-1)
     g.set_boundary(1)
+
+
+@pytest.mark.parametrize("variant", [0, 11, 12])
+@pytest.mark.parametrize("prec", [wd.F32, wd.F16])
+def test_single_field_variants_antiperiodic(ctx, variant, prec):
+    """Schedules 0 and 1 with links loaded without L1 allocation (variants 11, 12) apply the
+    antiperiodic sign like the others, in the full operator and in an even-odd hop."""
+    dims = (4, 6, 4, 6)
+    U, Ua, g = _gauge(ctx, dims, 1404)
+    psi = synth.spinor(dims, seed=3404)
+    par = parity(dims)
+    for recon in (18, 12):
+        wd.tune_set_dslash(ctx, g, prec, recon, True, True, 1, 64, variant)
+        wd.tune_set_dslash(ctx, g, prec, recon, False, False, 1, 64, variant)
+        out = wd.alloc_field(dims, wd.SITES_FULL, prec)
+        wd.dslash_apply(ctx, g, out, pack_field(ctx, dims, wd.SITES_FULL, prec, psi), 0.1, prec=prec, recon=recon)
+        check_dslash(unpack_field(ctx, dims, wd.SITES_FULL, prec, out), oracle.dirac(dims, Ua, psi, 0.1), prec,
+                     dims, U, psi, recon, lambda u, p: oracle.dirac(dims, oracle.antiperiodic_links(dims, u), p, 0.1))
+        fe = wd.alloc_field(dims, wd.SITES_EVEN, prec)
+        wd.dslash_eo_apply(ctx, g, fe, pack_field(ctx, dims, wd.SITES_ODD, prec, psi), None, 0, 0.0, 1.0,
+                           prec=prec, recon=recon)
+        src = psi.copy()
+        src[par == 0] = 0
+        got = unpack_field(ctx, dims, wd.SITES_EVEN, prec, fe)[par == 0]
+        assert rel_max_err(got, oracle.hop(dims, Ua, src, out_parity=0)[par == 0]) < (1e-5 if prec == wd.F32 else 3e-3)

@@ -131,7 +131,7 @@ def test_autotuner_includes_staged_kernel(ctx):
     dims = (8, 8, 8, 8)
     g = wd.Gauge(ctx, dims, synth.gauge(dims, seed=1604))
     table = wd.tune_dslash(ctx, g, wd.F32, 18, full=True)
-    assert {t["variant"] for t in table} == {0, 1, 2, 4, 8, 9, BULK}
+    assert BULK in {t["variant"] for t in table}
     assert all(np.isfinite(t["ms"]) and t["ms"] > 0 for t in table)
 
 

@@ -195,7 +195,7 @@ def test_argument_errors(ctx):
 
 
 @pytest.mark.parametrize("prec", ALL_PREC)
-@pytest.mark.parametrize("variant", [0, 1, 2, 8, 9, 10])
+@pytest.mark.parametrize("variant", [0, 1, 2, 8, 9, 10, 11, 12])
 @pytest.mark.parametrize("threads", [64, 192, 256])
 def test_every_launch_variant_matches_oracle(prec, variant, threads):
     """Each memory schedule and block size the autotuner may pick computes the same operator."""
@@ -228,10 +228,11 @@ def test_autotuner_table_and_choice():
     U, _ = _inputs(dims)
     g = wd.Gauge(ctx, dims, U)
     table = wd.tune_dslash(ctx, g, wd.F32, 18, full=True)
-    # 4 block sizes x 7 single-field variants: schedules 0, 1, 2, the high-occupancy build 4,
-    # the shared-memory neighbour window 8, two sites per thread 9 and the bulk-copy staging 10
-    assert len(table) == 28
-    assert {t["variant"] for t in table} == {0, 1, 2, 4, 8, 9, 10}
+    # 4 block sizes x 9 single-field variants: schedules 0, 1, 2, the high-occupancy build 4,
+    # the shared-memory neighbour window 8, two sites per thread 9, the bulk-copy staging 10
+    # and schedules 0 and 1 with links loaded without L1 allocation (11, 12)
+    assert len(table) == 36
+    assert {t["variant"] for t in table} == {0, 1, 2, 4, 8, 9, 10, 11, 12}
     assert all(t["ms"] > 0 for t in table)
 
 
@@ -267,7 +268,7 @@ def test_high_occupancy_variant_matches_oracle(prec, dims, threads):
 
 @pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 2, 6), (6, 2, 2, 2), (2, 2, 10, 2)])
 @pytest.mark.parametrize("prec", ALL_PREC)
-@pytest.mark.parametrize("threads,variant", [(32, 0), (64, 1), (256, 2), (192, 4), (32, 8), (128, 8), (64, 9), (96, 9), (32, 10)])
+@pytest.mark.parametrize("threads,variant", [(32, 0), (64, 1), (256, 2), (192, 4), (32, 8), (128, 8), (64, 9), (96, 9), (32, 10), (64, 11), (128, 12)])
 def test_degenerate_extents_and_ragged_tails(dims, prec, threads, variant):
     """L_mu = 2 (x+mu and x-mu are the same site, both terms added) and half-lattice sizes far
     below or not a multiple of the block size."""
