@@ -26,11 +26,14 @@ std::string hop_key(const wd_ctx *ctx, const HopArgs &A, int prec, int recon, in
 
 // Untuned defaults, from tuning runs on GB300 (32^4, 24^3x48, 16^3x32): the
 // FP32/FP16/BF16 kernels are fastest with 64-thread blocks and memory
-// schedule 1; the FP64 kernel (FP64-ALU bound) with 128 threads, schedule 0.
-static std::pair<int, int> hop_default(int prec, int nrhs)
+// schedule 1, even-odd hops (each link read once) with the links loaded
+// without L1 allocation; the FP64 kernel (FP64-ALU bound) with 128 threads,
+// schedule 0.
+static std::pair<int, int> hop_default(int prec, int nrhs, int nparity)
 {
     if (nrhs > 1) return {128, HOP_MRHS_VARIANT};   // shared-link kernel, 4 fields at a time
-    return prec == WD_F64 ? std::make_pair(128, 0) : std::make_pair(64, 1);
+    if (prec == WD_F64) return {128, 0};
+    return {64, nparity == 1 ? HOP_NA1_VARIANT : 1};
 }
 
 int hop_launch_cfg(const HopArgs &A, int prec, int recon, int dagger, int nrhs, int threads, int variant,
@@ -51,7 +54,7 @@ int hop_launch_cfg(const HopArgs &A, int prec, int recon, int dagger, int nrhs, 
 
 int hop_launch(wd_ctx *ctx, const HopArgs &A, int prec, int recon, int dagger, int nrhs, cudaStream_t s)
 {
-    auto cfg = tuned_config(ctx, hop_key(ctx, A, prec, recon, nrhs), hop_default(prec, nrhs));
+    auto cfg = tuned_config(ctx, hop_key(ctx, A, prec, recon, nrhs), hop_default(prec, nrhs, A.nparity));
     return hop_launch_cfg(A, prec, recon, dagger, nrhs, cfg.first, cfg.second, s);
 }
 
