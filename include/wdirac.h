@@ -93,10 +93,15 @@ int wd_field_bytes(const int dims[4], int sites, int prec, int nrhs, size_t *out
 
 /* Layout conversion (Sec. II-C lists precision conversion among the
  * machine-specific primitives).  wd_pack reads a canonical FP64 spinor of the
- * FULL lattice (device memory, V sites) and writes the device field holding
- * `sites` (full, even or odd half) in precision `prec`.  wd_unpack writes the
- * sites held by the field back into a canonical full-lattice array; sites of
- * the other parity are left untouched.  Asynchronous on `stream`. */
+ * FULL lattice (V sites) and writes the device field holding `sites` (full,
+ * even or odd half) in precision `prec`.  wd_unpack writes the sites held by
+ * the field back into a canonical full-lattice array; sites of the other
+ * parity are left untouched.  Asynchronous on `stream`.
+ * The canonical array may be device memory of the context's GPU, managed
+ * memory, page-locked host memory (the kernel then reads or writes it
+ * directly over the host link, with no staging copy) or, where the device
+ * can access pageable memory (Grace systems), ordinary host memory; anything
+ * else gives WD_EINVAL.  The field must be device memory. */
 int wd_pack(wd_ctx *ctx, const int dims[4], int sites, int prec, const double *aos,
             void *field, void *stream);
 int wd_unpack(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *field,
@@ -172,8 +177,8 @@ int wd_probe_fma(wd_ctx *ctx, int prec, double *tflops);
 
 /* Device attributes of the context's GPU, for rooflines: SM count, memory
  * clock (kHz), memory bus width (bits), L2 size (bytes), compute capability,
- * and the nominal HBM bandwidth 2 x clock x width / 8 (GB/s; two transfers
- * per clock).  Measurement support; the paper has no counterpart. */
+ * the nominal HBM bandwidth 2 x clock x width / 8 (GB/s; two transfers per
+ * clock), and whether kernels can access pageable host memory.  Measurement support; the paper has no counterpart. */
 typedef struct {
     int sm_count;
     int mem_clock_khz;
@@ -181,6 +186,7 @@ typedef struct {
     int l2_bytes;
     int cc_major, cc_minor;
     double nominal_hbm_gbs;
+    int pageable_memory_access;   /* 1: kernels may dereference ordinary host memory */
 } wd_device_props;
 
 int wd_device_info(const wd_ctx *ctx, wd_device_props *out);

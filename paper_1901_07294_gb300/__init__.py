@@ -195,12 +195,14 @@ def alloc_field(dims, sites: int, prec: int, nrhs: int = 1, device="cuda"):
 
 
 def pack(ctx: Context, dims, sites: int, prec: int, aos, field, stream=None) -> None:
-    """Canonical FP64 full-lattice spinor (device) -> device field holding `sites`."""
+    """Canonical FP64 full-lattice spinor (device, or pinned host memory the kernel reads
+    directly) -> device field holding `sites`."""
     _check(load().wd_pack(ctx.handle, _dims(dims), int(sites), int(prec), _ptr(aos), _ptr(field), _stream(stream)))
 
 
 def unpack(ctx: Context, dims, sites: int, prec: int, field, aos, stream=None) -> None:
-    """Device field -> the sites it holds inside a canonical FP64 full-lattice array."""
+    """Device field -> the sites it holds inside a canonical FP64 full-lattice array (device,
+    or pinned host memory the kernel writes directly)."""
     _check(load().wd_unpack(ctx.handle, _dims(dims), int(sites), int(prec), _ptr(field), _ptr(aos), _stream(stream)))
 
 
@@ -569,11 +571,12 @@ def solve_workspace_bytes(dims, inner_prec: int) -> int:
 class DeviceProps(ctypes.Structure):
     """wd_device_props"""
     _fields_ = [("sm_count", _ip), ("mem_clock_khz", _ip), ("mem_bus_bits", _ip), ("l2_bytes", _ip),
-                ("cc_major", _ip), ("cc_minor", _ip), ("nominal_hbm_gbs", _dp)]
+                ("cc_major", _ip), ("cc_minor", _ip), ("nominal_hbm_gbs", _dp), ("pageable_memory_access", _ip)]
 
 
 def device_info(ctx: Context) -> dict:
-    """SM count, memory clock and bus width, L2 size, compute capability and the nominal HBM GB/s."""
+    """SM count, memory clock and bus width, L2 size, compute capability, the nominal HBM GB/s
+    and whether kernels can access pageable host memory."""
     p = DeviceProps()
     _check(load().wd_device_info(ctx.handle, ctypes.byref(p)))
     return {f: getattr(p, f) for f, _ in DeviceProps._fields_}

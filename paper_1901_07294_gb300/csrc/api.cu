@@ -448,6 +448,34 @@ int wd_field_bytes(const int dims[4], int sites, int prec, int nrhs, size_t *out
     return WD_OK;
 }
 
+// The address through which this context's kernels reach the canonical
+// array p: device memory of the context's GPU and managed memory as they are;
+// page-locked host memory through its device mapping (the kernel then reads
+// or writes host memory directly over the host link); pageable host memory
+// only where the device can access it (address translation, as on Grace
+// systems).  nullptr if the device cannot dereference p.
+static void *device_view(const wd_ctx *ctx, const void *p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    switch (at.type) {
+    case cudaMemoryTypeDevice: return at.device == ctx->device ? const_cast<void *>(p) : nullptr;
+    case cudaMemoryTypeManaged: return const_cast<void *>(p);
+    case cudaMemoryTypeHost: return at.devicePointer;
+    default: {
+        int pageable = 0;
+        if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, ctx->device) != cudaSuccess) {
+            cudaGetLastError();
+            pageable = 0;
+        }
+        return pageable ? const_cast<void *>(p) : nullptr;
+    }
+    }
+}
+
 static int pack_common(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *a, const void *b,
                        Geometry &g, SiteMap &m)
 {
@@ -465,6 +493,8 @@ int wd_pack(wd_ctx *ctx, const int dims[4], int sites, int prec, const double *a
     Geometry g;
     SiteMap m;
     WD_TRY(pack_common(ctx, dims, sites, prec, aos, field, g, m));
+    aos = (const double *)device_view(ctx, aos);
+    if (!aos) return set_error(WD_EINVAL, "the canonical array is not accessible from the context's device");
     cudaStream_t s = (cudaStream_t)stream;
     char *f = (char *)field;
     if (m.np == 2) {
@@ -497,6 +527,8 @@ int wd_unpack(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *f
     Geometry g;
     SiteMap m;
     WD_TRY(pack_common(ctx, dims, sites, prec, field, aos, g, m));
+    aos = (double *)device_view(ctx, aos);
+    if (!aos) return set_error(WD_EINVAL, "the canonical array is not accessible from the context's device");
     cudaStream_t s = (cudaStream_t)stream;
     const char *f = (const char *)field;
     if (m.np == 2) {

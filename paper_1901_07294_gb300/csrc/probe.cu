@@ -85,6 +85,9 @@ extern "C" int wd_device_info(const wd_ctx *ctx, wd_device_props *out)
     out->cc_minor = v[5];
     // double data rate: two transfers per memory clock
     out->nominal_hbm_gbs = 2.0 * (double)v[1] * 1e3 * (double)v[2] / 8.0 / 1e9;
+    int pageable = 0;
+    WD_CUDA_TRY(cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, ctx->device));
+    out->pageable_memory_access = pageable;
     return WD_OK;
 }
 

@@ -91,6 +91,38 @@ def test_pack_half_fields_touch_only_their_parity(ctx):
         assert np.all(back[par != p] == 0)
 
 
+@pytest.mark.parametrize("prec", ALL_PREC)
+@pytest.mark.parametrize("sites", [wd.SITES_FULL, wd.SITES_EVEN])
+def test_pack_unpack_with_host_memory(ctx, prec, sites):
+    """The canonical array may be pinned host memory (or, on systems where the device can
+    access pageable memory, ordinary host memory): the kernels read and write it directly and
+    give the same bytes as with a device array.  Device memory is used unchanged."""
+    import torch
+    dims = (4, 6, 8, 10)
+    psi = synth.spinor(dims, seed=2013)
+    flat = psi.view(np.float64).reshape(-1)
+    dev = torch.from_numpy(flat.copy()).cuda()
+    pinned = torch.from_numpy(flat.copy()).pin_memory()
+    f_dev = wd.alloc_field(dims, sites, prec)
+    f_host = wd.alloc_field(dims, sites, prec)
+    wd.pack(ctx, dims, sites, prec, dev, f_dev)
+    wd.pack(ctx, dims, sites, prec, pinned, f_host)
+    torch.cuda.synchronize()
+    assert torch.equal(f_dev, f_host)
+    out_dev = torch.zeros_like(dev)
+    out_pinned = torch.zeros(flat.size, dtype=torch.float64).pin_memory()
+    wd.unpack(ctx, dims, sites, prec, f_dev, out_dev)
+    wd.unpack(ctx, dims, sites, prec, f_dev, out_pinned)
+    torch.cuda.synchronize()
+    assert torch.equal(out_dev.cpu(), out_pinned)
+    if wd.device_info(ctx)["pageable_memory_access"]:
+        pageable = flat.copy()
+        f_pg = wd.alloc_field(dims, sites, prec)
+        wd.pack(ctx, dims, sites, prec, pageable.ctypes.data, f_pg)
+        torch.cuda.synchronize()
+        assert torch.equal(f_dev, f_pg)
+
+
 @pytest.mark.parametrize("dims", DIMS)
 @pytest.mark.parametrize("recon", [18, 12])
 @pytest.mark.parametrize("prec", ALL_PREC)
