@@ -756,8 +756,8 @@ def _mrhs_section(wd, torch, ctx, U, psi, peak, reps=20):
 
 def _batch_section(wd, torch, ctx, peak):
     """24 solves of uneven volumes (8 each of 8^4, 16^4, 24^3x48), masses U[0.05, 0.5] (seed 4001),
-    tol 1e-10, mixed FP32 reliable-update CG: one persistent launch vs per-solve CUDA graphs vs
-    24 sequential cg_solve calls."""
+    tol 1e-10, mixed reliable-update CG with FP32 and with FP16 inner storage: one persistent
+    launch vs per-solve CUDA graphs vs 24 sequential cg_solve calls."""
     import numpy as np
 
     import synth
@@ -777,13 +777,19 @@ def _batch_section(wd, torch, ctx, peak):
     t0 = time.perf_counter()
     for p in probs[:1] + probs[8:9] + probs[16:17]:
         for with_x in (False, True):
-            wd.tune_dslash(ctx, p["gauge"], wd.F32, 18, full=False, with_x=with_x)
-            wd.tune_dslash(ctx, p["gauge"], wd.F64, 18, full=False, with_x=with_x)
+            for prec in (wd.F32, wd.F16, wd.F64):
+                wd.tune_dslash(ctx, p["gauge"], prec, 18, full=False, with_x=with_x)
     tune_s = time.perf_counter() - t0
     out = {"solves": 24, "lattices": [list(d) for d in lattices], "tol": 1e-10, "inner": "fp32 reliable-update, delta 0.01",
            "autotune_seconds": round(tune_s, 3)}
-    for name, mode in (("sequential", wd.BATCH_SEQUENTIAL), ("graph", wd.BATCH_GRAPH),
-                       ("persistent", wd.BATCH_PERSISTENT)):
+    runs = [(name, mode, wd.F32) for name, mode in (("sequential", wd.BATCH_SEQUENTIAL), ("graph", wd.BATCH_GRAPH),
+                                                    ("persistent", wd.BATCH_PERSISTENT))]
+    runs += [(name, mode, wd.F16) for name, mode in (("fp16_sequential", wd.BATCH_SEQUENTIAL),
+                                                     ("fp16_graph", wd.BATCH_GRAPH),
+                                                     ("fp16_persistent", wd.BATCH_PERSISTENT))]
+    for name, mode, inner in runs:
+        for p in probs:
+            p["inner_prec"] = inner
         wd.cg_solve_batch(ctx, probs, mode=mode)   # warm
         best = None
         for _ in range(2):
@@ -797,7 +803,7 @@ def _batch_section(wd, torch, ctx, peak):
             if best is None or ms < best[0]:
                 best = (ms, st)
         ms, st = best
-        it_bytes = sum(s_["iters"] * int(np.prod(p["gauge"].dims)) // 2 * _cg_iteration_bytes(wd.F32, 18)
+        it_bytes = sum(s_["iters"] * int(np.prod(p["gauge"].dims)) // 2 * _cg_iteration_bytes(inner, 18)
                        for s_, p in zip(st, probs))
         out[name] = {"seconds": round(ms / 1e3, 4), "solves_per_s": round(24 / (ms / 1e3), 1),
                      "iters_total": int(sum(s["iters"] for s in st)),

@@ -417,9 +417,10 @@ int wilson_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x, const voi
  *                        group of thread blocks (sized by volume), steps
  *                        separated by group barriers whose waits are bounded
  *                        (1 s of clock cycles; WD_BARRIER_TIMEOUT_S overrides);
- *                        options must be inner_prec WD_F32, 18-real links,
- *                        reliable = 1.  Batches larger than one co-resident
- *                        grid run as several launches.
+ *                        options must be inner_prec WD_F32, WD_F16 or WD_BF16
+ *                        (the same for all), 18-real links, reliable = 1.
+ *                        Batches larger than one co-resident grid run as
+ *                        several launches.
  * stats[k] receives solve k's statistics; `seconds` is the wall time of the
  * whole call.  Returns the first failure (WD_ENOCONV, WD_ETIMEOUT, ...).
  * Synchronous; allocates its workspace for the duration of the call. */

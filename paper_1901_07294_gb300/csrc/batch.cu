@@ -10,7 +10,8 @@
 //                        solve; the graphs of all active solves run on their
 //                        own streams until a reliable update is due, and the
 //                        host does the FP64 updates between launches;
-//   WD_BATCH_PERSISTENT  one cooperative launch: each solve owns a group of
+//   WD_BATCH_PERSISTENT  one cooperative launch (all solves with the same
+//                        inner precision): each solve owns a group of
 //                        thread blocks (sized in proportion to its volume)
 //                        that runs the whole solve, separated by group-local
 //                        barriers and deterministic group reductions.  Every
@@ -38,11 +39,12 @@ namespace {
 // persistent kernel
 // ---------------------------------------------------------------------------
 struct PSolve {
-    HopArgs hs;            // FP32 geometry and links
+    HopArgs hs;            // inner-precision geometry and links
     HopArgs hd;            // FP64 geometry and links
     const char *b;         // FP64 even half fields
     char *x, *r, *ax, *to64, *te64;
-    char *rs, *ps, *aps, *tso, *tse, *xs;   // FP32 even/odd half fields
+    char *rs, *ps, *aps, *tso, *tse;   // inner-precision even/odd half fields
+    char *xs;              // FP32 solution increment since the last reliable update
     double mass, tol, delta;
     int maxiter;
     int block0, nblocks;
@@ -160,8 +162,17 @@ __device__ bool group_mdagm(GroupCtx &g, const HopArgs &A, double mass, const ch
     return true;   // the caller's next step reads only its own sites of `out`
 }
 
-// One 256-thread block per SM: the FP32 and FP64 hop bodies inlined together
-// need up to 255 registers per thread.
+// Half-field bytes of precision P on the device (as half_field_bytes).
+template <int P> __host__ __device__ constexpr size_t half_bytes_of(int vh)
+{
+    return (size_t)vh * (24 * Prec<P>::bytes + (Prec<P>::scaled ? 4 : 0));
+}
+
+// One 256-thread block per SM: the inner-precision and FP64 hop bodies inlined
+// together need up to 255 registers per thread.  P: storage precision of the
+// iterated residual, the direction and the operator's intermediate fields
+// (FP32, FP16 or BF16; FP32 arithmetic).
+template <int P>
 __global__ void __launch_bounds__(256, 1) cg_persistent_kernel(const PSolve *__restrict__ solves,
                                                                 const int *__restrict__ block_solve, int *err,
                                                                 long long limit)
@@ -169,9 +180,10 @@ __global__ void __launch_bounds__(256, 1) cg_persistent_kernel(const PSolve *__r
     const PSolve *S = solves + block_solve[blockIdx.x];
     GroupCtx g{S, (int)blockIdx.x - S->block0, S->nblocks, 0u, 0, limit, err};
     const int vh = S->hs.vh;
-    const size_t h64 = (size_t)vh * 192, h32 = (size_t)vh * 96;
+    const size_t h64 = (size_t)vh * 192, h32 = (size_t)vh * 96, hp = half_bytes_of<P>(vh);
     const FieldRef<PREC_F64> fb{(char *)S->b, h64, vh}, fx{S->x, h64, vh}, fr{S->r, h64, vh}, fax{S->ax, h64, vh};
-    const FieldRef<PREC_F32> frs{S->rs, h32, vh}, fps{S->ps, h32, vh}, faps{S->aps, h32, vh}, fxs{S->xs, h32, vh};
+    const FieldRef<P> frs{S->rs, hp, vh}, fps{S->ps, hp, vh}, faps{S->aps, hp, vh};
+    const FieldRef<PREC_F32> fxs{S->xs, h32, vh};
     const int i0 = g.gb * blockDim.x + threadIdx.x, stride = g.G * blockDim.x;
 
     // |b|^2, then x = 0, r = b, rs = ps = (FP32) b, xs = 0 on this block's sites
@@ -201,7 +213,7 @@ __global__ void __launch_bounds__(256, 1) cg_persistent_kernel(const PSolve *__r
         double r2 = b2, maxr = sqrt(b2);
         bool converged = false;
         while (it < S->maxiter) {
-            if (!group_mdagm<PREC_F32>(g, S->hs, S->mass, S->ps, S->aps, S->tso, S->tse)) return;
+            if (!group_mdagm<P>(g, S->hs, S->mass, S->ps, S->aps, S->tso, S->tse)) return;
             double pap[1] = {0.0};
             for (int i = i0; i < vh; i += stride) {
                 float pv[24], av[24];
@@ -314,9 +326,9 @@ int check_desc(const wd_solve_desc &d, int mode)
     if (!valid_recon(d.opts.inner_recon) || !valid_recon(d.opts.outer_recon))
         return set_error(WD_EINVAL, "bad link reconstruction");
     if (mode == WD_BATCH_PERSISTENT) {
-        if (d.opts.inner_prec != WD_F32 || d.opts.inner_recon != 18 || d.opts.outer_recon != 18 || !d.opts.reliable)
-            return set_error(WD_EINVAL,
-                             "the persistent batch runs FP32 reliable-update CG with 18-real links only");
+        if (d.opts.inner_prec == WD_F64 || d.opts.inner_recon != 18 || d.opts.outer_recon != 18 || !d.opts.reliable)
+            return set_error(WD_EINVAL, "the persistent batch runs mixed-precision reliable-update CG "
+                                        "(FP32, FP16 or BF16 inner) with 18-real links only");
         if (!(d.opts.delta > 0.0 && d.opts.delta < 1.0)) return set_error(WD_EINVAL, "delta must be in (0, 1)");
     }
     if (mode == WD_BATCH_GRAPH && (d.opts.inner_prec == WD_F64 || !d.opts.reliable))
@@ -326,8 +338,16 @@ int check_desc(const wd_solve_desc &d, int mode)
 
 int run_persistent(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stats, cudaStream_t s)
 {
+    // one kernel per launch: every solve of the batch has the same inner precision
+    const int inner = d[0].opts.inner_prec;
+    for (int k = 1; k < n; ++k)
+        if (d[k].opts.inner_prec != inner)
+            return set_error(WD_EINVAL, "the solves of a persistent batch must share their inner precision");
+    const void *kernel = inner == WD_F16    ? (const void *)cg_persistent_kernel<PREC_F16>
+                         : inner == WD_BF16 ? (const void *)cg_persistent_kernel<PREC_BF16>
+                                            : (const void *)cg_persistent_kernel<PREC_F32>;
     int per_sm = 0;
-    WD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_persistent_kernel, 256, 0));
+    WD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0));
     const int capacity = per_sm * ctx->num_sms;
     if (capacity < 1) return set_error(WD_ECUDA, "persistent kernel cannot be resident");
     // host-side fault injection for tests: WD_FAULT=barrier_missing makes each
@@ -369,7 +389,8 @@ int run_persistent(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stat
         for (int k = 0; k < m; ++k) {
             const int vh = d[done + k].gauge->geo.Vh;
             off[k] = bytes;
-            bytes += 4 * ((size_t)vh * 192 + 256) + 6 * ((size_t)vh * 96 + 256) + 256 + 4096 +
+            bytes += 4 * ((size_t)vh * 192 + 256) + 5 * (half_field_bytes(vh, inner) + 256) + ((size_t)vh * 96 + 256) +
+                     256 + 4096 +
                      (size_t)nb[k] * 32 + 256;
         }
         DevBuf work, meta;
@@ -383,7 +404,7 @@ int run_persistent(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stat
             const wd_solve_desc &dk = d[done + k];
             PSolve &P = ps[k];
             std::memset(&P, 0, sizeof(P));
-            WD_TRY(hop_setup(dk.gauge, WD_F32, 18, P.hs));
+            WD_TRY(hop_setup(dk.gauge, inner, 18, P.hs));
             WD_TRY(hop_setup(dk.gauge, WD_F64, 18, P.hd));
             P.hs.nparity = P.hd.nparity = 1;
             const int vh = dk.gauge->geo.Vh;
@@ -399,11 +420,12 @@ int run_persistent(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stat
             P.ax = take((size_t)vh * 192);
             P.to64 = take((size_t)vh * 192);
             P.te64 = take((size_t)vh * 192);
-            P.rs = take((size_t)vh * 96);
-            P.ps = take((size_t)vh * 96);
-            P.aps = take((size_t)vh * 96);
-            P.tso = take((size_t)vh * 96);
-            P.tse = take((size_t)vh * 96);
+            const size_t hp = half_field_bytes(vh, inner);
+            P.rs = take(hp);
+            P.ps = take(hp);
+            P.aps = take(hp);
+            P.tso = take(hp);
+            P.tse = take(hp);
             P.xs = take((size_t)vh * 96);
             P.bar = (unsigned *)take(256);
             P.out_int = (int *)take(64);
@@ -431,7 +453,7 @@ int run_persistent(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stat
         WD_CUDA_TRY(cudaMemcpyAsync(d_map, bmap.data(), sizeof(int) * used, cudaMemcpyHostToDevice, s));
         WD_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s));
         void *args[] = {(void *)&d_ps, (void *)&d_map, (void *)&d_err, (void *)&limit};
-        WD_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)cg_persistent_kernel, dim3(used), dim3(256), args, 0, s));
+        WD_CUDA_TRY(cudaLaunchCooperativeKernel(kernel, dim3(used), dim3(256), args, 0, s));
         WD_CUDA_TRY(cudaStreamSynchronize(s));
         int herr = 0;
         WD_CUDA_TRY(cudaMemcpy(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost));

@@ -66,12 +66,16 @@ def test_batch_converges_and_matches_alone(mode):
         assert rel_max_err(xs_mix[k], x_alone) < 1e-7
 
 
-def test_graph_batch_fp16_inner():
+@pytest.mark.parametrize("mode,prec", [(wd.BATCH_GRAPH, wd.F16), (wd.BATCH_PERSISTENT, wd.F16),
+                                       (wd.BATCH_PERSISTENT, wd.BF16)])
+def test_batch_16bit_inner(mode, prec):
+    """FP16 / BF16 storage of the iterated residual, direction and operator intermediates
+    (FP32 arithmetic, FP32 solution increment, FP64 reliable updates)."""
     ctx = wd.Context(0)
     probs, host = _problems(ctx, 4, seed=4002)
     for p in probs:
-        p["inner_prec"] = wd.F16
-    stats = wd.cg_solve_batch(ctx, probs, mode=wd.BATCH_GRAPH)
+        p["inner_prec"] = prec
+    stats = wd.cg_solve_batch(ctx, probs, mode=mode)
     for k, st in enumerate(stats):
         assert st["status"] == 0 and st["true_rel_resid"] <= 1e-10
         assert _true_rel(ctx, host[k], probs[k]["x"])[0] <= 1.05e-10
@@ -80,7 +84,13 @@ def test_graph_batch_fp16_inner():
 def test_persistent_rejects_unsupported_options():
     ctx = wd.Context(0)
     probs, _ = _problems(ctx, 1)
-    probs[0]["inner_prec"] = wd.F16
+    probs[0]["inner_prec"] = wd.F64
+    with pytest.raises(wd.WdError) as e:
+        wd.cg_solve_batch(ctx, probs, mode=wd.BATCH_PERSISTENT)
+    assert e.value.status == wd.WD_EINVAL
+    # one launch runs one inner precision
+    probs, _ = _problems(ctx, 2)
+    probs[1]["inner_prec"] = wd.F16
     with pytest.raises(wd.WdError) as e:
         wd.cg_solve_batch(ctx, probs, mode=wd.BATCH_PERSISTENT)
     assert e.value.status == wd.WD_EINVAL

@@ -138,10 +138,11 @@ def test_full_solve_24_3x48(ctx, solver, kw):
     assert st["status"] == 0 and rel <= 1.05e-10, (st, rel)
 
 
-@pytest.mark.parametrize("mode", [wd.BATCH_GRAPH, wd.BATCH_PERSISTENT])
-def test_uneven_batch_benchmark_configuration(ctx, mode):
+@pytest.mark.parametrize("mode,inner", [(wd.BATCH_GRAPH, wd.F32), (wd.BATCH_PERSISTENT, wd.F32),
+                                        (wd.BATCH_PERSISTENT, wd.F16)])
+def test_uneven_batch_benchmark_configuration(ctx, mode, inner):
     """The 24 solves of the batch benchmark (8 each of 8^4, 16^4, 24^3x48; masses U[0.05, 0.5],
-    seed 4001; FP32 inner, delta 0.01), every solve checked by the oracle operator."""
+    seed 4001; FP32 or FP16 inner, delta 0.01), every solve checked by the oracle operator."""
     rng = np.random.default_rng(4001)
     lattices = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48)]
     gauges, probs, host = {}, [], []
@@ -154,7 +155,7 @@ def test_uneven_batch_benchmark_configuration(ctx, mode):
         b = synth.even_spinor(dims, seed=3200 + k)
         mass = float(rng.uniform(0.05, 0.5))
         probs.append(dict(gauge=g, mass=mass, tol=1e-10, b=pack_field(ctx, dims, wd.SITES_EVEN, wd.F64, b),
-                          x=wd.alloc_field(dims, wd.SITES_EVEN, wd.F64), inner_prec=wd.F32, delta=0.01))
+                          x=wd.alloc_field(dims, wd.SITES_EVEN, wd.F64), inner_prec=inner, delta=0.01))
         host.append((dims, U, mass, b))
     stats = wd.cg_solve_batch(ctx, probs, mode=mode)
     for k, (st, (dims, U, mass, b)) in enumerate(zip(stats, host)):
