@@ -6,7 +6,7 @@
 // data.  Here the sub-lattices are slabs of L_t / nsub time slices.  Each has
 // its own gauge object (its slice of the links: with t slowest in the
 // canonical order, slab k is a contiguous range) and its own fields, exactly
-// as one process per slab would hold them.  In this build all slabs live on
+// as one process per slab would hold them.  This library keeps all slabs on
 // one GPU: the exchange is a device-to-device copy into the receiver's own
 // halo buffer, the step a multi-GPU build does with NCCL send/recv.
 //
