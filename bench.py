@@ -183,7 +183,50 @@ def _cpu_baseline(samples_dims=(8, 8, 8, 8), min_seconds=10.0, max_reps=1_000_00
     gbs = BYTES_PER_SITE[("f32", "full", 18)] * v * reps / el / 1e9
     return {"value": gbs, "unit": "GB/s", "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"FP64 oracle D on {'x'.join(map(str, samples_dims))} ({v} sites) x {reps} reps, "
-                      f"{el:.1f} s; GB/s = sites/s x 480 B"}
+                      f"{el:.1f} s; GB/s = sites/s x 480 B",
+            "cpu_model": _cpu_model(), "host_threads": os.cpu_count()}
+
+
+def _cpu_model():
+    """The host CPU's model name (lscpu), or the architecture if lscpu is missing."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+def _cpu_sizes(U32, psi32, reps=5):
+    """The FP64 oracle D on the operator-benchmark lattices (32^4 with the GPU step's links and
+    source, 16^3x32 with its own), `reps` applications each with 1 thread and with all host
+    threads: ms per application and GB/s in the 480 B/site unit."""
+    import oracle
+    import synth
+    out = {}
+    nmax = oracle.max_threads()
+    cases = [((32, 32, 32, 32), U32, psi32),
+             ((16, 16, 16, 32), synth.gauge((16, 16, 16, 32), seed=1000 + 2), synth.spinor((16, 16, 16, 32), seed=2002))]
+    try:
+        for dims, U, psi in cases:
+            v = synth.volume(dims)
+            row = {}
+            for nt in (1, nmax):
+                oracle.set_threads(nt)
+                oracle.dirac(dims, U, psi, MASS)
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    oracle.dirac(dims, U, psi, MASS)
+                ms = (time.perf_counter() - t0) / reps * 1e3
+                row[f"threads_{nt}"] = {"ms_per_D": round(ms, 2),
+                                        "gbs": round(BYTES_PER_SITE[("f32", "full", 18)] * v / (ms * 1e-3) / 1e9, 3)}
+            out["x".join(map(str, dims))] = row
+    finally:
+        oracle.set_threads(nmax)
+    return out
 
 
 def run_reference(args):
@@ -445,6 +488,7 @@ def run_gpu(args):
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline()
+        line["cpu_baseline"]["sizes"] = _cpu_sizes(U, psi)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
