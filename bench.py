@@ -326,19 +326,28 @@ def run_gpu(args):
     achieved = bytes_step / (mean_launch * 1e-3) / 1e9
     peak, peak_kind = _peaks()
 
-    # end to end through the public API with host buffers: H2D of the canonical
-    # FP64 source (pinned), pack, operator, unpack, D2H of the canonical result.
-    # Consecutive steps alternate between two streams and buffer sets, so one
-    # step's H2D copy overlaps the previous step's D2H copy (C2C is full duplex).
+    # end to end through the public API with host buffers.  Three paths, each over the same
+    # host-resident spinor, timed the same way (consecutive steps alternate between two
+    # streams and buffer sets, so one step's H2D copy overlaps the previous step's D2H copy):
+    #   fp64_copy:   pinned FP64 canonical source -> H2D -> wd.pack -> wd.dslash_apply ->
+    #                wd.unpack -> D2H into a pinned FP64 canonical result;
+    #   fp64_direct: the pinned FP64 buffers handed to wd.pack / wd.unpack, which read and
+    #                write them over the host link (no staging copies);
+    #   fp32_copy:   as fp64_copy with FP32 canonical host buffers (wd_pack_f32 /
+    #                wd_unpack_f32), half the bytes over the link.
     e2e_steps = max(4, min(args.steps, 20))
+    host32 = torch.from_numpy(psi.view(np.float64).reshape(-1).astype(np.float32)).pin_memory()
     sets = []
     for k in range(2):
         s_k = torch.cuda.Stream() if k else stream
         sets.append(dict(s=s_k, aos=aos if k == 0 else torch.empty_like(aos), fin=fin if k == 0 else torch.empty_like(fin),
                          fout=fout if k == 0 else torch.empty_like(fout), aos_out=torch.empty_like(aos),
-                         out_host=torch.empty_like(psi_host).pin_memory()))
+                         out_host=torch.empty_like(psi_host).pin_memory(),
+                         aos32=torch.empty(host32.numel(), dtype=torch.float32, device="cuda"),
+                         aos32_out=torch.empty(host32.numel(), dtype=torch.float32, device="cuda"),
+                         out_host32=torch.empty_like(host32).pin_memory()))
 
-    def e2e_step(k):
+    def fp64_copy(k):
         b = sets[k % 2]
         with torch.cuda.stream(b["s"]):
             b["aos"].copy_(psi_host, non_blocking=True)
@@ -347,59 +356,61 @@ def run_gpu(args):
             wd.unpack(ctx, dims, wd.SITES_FULL, prec, b["fout"], b["aos_out"], stream=b["s"])
             b["out_host"].copy_(b["aos_out"], non_blocking=True)
 
-    for k in range(4):
-        e2e_step(k)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sets[1]["s"].wait_event(e0)
-    for k in range(e2e_steps):
-        e2e_step(k)
-    stream.wait_stream(sets[1]["s"])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_copy_ms = e0.elapsed_time(e1) / e2e_steps
-
-    # the same loop with the host buffers handed to the API: wd.pack reads the pinned source
-    # and wd.unpack writes the pinned result directly over the host link (no staging copies)
-    def e2e_direct_step(k):
+    def fp64_direct(k):
         b = sets[k % 2]
         wd.pack(ctx, dims, wd.SITES_FULL, prec, psi_host, b["fin"], stream=b["s"])
         wd.dslash_apply(ctx, g, b["fout"], b["fin"], MASS, prec=prec, recon=recon, stream=b["s"])
         wd.unpack(ctx, dims, wd.SITES_FULL, prec, b["fout"], b["out_host"], stream=b["s"])
 
-    for k in range(4):
-        e2e_direct_step(k)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    sets[1]["s"].wait_event(e0)
-    for k in range(e2e_steps):
-        e2e_direct_step(k)
-    stream.wait_stream(sets[1]["s"])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_direct_ms = e0.elapsed_time(e1) / e2e_steps
-    e2e_ms = min(e2e_copy_ms, e2e_direct_ms)
-    e2e_value = bytes_step * ws / (e2e_ms * 1e-3) / 1e9
+    def fp32_copy(k):
+        b = sets[k % 2]
+        with torch.cuda.stream(b["s"]):
+            b["aos32"].copy_(host32, non_blocking=True)
+            wd.pack(ctx, dims, wd.SITES_FULL, prec, b["aos32"], b["fin"], stream=b["s"])
+            wd.dslash_apply(ctx, g, b["fout"], b["fin"], MASS, prec=prec, recon=recon, stream=b["s"])
+            wd.unpack(ctx, dims, wd.SITES_FULL, prec, b["fout"], b["aos32_out"], stream=b["s"])
+            b["out_host32"].copy_(b["aos32_out"], non_blocking=True)
 
-    # the host-link floor of that loop: the same H2D and D2H copies alone, concurrently
-    def copies_only(k):
+    # the host-link floor of a path: its H2D and D2H copies alone, concurrently
+    def copies64(k):
         b = sets[k % 2]
         with torch.cuda.stream(b["s"]):
             b["aos"].copy_(psi_host, non_blocking=True)
             b["out_host"].copy_(b["aos_out"], non_blocking=True)
 
-    for k in range(4):
-        copies_only(k)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    sets[1]["s"].wait_event(e0)
-    for k in range(e2e_steps):
-        copies_only(k)
-    stream.wait_stream(sets[1]["s"])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    copy_floor_ms = e0.elapsed_time(e1) / e2e_steps
+    def copies32(k):
+        b = sets[k % 2]
+        with torch.cuda.stream(b["s"]):
+            b["aos32"].copy_(host32, non_blocking=True)
+            b["out_host32"].copy_(b["aos32_out"], non_blocking=True)
+
+    def time_loop(step):
+        for k in range(4):
+            step(k)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sets[1]["s"].wait_event(e0)
+        for k in range(e2e_steps):
+            step(k)
+        stream.wait_stream(sets[1]["s"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / e2e_steps
+
+    e2e_paths = {"fp64_copy": time_loop(fp64_copy), "fp64_direct": time_loop(fp64_direct),
+                 "fp32_copy": time_loop(fp32_copy)}
+    e2e_floor = {"fp64_copy": time_loop(copies64), "fp32_copy": time_loop(copies32)}
+    e2e_floor["fp64_direct"] = e2e_floor["fp64_copy"]
+    e2e_best = min(e2e_paths, key=e2e_paths.get)
+    e2e_ms = e2e_paths[e2e_best]
+    e2e_value = bytes_step * ws / (e2e_ms * 1e-3) / 1e9
+    e2e_io_bytes = v * 24 * (4 if e2e_best == "fp32_copy" else 8)
+    e2e_desc = {"fp64_copy": "pinned FP64 canonical H2D -> wd.pack -> wd.dslash_apply -> wd.unpack -> D2H",
+                "fp64_direct": "pinned FP64 canonical source and result passed to wd.pack / wd.unpack, which "
+                               "read and write them over the host link; wd.dslash_apply between",
+                "fp32_copy": "pinned FP32 canonical H2D -> wd.pack (wd_pack_f32) -> wd.dslash_apply -> "
+                             "wd.unpack (wd_unpack_f32) -> D2H"}
 
     variants = {}
     if not args.no_variants:
@@ -461,15 +472,11 @@ def run_gpu(args):
                      "traffic_gbs": (traffic / (mean_launch * 1e-3) / 1e9) if traffic else None,
                      "nominal_peak": props["nominal_hbm_gbs"], "frac_of_nominal": achieved / props["nominal_hbm_gbs"],
                      "nominal_from": f"2 x {props['mem_clock_khz'] / 1e3:.0f} MHz x {props['mem_bus_bits']} bit / 8"},
-        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": v * 24 * 8,
-                "d2h_bytes_per_step": v * 24 * 8, "ms_per_step": e2e_ms,
-                "copy_floor_ms_per_step": copy_floor_ms, "frac_of_copy_floor": copy_floor_ms / e2e_ms,
-                "path": ("pinned FP64 canonical source and result passed to wd.pack / wd.unpack, which read "
-                         "and write them directly over the host link; wd.dslash_apply between"
-                         if e2e_direct_ms <= e2e_copy_ms else
-                         "pinned H2D FP64 canonical -> wd.pack -> wd.dslash_apply -> wd.unpack -> D2H")
-                        + ", steps alternating over two streams",
-                "paths_ms_per_step": {"copy_engines": e2e_copy_ms, "direct_host_access": e2e_direct_ms}},
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": e2e_io_bytes,
+                "d2h_bytes_per_step": e2e_io_bytes, "ms_per_step": e2e_ms,
+                "copy_floor_ms_per_step": e2e_floor[e2e_best], "frac_of_copy_floor": e2e_floor[e2e_best] / e2e_ms,
+                "path": e2e_desc[e2e_best] + ", steps alternating over two streams",
+                "paths_ms_per_step": e2e_paths, "paths_copy_floor_ms_per_step": e2e_floor},
         "autotune": {"chosen": {"threads": best["threads"], "variant": best["variant"]},
                      "candidates_us": {f"{t['threads']}/v{t['variant']}":
                                        (round(t["ms"] * 1e3, 1) if t["ms"] == t["ms"] else None)

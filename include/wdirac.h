@@ -106,6 +106,14 @@ int wd_pack(wd_ctx *ctx, const int dims[4], int sites, int prec, const double *a
             void *field, void *stream);
 int wd_unpack(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *field,
               double *aos, void *stream);
+/* The same with a canonical array of FP32 reals (24 per site, same order): for
+ * callers whose host fields are single precision, which halves the bytes that
+ * cross the host link for an FP32 or 16-bit workload.  wd_unpack_f32 rounds
+ * FP64 fields to FP32. */
+int wd_pack_f32(wd_ctx *ctx, const int dims[4], int sites, int prec, const float *aos,
+                void *field, void *stream);
+int wd_unpack_f32(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *field,
+                  float *aos, void *stream);
 
 /* Gauge field (Sec. II-A: one SU(3) matrix per link).  `links` is canonical
  * FP64 (device memory, or host memory if links_on_host != 0); the library

@@ -46,7 +46,9 @@ _SIGS = {
     "wd_ctx_destroy": (_ip, [_vp]),
     "wd_field_bytes": (_ip, [_DIMS, _ip, _ip, _ip, ctypes.POINTER(_sz)]),
     "wd_pack": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _vp, _vp]),
+    "wd_pack_f32": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _vp, _vp]),
     "wd_unpack": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _vp, _vp]),
+    "wd_unpack_f32": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _vp, _vp]),
     "wd_gauge_create": (_ip, [_vp, _DIMS, _vp, _ip, ctypes.POINTER(_vp)]),
     "wd_gauge_prepare": (_ip, [_vp, _ip, _ip]),
     "wd_stream_mul": (_ip, [_vp, _ip, _sz, _vp, _vp, _vp, _vp]),
@@ -194,16 +196,22 @@ def alloc_field(dims, sites: int, prec: int, nrhs: int = 1, device="cuda"):
     return torch.empty(field_bytes(dims, sites, prec, nrhs), dtype=torch.uint8, device=device)
 
 
+def _is_f32(t) -> bool:
+    return getattr(t, "dtype", None) is not None and str(t.dtype) in ("torch.float32", "float32")
+
+
 def pack(ctx: Context, dims, sites: int, prec: int, aos, field, stream=None) -> None:
-    """Canonical FP64 full-lattice spinor (device, or pinned host memory the kernel reads
-    directly) -> device field holding `sites`."""
-    _check(load().wd_pack(ctx.handle, _dims(dims), int(sites), int(prec), _ptr(aos), _ptr(field), _stream(stream)))
+    """Canonical full-lattice spinor (FP64, or FP32 for a float32 tensor; device, or pinned
+    host memory the kernel reads directly) -> device field holding `sites`."""
+    fn = load().wd_pack_f32 if _is_f32(aos) else load().wd_pack
+    _check(fn(ctx.handle, _dims(dims), int(sites), int(prec), _ptr(aos), _ptr(field), _stream(stream)))
 
 
 def unpack(ctx: Context, dims, sites: int, prec: int, field, aos, stream=None) -> None:
-    """Device field -> the sites it holds inside a canonical FP64 full-lattice array (device,
-    or pinned host memory the kernel writes directly)."""
-    _check(load().wd_unpack(ctx.handle, _dims(dims), int(sites), int(prec), _ptr(field), _ptr(aos), _stream(stream)))
+    """Device field -> the sites it holds inside a canonical full-lattice array (FP64, or FP32
+    for a float32 tensor; device, or pinned host memory the kernel writes directly)."""
+    fn = load().wd_unpack_f32 if _is_f32(aos) else load().wd_unpack
+    _check(fn(ctx.handle, _dims(dims), int(sites), int(prec), _ptr(field), _ptr(aos), _stream(stream)))
 
 
 class Gauge:

@@ -79,28 +79,36 @@ struct SiteMap {
     }
 };
 
-template <int P>
-__global__ void pack_spinor_kernel(const double *__restrict__ aos, char *__restrict__ field, SiteMap m)
+// Canonical spinor arrays hold 24 reals per site of type CT (double or
+// float): CT2 is a complex pair, NC the site's 16-byte chunks.
+template <typename CT> struct Canon;
+template <> struct Canon<double> { using CT2 = double2; static constexpr int NC = 12; };
+template <> struct Canon<float> { using CT2 = float2; static constexpr int NC = 6; };
+
+template <int P, typename CT>
+__global__ void pack_spinor_kernel(const CT *__restrict__ aos, char *__restrict__ field, SiteMap m)
 {
+    using CT2 = typename Canon<CT>::CT2;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (int64_t)m.np * m.vh) return;
     const int slot = (int)(gid / m.vh);
     const int i = (int)(gid - (int64_t)slot * m.vh);
     const int64_t s = m.lex(m.p0 + slot, i);
     typename Prec<P>::real v[24];
-    const double2 *src = reinterpret_cast<const double2 *>(aos + s * 24);
+    const CT2 *src = reinterpret_cast<const CT2 *>(aos + s * 24);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        double2 d = src[k];
+        const CT2 d = src[k];
         v[2 * k] = (typename Prec<P>::real)d.x;
         v[2 * k + 1] = (typename Prec<P>::real)d.y;
     }
     Spinor<P>::store(field + slot * m.half_bytes, m.vh, i, v);
 }
 
-template <int P>
-__global__ void unpack_spinor_kernel(const char *__restrict__ field, double *__restrict__ aos, SiteMap m)
+template <int P, typename CT>
+__global__ void unpack_spinor_kernel(const char *__restrict__ field, CT *__restrict__ aos, SiteMap m)
 {
+    using CT2 = typename Canon<CT>::CT2;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (int64_t)m.np * m.vh) return;
     const int slot = (int)(gid / m.vh);
@@ -108,20 +116,20 @@ __global__ void unpack_spinor_kernel(const char *__restrict__ field, double *__r
     const int64_t s = m.lex(m.p0 + slot, i);
     typename Prec<P>::real v[24];
     Spinor<P>::load(field + slot * m.half_bytes, m.vh, i, v);
-    double2 *dst = reinterpret_cast<double2 *>(aos + s * 24);
+    CT2 *dst = reinterpret_cast<CT2 *>(aos + s * 24);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) dst[k] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
+    for (int k = 0; k < 12; ++k) dst[k] = CT2{(CT)v[2 * k], (CT)v[2 * k + 1]};
 }
 
 // Full-lattice fields (both parities) in lexicographic order: block b takes
 // sites [LEX_TILE*b, LEX_TILE*b + LEX_TILE), so the canonical array moves as
-// contiguous 16-byte chunks staged in shared memory (a site's 12 double2 at a
-// padded stride of 13, which keeps the 16-byte shared accesses conflict-free),
-// while the field side is read or written per site from its parity's planes.
-// (In checkerboard order the canonical side is touched at a 2-site stride, so
-// each cache line is filled in two passes that lie a half field apart.)
+// contiguous 16-byte chunks staged in shared memory (a site's NC chunks at a
+// padded stride of NC + 1, an odd number of chunks, which keeps the 16-byte
+// shared accesses conflict-free), while the field side is read or written per
+// site from its parity's planes.  (In checkerboard order the canonical side is
+// touched at a 2-site stride, so each cache line is filled in two passes that
+// lie a half field apart.)
 constexpr int LEX_TILE = 128;
-constexpr int LEX_PAD = 13;
 
 __device__ __forceinline__ void lex_to_cb(const SiteMap &m, int64_t s, int &p, int &i)
 {
@@ -135,34 +143,33 @@ __device__ __forceinline__ void lex_to_cb(const SiteMap &m, int64_t s, int &p, i
     i = (int)(r * (m.Lx >> 1) + (x >> 1));
 }
 
-template <int P>
-__global__ void __launch_bounds__(LEX_TILE) pack_lex_kernel(const double *__restrict__ aos, char *__restrict__ field,
+template <int P, typename CT>
+__global__ void __launch_bounds__(LEX_TILE) pack_lex_kernel(const CT *__restrict__ aos, char *__restrict__ field,
                                                             SiteMap m, int64_t V)
 {
-    __shared__ double2 sh[LEX_TILE * LEX_PAD];
+    constexpr int NC = Canon<CT>::NC, PAD = NC + 1;
+    __shared__ uint4 sh[LEX_TILE * PAD];
     const int64_t s0 = (int64_t)blockIdx.x * LEX_TILE;
     const int n = (int)min((int64_t)LEX_TILE, V - s0);
-    const double2 *src = reinterpret_cast<const double2 *>(aos + s0 * 24);
-    for (int c = threadIdx.x; c < n * 12; c += LEX_TILE) sh[(c / 12) * LEX_PAD + c % 12] = src[c];
+    const uint4 *src = reinterpret_cast<const uint4 *>(aos + s0 * 24);
+    for (int c = threadIdx.x; c < n * NC; c += LEX_TILE) sh[(c / NC) * PAD + c % NC] = src[c];
     __syncthreads();
     if ((int)threadIdx.x >= n) return;
     int p, i;
     lex_to_cb(m, s0 + threadIdx.x, p, i);
+    const CT *site = reinterpret_cast<const CT *>(&sh[threadIdx.x * PAD]);
     typename Prec<P>::real v[24];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        const double2 d = sh[threadIdx.x * LEX_PAD + k];
-        v[2 * k] = (typename Prec<P>::real)d.x;
-        v[2 * k + 1] = (typename Prec<P>::real)d.y;
-    }
+    for (int k = 0; k < 24; ++k) v[k] = (typename Prec<P>::real)site[k];
     Spinor<P>::store(field + p * m.half_bytes, m.vh, i, v);
 }
 
-template <int P>
-__global__ void __launch_bounds__(LEX_TILE) unpack_lex_kernel(const char *__restrict__ field, double *__restrict__ aos,
+template <int P, typename CT>
+__global__ void __launch_bounds__(LEX_TILE) unpack_lex_kernel(const char *__restrict__ field, CT *__restrict__ aos,
                                                               SiteMap m, int64_t V)
 {
-    __shared__ double2 sh[LEX_TILE * LEX_PAD];
+    constexpr int NC = Canon<CT>::NC, PAD = NC + 1;
+    __shared__ uint4 sh[LEX_TILE * PAD];
     const int64_t s0 = (int64_t)blockIdx.x * LEX_TILE;
     const int n = (int)min((int64_t)LEX_TILE, V - s0);
     if ((int)threadIdx.x < n) {
@@ -170,12 +177,13 @@ __global__ void __launch_bounds__(LEX_TILE) unpack_lex_kernel(const char *__rest
         lex_to_cb(m, s0 + threadIdx.x, p, i);
         typename Prec<P>::real v[24];
         Spinor<P>::load(field + p * m.half_bytes, m.vh, i, v);
+        CT *site = reinterpret_cast<CT *>(&sh[threadIdx.x * PAD]);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) sh[threadIdx.x * LEX_PAD + k] = make_double2((double)v[2 * k], (double)v[2 * k + 1]);
+        for (int k = 0; k < 24; ++k) site[k] = (CT)v[k];
     }
     __syncthreads();
-    double2 *dst = reinterpret_cast<double2 *>(aos + s0 * 24);
-    for (int c = threadIdx.x; c < n * 12; c += LEX_TILE) dst[c] = sh[(c / 12) * LEX_PAD + c % 12];
+    uint4 *dst = reinterpret_cast<uint4 *>(aos + s0 * 24);
+    for (int c = threadIdx.x; c < n * NC; c += LEX_TILE) dst[c] = sh[(c / NC) * PAD + c % NC];
 }
 
 // ---- link pack -----------------------------------------------------------
@@ -487,13 +495,18 @@ static int pack_common(wd_ctx *ctx, const int dims[4], int sites, int prec, cons
     return sites_to_map(g, sites, prec, m);
 }
 
-int wd_pack(wd_ctx *ctx, const int dims[4], int sites, int prec, const double *aos, void *field, void *stream)
+} // extern "C"
+
+namespace wd {
+
+template <typename CT>
+static int pack_impl(wd_ctx *ctx, const int dims[4], int sites, int prec, const CT *aos, void *field, void *stream)
 {
     clear_error();
     Geometry g;
     SiteMap m;
     WD_TRY(pack_common(ctx, dims, sites, prec, aos, field, g, m));
-    aos = (const double *)device_view(ctx, aos);
+    aos = (const CT *)device_view(ctx, aos);
     if (!aos) return set_error(WD_EINVAL, "the canonical array is not accessible from the context's device");
     cudaStream_t s = (cudaStream_t)stream;
     char *f = (char *)field;
@@ -501,10 +514,10 @@ int wd_pack(wd_ctx *ctx, const int dims[4], int sites, int prec, const double *a
         const int64_t V = 2 * (int64_t)m.vh;
         const int blocks = (int)((V + LEX_TILE - 1) / LEX_TILE);
         switch (prec) {
-        case WD_F64: pack_lex_kernel<PREC_F64><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
-        case WD_F32: pack_lex_kernel<PREC_F32><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
-        case WD_F16: pack_lex_kernel<PREC_F16><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
-        case WD_BF16: pack_lex_kernel<PREC_BF16><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
+        case WD_F64: pack_lex_kernel<PREC_F64, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
+        case WD_F32: pack_lex_kernel<PREC_F32, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
+        case WD_F16: pack_lex_kernel<PREC_F16, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
+        case WD_BF16: pack_lex_kernel<PREC_BF16, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
         }
         WD_CUDA_TRY(cudaGetLastError());
         return WD_OK;
@@ -512,22 +525,23 @@ int wd_pack(wd_ctx *ctx, const int dims[4], int sites, int prec, const double *a
     const int threads = 256;
     const int blocks = (int)(((int64_t)m.np * m.vh + threads - 1) / threads);
     switch (prec) {
-    case WD_F64: pack_spinor_kernel<PREC_F64><<<blocks, threads, 0, s>>>(aos, f, m); break;
-    case WD_F32: pack_spinor_kernel<PREC_F32><<<blocks, threads, 0, s>>>(aos, f, m); break;
-    case WD_F16: pack_spinor_kernel<PREC_F16><<<blocks, threads, 0, s>>>(aos, f, m); break;
-    case WD_BF16: pack_spinor_kernel<PREC_BF16><<<blocks, threads, 0, s>>>(aos, f, m); break;
+    case WD_F64: pack_spinor_kernel<PREC_F64, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
+    case WD_F32: pack_spinor_kernel<PREC_F32, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
+    case WD_F16: pack_spinor_kernel<PREC_F16, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
+    case WD_BF16: pack_spinor_kernel<PREC_BF16, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
     }
     WD_CUDA_TRY(cudaGetLastError());
     return WD_OK;
 }
 
-int wd_unpack(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *field, double *aos, void *stream)
+template <typename CT>
+static int unpack_impl(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *field, CT *aos, void *stream)
 {
     clear_error();
     Geometry g;
     SiteMap m;
     WD_TRY(pack_common(ctx, dims, sites, prec, field, aos, g, m));
-    aos = (double *)device_view(ctx, aos);
+    aos = (CT *)device_view(ctx, aos);
     if (!aos) return set_error(WD_EINVAL, "the canonical array is not accessible from the context's device");
     cudaStream_t s = (cudaStream_t)stream;
     const char *f = (const char *)field;
@@ -535,10 +549,10 @@ int wd_unpack(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *f
         const int64_t V = 2 * (int64_t)m.vh;
         const int blocks = (int)((V + LEX_TILE - 1) / LEX_TILE);
         switch (prec) {
-        case WD_F64: unpack_lex_kernel<PREC_F64><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
-        case WD_F32: unpack_lex_kernel<PREC_F32><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
-        case WD_F16: unpack_lex_kernel<PREC_F16><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
-        case WD_BF16: unpack_lex_kernel<PREC_BF16><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
+        case WD_F64: unpack_lex_kernel<PREC_F64, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
+        case WD_F32: unpack_lex_kernel<PREC_F32, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
+        case WD_F16: unpack_lex_kernel<PREC_F16, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
+        case WD_BF16: unpack_lex_kernel<PREC_BF16, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
         }
         WD_CUDA_TRY(cudaGetLastError());
         return WD_OK;
@@ -546,13 +560,37 @@ int wd_unpack(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *f
     const int threads = 256;
     const int blocks = (int)(((int64_t)m.np * m.vh + threads - 1) / threads);
     switch (prec) {
-    case WD_F64: unpack_spinor_kernel<PREC_F64><<<blocks, threads, 0, s>>>(f, aos, m); break;
-    case WD_F32: unpack_spinor_kernel<PREC_F32><<<blocks, threads, 0, s>>>(f, aos, m); break;
-    case WD_F16: unpack_spinor_kernel<PREC_F16><<<blocks, threads, 0, s>>>(f, aos, m); break;
-    case WD_BF16: unpack_spinor_kernel<PREC_BF16><<<blocks, threads, 0, s>>>(f, aos, m); break;
+    case WD_F64: unpack_spinor_kernel<PREC_F64, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
+    case WD_F32: unpack_spinor_kernel<PREC_F32, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
+    case WD_F16: unpack_spinor_kernel<PREC_F16, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
+    case WD_BF16: unpack_spinor_kernel<PREC_BF16, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
     }
     WD_CUDA_TRY(cudaGetLastError());
     return WD_OK;
+}
+
+} // namespace wd
+
+extern "C" {
+
+int wd_pack(wd_ctx *ctx, const int dims[4], int sites, int prec, const double *aos, void *field, void *stream)
+{
+    return pack_impl<double>(ctx, dims, sites, prec, aos, field, stream);
+}
+
+int wd_unpack(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *field, double *aos, void *stream)
+{
+    return unpack_impl<double>(ctx, dims, sites, prec, field, aos, stream);
+}
+
+int wd_pack_f32(wd_ctx *ctx, const int dims[4], int sites, int prec, const float *aos, void *field, void *stream)
+{
+    return pack_impl<float>(ctx, dims, sites, prec, aos, field, stream);
+}
+
+int wd_unpack_f32(wd_ctx *ctx, const int dims[4], int sites, int prec, const void *field, float *aos, void *stream)
+{
+    return unpack_impl<float>(ctx, dims, sites, prec, field, aos, stream);
 }
 
 int wd_gauge_create(wd_ctx *ctx, const int dims[4], const double *links, int links_on_host, wd_gauge **out)

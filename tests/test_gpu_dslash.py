@@ -123,6 +123,33 @@ def test_pack_unpack_with_host_memory(ctx, prec, sites):
         assert torch.equal(f_dev, f_pg)
 
 
+@pytest.mark.parametrize("prec", ALL_PREC)
+@pytest.mark.parametrize("sites", [wd.SITES_FULL, wd.SITES_ODD])
+def test_pack_unpack_fp32_canonical(ctx, prec, sites):
+    """wd_pack_f32 / wd_unpack_f32: an FP32 canonical array gives the same field bytes as the
+    FP64 path fed the same (FP32-rounded) values, and unpacks to the FP64 result rounded to
+    FP32, from device and from pinned host memory."""
+    import torch
+    dims = (4, 6, 8, 10)
+    psi = synth.spinor(dims, seed=2014)
+    flat32 = psi.view(np.float64).reshape(-1).astype(np.float32)
+    as64 = torch.from_numpy(flat32.astype(np.float64)).cuda()
+    f64path = wd.alloc_field(dims, sites, prec)
+    wd.pack(ctx, dims, sites, prec, as64, f64path)
+    for src in (torch.from_numpy(flat32.copy()).cuda(), torch.from_numpy(flat32.copy()).pin_memory()):
+        f32path = wd.alloc_field(dims, sites, prec)
+        wd.pack(ctx, dims, sites, prec, src, f32path)
+        torch.cuda.synchronize()
+        assert torch.equal(f64path, f32path)
+    out64 = torch.zeros(flat32.size, dtype=torch.float64, device="cuda")
+    wd.unpack(ctx, dims, sites, prec, f64path, out64)
+    for dst in (torch.zeros(flat32.size, dtype=torch.float32, device="cuda"),
+                torch.zeros(flat32.size, dtype=torch.float32).pin_memory()):
+        wd.unpack(ctx, dims, sites, prec, f64path, dst)
+        torch.cuda.synchronize()
+        assert np.array_equal(dst.cpu().numpy(), out64.cpu().numpy().astype(np.float32))
+
+
 @pytest.mark.parametrize("dims", DIMS)
 @pytest.mark.parametrize("recon", [18, 12])
 @pytest.mark.parametrize("prec", ALL_PREC)
