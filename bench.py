@@ -327,8 +327,8 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
 
     # end to end through the public API with host buffers.  Three paths, each over the same
-    # host-resident spinor, timed the same way (consecutive steps alternate between two
-    # streams and buffer sets, so one step's H2D copy overlaps the previous step's D2H copy):
+    # host-resident spinor, timed the same way (consecutive steps rotate over 2 or 3 streams
+    # and buffer sets, so one step's H2D copy overlaps another step's D2H copy and compute):
     #   fp64_copy:   pinned FP64 canonical source -> H2D -> wd.pack -> wd.dslash_apply ->
     #                wd.unpack -> D2H into a pinned FP64 canonical result;
     #   fp64_direct: the pinned FP64 buffers handed to wd.pack / wd.unpack, which read and
@@ -337,8 +337,9 @@ def run_gpu(args):
     #                wd_unpack_f32), half the bytes over the link.
     e2e_steps = max(4, min(args.steps, 20))
     host32 = torch.from_numpy(psi.view(np.float64).reshape(-1).astype(np.float32)).pin_memory()
+    NS = 3   # streams (and buffer sets) the end-to-end loops rotate over
     sets = []
-    for k in range(2):
+    for k in range(NS):
         s_k = torch.cuda.Stream() if k else stream
         sets.append(dict(s=s_k, aos=aos if k == 0 else torch.empty_like(aos), fin=fin if k == 0 else torch.empty_like(fin),
                          fout=fout if k == 0 else torch.empty_like(fout), aos_out=torch.empty_like(aos),
@@ -348,7 +349,7 @@ def run_gpu(args):
                          out_host32=torch.empty_like(host32).pin_memory()))
 
     def fp64_copy(k):
-        b = sets[k % 2]
+        b = sets[k % nsets[0]]
         with torch.cuda.stream(b["s"]):
             b["aos"].copy_(psi_host, non_blocking=True)
             wd.pack(ctx, dims, wd.SITES_FULL, prec, b["aos"], b["fin"], stream=b["s"])
@@ -357,13 +358,13 @@ def run_gpu(args):
             b["out_host"].copy_(b["aos_out"], non_blocking=True)
 
     def fp64_direct(k):
-        b = sets[k % 2]
+        b = sets[k % nsets[0]]
         wd.pack(ctx, dims, wd.SITES_FULL, prec, psi_host, b["fin"], stream=b["s"])
         wd.dslash_apply(ctx, g, b["fout"], b["fin"], MASS, prec=prec, recon=recon, stream=b["s"])
         wd.unpack(ctx, dims, wd.SITES_FULL, prec, b["fout"], b["out_host"], stream=b["s"])
 
     def fp32_copy(k):
-        b = sets[k % 2]
+        b = sets[k % nsets[0]]
         with torch.cuda.stream(b["s"]):
             b["aos32"].copy_(host32, non_blocking=True)
             wd.pack(ctx, dims, wd.SITES_FULL, prec, b["aos32"], b["fin"], stream=b["s"])
@@ -373,39 +374,47 @@ def run_gpu(args):
 
     # the host-link floor of a path: its H2D and D2H copies alone, concurrently
     def copies64(k):
-        b = sets[k % 2]
+        b = sets[k % nsets[0]]
         with torch.cuda.stream(b["s"]):
             b["aos"].copy_(psi_host, non_blocking=True)
             b["out_host"].copy_(b["aos_out"], non_blocking=True)
 
     def copies32(k):
-        b = sets[k % 2]
+        b = sets[k % nsets[0]]
         with torch.cuda.stream(b["s"]):
             b["aos32"].copy_(host32, non_blocking=True)
             b["out_host32"].copy_(b["aos32_out"], non_blocking=True)
 
-    def time_loop(step):
-        for k in range(4):
+    nsets = [NS]   # streams in use by the loops below
+
+    def time_loop(step, n):
+        nsets[0] = n
+        for k in range(2 * n):
             step(k)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        sets[1]["s"].wait_event(e0)
+        for b in sets[1:n]:
+            b["s"].wait_event(e0)
         for k in range(e2e_steps):
             step(k)
-        stream.wait_stream(sets[1]["s"])
+        for b in sets[1:n]:
+            stream.wait_stream(b["s"])
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / e2e_steps
 
-    e2e_paths = {"fp64_copy": time_loop(fp64_copy), "fp64_direct": time_loop(fp64_direct),
-                 "fp32_copy": time_loop(fp32_copy)}
-    e2e_floor = {"fp64_copy": time_loop(copies64), "fp32_copy": time_loop(copies32)}
-    e2e_floor["fp64_direct"] = e2e_floor["fp64_copy"]
+    e2e_paths, e2e_floor = {}, {}
+    for n in (2, NS):
+        for name, fn in (("fp64_copy", fp64_copy), ("fp64_direct", fp64_direct), ("fp32_copy", fp32_copy)):
+            e2e_paths[f"{name}_{n}streams"] = time_loop(fn, n)
+        e2e_floor[f"fp64_copy_{n}streams"] = time_loop(copies64, n)
+        e2e_floor[f"fp32_copy_{n}streams"] = time_loop(copies32, n)
+        e2e_floor[f"fp64_direct_{n}streams"] = e2e_floor[f"fp64_copy_{n}streams"]
     e2e_best = min(e2e_paths, key=e2e_paths.get)
     e2e_ms = e2e_paths[e2e_best]
     e2e_value = bytes_step * ws / (e2e_ms * 1e-3) / 1e9
-    e2e_io_bytes = v * 24 * (4 if e2e_best == "fp32_copy" else 8)
+    e2e_io_bytes = v * 24 * (4 if e2e_best.startswith("fp32") else 8)
     e2e_desc = {"fp64_copy": "pinned FP64 canonical H2D -> wd.pack -> wd.dslash_apply -> wd.unpack -> D2H",
                 "fp64_direct": "pinned FP64 canonical source and result passed to wd.pack / wd.unpack, which "
                                "read and write them over the host link; wd.dslash_apply between",
@@ -475,7 +484,8 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": e2e_io_bytes,
                 "d2h_bytes_per_step": e2e_io_bytes, "ms_per_step": e2e_ms,
                 "copy_floor_ms_per_step": e2e_floor[e2e_best], "frac_of_copy_floor": e2e_floor[e2e_best] / e2e_ms,
-                "path": e2e_desc[e2e_best] + ", steps alternating over two streams",
+                "path": e2e_desc[e2e_best.rsplit("_", 1)[0]] + ", consecutive steps rotating over "
+                        + e2e_best.rsplit("_", 1)[1].replace("streams", " streams"),
                 "paths_ms_per_step": e2e_paths, "paths_copy_floor_ms_per_step": e2e_floor},
         "autotune": {"chosen": {"threads": best["threads"], "variant": best["variant"]},
                      "candidates_us": {f"{t['threads']}/v{t['variant']}":
