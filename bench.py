@@ -135,6 +135,90 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+HEADLINE_MAX_BYTES = 4096
+
+
+def compose_headline(headline: dict, detail: dict, detail_path) -> dict:
+    """The one JSON object printed last on stdout: the headline measurement and a
+    few key secondary numbers pulled from the detail sections, nothing bulky.
+
+    `headline` holds the measured keys (metric, value, unit, n_gpus, steps, warmup,
+    ms_per_step, dtype, config, roofline, e2e, clocks, gpu_launches, cpu_baseline);
+    `detail` the full sections, which go to the file `detail_path` instead."""
+    line = {"impl": "wdirac"}
+    line.update({k: headline[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step")})
+    line.update({"higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                 "dtype": headline["dtype"], "data": "synthetic"})
+    for k in ("config", "gflops", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"):
+        if k in headline:
+            line[k] = headline[k]
+    cb = line.get("cpu_baseline")
+    if cb is not None:
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample") if k in cb}
+    sec = {}
+    cg = detail.get("cg") or {}
+    runs = cg.get("runs", {})
+    for m in ("0.1", "0.05"):
+        r64, r16 = runs.get(f"m{m}/fp64"), runs.get(f"m{m}/fp16")
+        if r64 and r16:
+            sec[f"cg_24x24x24x48_m{m}"] = {"fp64_s": r64["seconds"], "fp16_s": r16["seconds"],
+                                            "speedup": round(r64["seconds"] / r16["seconds"], 2),
+                                            "fp16_true_rel_resid": r16["true_rel_resid"]}
+    oc = detail.get("cpu_oracle_cg")
+    if oc:
+        sec["cpu_oracle_cg_24x24x24x48_m0.1_s"] = oc.get("seconds")
+    mr = (detail.get("multi_rhs") or {}).get("eo")
+    if mr:
+        sec["mrhs12_eo_32x32x32x32"] = {"multi_ms": mr["multi_ms"], "singles_ms": mr["singles_ms"],
+                                        "frac_hbm": mr["multi_frac_hbm"]}
+    srv = (detail.get("serving") or {}).get("rate_200")
+    if srv:
+        sec["serving_200_per_s"] = {"p50_ms": srv["p50_ms"], "p99_ms": srv["p99_ms"],
+                                    "solves_per_s": srv["achieved_per_s"]}
+        if "frac_hbm" in srv:
+            sec["serving_200_per_s"]["frac_hbm"] = srv["frac_hbm"]
+    bt = detail.get("batch") or {}
+    if "graph" in bt and "persistent" in bt:
+        sec["batch24"] = {"graph_s": bt["graph"]["seconds"], "persistent_s": bt["persistent"]["seconds"],
+                          "sequential_s": bt.get("sequential", {}).get("seconds")}
+    if sec:
+        line["secondary"] = sec
+    line["detail"] = detail_path
+    return line
+
+
+def write_detail(detail: dict, path: str):
+    """Writes the full detail sections as JSON to `path` (created with its folder);
+    returns the path, or None if it could not be written."""
+    if not path:
+        return None
+    try:
+        d = os.path.dirname(os.path.abspath(path))
+        os.makedirs(d, exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(detail, f, indent=1, default=float)
+        return path
+    except OSError as e:
+        print(f"[bench] detail not written: {e}", file=sys.stderr, flush=True)
+        return None
+
+
+def _cpu_oracle_cg(dims=(24, 24, 24, 48), mass=0.1, tol=1e-10):
+    """One full FP64 oracle CG solve of the even-odd normal equations on 24^3x48 (the mixed-CG
+    benchmark's gauge field and source), on all host threads: seconds, iterations and the
+    oracle's own true residual."""
+    import oracle
+    import synth
+    U = synth.gauge(dims, seed=1000 + 3)
+    b = synth.even_spinor(dims, seed=3001)
+    t0 = time.perf_counter()
+    _, it, rel = oracle.cg(dims, U, mass, b, tol=tol)
+    el = time.perf_counter() - t0
+    return {"seconds": round(el, 3), "iters": it, "true_rel_resid": rel, "cores": oracle.max_threads(),
+            "cpu_model": _cpu_model(), "lattice": list(dims), "mass": mass, "tol": tol,
+            "how": "oracle.cg, textbook FP64 CG from x0 = 0, one full solve"}
+
+
 _T0 = time.perf_counter()
 
 
@@ -464,15 +548,14 @@ def run_gpu(args):
     cg = None
     if not args.no_cg:
         _log("cg")
-        cg = _cg_section(wd, torch, ctx, with_cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline), peak=peak)
+        cg = _cg_section(wd, torch, ctx, peak=peak)
     _log("done")
 
     traffic = _traffic_from_profile()
     props = wd.device_info(ctx)
-    line = {
+    headline = {
         "metric": "dslash_hbm_gbs", "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "dtype": "f32",
         "config": {"workload": "wilson_dslash_full_fp32_recon18_32x32x32x32", "lattice": list(dims),
                    "sites": v, "mass": MASS, "links": "exp(0.2 i H) smoothed SU(3), seed 1001",
                    "source": "Gaussian N(0,1), seed 2001", "bytes_per_site": 480,
@@ -481,23 +564,25 @@ def run_gpu(args):
         "gflops": FLOPS_PER_SITE * v * args.steps * ws / (total_ms * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "kernel": HEADLINE_KERNEL, "achieved": achieved, "peak": peak,
                      "peak_kind": f"{peak_kind} copy bandwidth (burst)", "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_step,
-                     "mean_launch_ms": mean_launch, "median_launch_ms": statistics.median(launch_ms),
+                     "traffic": traffic, "mean_launch_ms": mean_launch},
+        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": e2e_io_bytes,
+                "d2h_bytes_per_step": e2e_io_bytes, "ms_per_step": e2e_ms,
+                "path": e2e_desc[e2e_best.rsplit("_", 1)[0]] + ", consecutive steps rotating over "
+                        + e2e_best.rsplit("_", 1)[1].replace("streams", " streams")},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    detail = {
+        "roofline": {"algorithmic_bytes_per_launch": bytes_step, "median_launch_ms": statistics.median(launch_ms),
                      "traffic_gbs": (traffic / (mean_launch * 1e-3) / 1e9) if traffic else None,
                      "nominal_peak": props["nominal_hbm_gbs"], "frac_of_nominal": achieved / props["nominal_hbm_gbs"],
                      "nominal_from": f"2 x {props['mem_clock_khz'] / 1e3:.0f} MHz x {props['mem_bus_bits']} bit / 8"},
-        "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": e2e_io_bytes,
-                "d2h_bytes_per_step": e2e_io_bytes, "ms_per_step": e2e_ms,
-                "copy_floor_ms_per_step": e2e_floor[e2e_best], "frac_of_copy_floor": e2e_floor[e2e_best] / e2e_ms,
-                "path": e2e_desc[e2e_best.rsplit("_", 1)[0]] + ", consecutive steps rotating over "
-                        + e2e_best.rsplit("_", 1)[1].replace("streams", " streams"),
+        "e2e": {"copy_floor_ms_per_step": e2e_floor[e2e_best], "frac_of_copy_floor": e2e_floor[e2e_best] / e2e_ms,
                 "paths_ms_per_step": e2e_paths, "paths_copy_floor_ms_per_step": e2e_floor},
         "autotune": {"chosen": {"threads": best["threads"], "variant": best["variant"]},
                      "candidates_us": {f"{t['threads']}/v{t['variant']}":
                                        (round(t["ms"] * 1e3, 1) if t["ms"] == t["ms"] else None)
                                        for t in tune_table}},
-        "gpu_launches": args.steps,
-        "clocks": clk.summary(),
         "variants": variants,
         "multi_rhs": mrhs,
         "blas": blas,
@@ -509,10 +594,17 @@ def run_gpu(args):
         "serving": serving,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline()
-        line["cpu_baseline"]["sizes"] = _cpu_sizes(U, psi)
+        _log("cpu_baseline")
+        headline["cpu_baseline"] = _cpu_baseline()
+        _log("cpu_sizes")
+        detail["cpu_sizes"] = _cpu_sizes(U, psi)
+        if cg is not None and not args.no_oracle_cg:
+            _log("cpu_oracle_cg")
+            detail["cpu_oracle_cg"] = _cpu_oracle_cg()
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        detail_path = write_detail(detail, args.detail_out)
+        line = compose_headline(headline, detail, detail_path)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -1049,7 +1141,7 @@ def _solve_section(wd, torch, ctx, peak):
     return out
 
 
-def _cg_section(wd, torch, ctx, with_cpu: bool, peak: float):
+def _cg_section(wd, torch, ctx, peak: float):
     """Mixed-precision vs FP64 CG on the even-odd normal equations, 24^3x48, tol 1e-10."""
     import numpy as np
 
@@ -1101,19 +1193,126 @@ def _cg_section(wd, torch, ctx, with_cpu: bool, peak: float):
         out[f"speedup_fp16_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/fp16"]["seconds"], 2)
         out[f"speedup_fp16_graph_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/fp16_graph"]["seconds"], 2)
         out[f"speedup_bf16_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/bf16"]["seconds"], 2)
-    if with_cpu:
-        import oracle
-        oracle.mdagm(dims, U, 0.1, b)
-        t0 = time.perf_counter()
-        for _ in range(2):
-            oracle.mdagm(dims, U, 0.1, b)
-        per_it = (time.perf_counter() - t0) / 2
-        it64 = out["runs"]["m0.1/fp64"]["iters"]
-        out["cpu_oracle_cg_estimate"] = {
-            "seconds": round(per_it * it64, 2), "cores": oracle.max_threads(),
-            "how": f"oracle Mhat^dagger Mhat time per application ({per_it:.3f} s, 2 reps) x {it64} FP64 GPU iterations"}
     g.close()
     return out
+
+
+def run_case(argv) -> int:
+    """Runs one operator case a few times, for profiling (e.g. under ncu):
+
+        python bench.py --case --op eo --prec f32 --dims 32,32,32,32 --nrhs 12 --launches 4 [--threads 128 --variant 3]
+        python bench.py --case --op cg --prec f16 --dims 24,24,24,48 --launches 1
+        python bench.py --case --op stream --kind 1 --n 16777216 --launches 3
+        python bench.py --case --op dd --nsub 4 --halo f16 --launches 3
+        python bench.py --case --op solve --prec f16 --dims 24,24,24,48 --launches 1
+
+    Inputs are the seeded synthetic gauge field and source of the benchmark.  With
+    --threads/--variant the launch shape is pinned; otherwise the library default
+    is used (no tuning, so few launches precede the profiled ones).  --op cg runs
+    `launches` mixed-precision CG solves (inner precision --prec, reliable updates,
+    delta 0.01, tol 1e-10, mass 0.1) on an even Gaussian source; --graph drives
+    them with CUDA graphs.  --op stream runs `launches` element-wise products of
+    kind --kind on --n elements of N(0,1) arrays.  --op dd applies the operator
+    `launches` times to the lattice split into --nsub slabs (field precision
+    --prec, halos --halo).  --op solve runs `launches` full-system solves
+    D x = b by BiCGStab (inner precision --prec, delta 0.01, tol 1e-10, mass 0.1)."""
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", choices=["full", "eo", "cg", "stream", "dd", "solve"], default="full")
+    ap.add_argument("--nsub", type=int, default=2)
+    ap.add_argument("--halo", choices=["f64", "f32", "f16"], default="f32")
+    ap.add_argument("--kind", type=int, default=1)
+    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--recon", type=int, default=18)
+    ap.add_argument("--dims", default="32,32,32,32")
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--launches", type=int, default=4)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=-1)
+    ap.add_argument("--graph", action="store_true")
+    a = ap.parse_args(argv)
+    import numpy as np
+    import torch
+
+    import paper_1901_07294_gb300 as wd
+    import synth
+
+    prec = {"f64": wd.F64, "f32": wd.F32, "f16": wd.F16, "bf16": wd.BF16}[a.prec]
+    dims = tuple(int(t) for t in a.dims.split(","))
+    ctx = wd.Context(0)
+    if a.op == "stream":
+        gen = torch.Generator(device="cuda").manual_seed(6001)
+        x, y, z = (torch.randn(2 * a.n, dtype=torch.float64, device="cuda", generator=gen) for _ in range(3))
+        for _ in range(a.launches):
+            wd.stream_mul(ctx, a.kind, a.n, x, y, z)
+        torch.cuda.synchronize()
+        print(f"case: stream kind={a.kind} n={a.n} launches={a.launches} ok")
+        return 0
+    if a.op == "dd":
+        hp = {"f64": wd.F64, "f32": wd.F32, "f16": wd.F16}[a.halo]
+        dd = wd.DomainDecomposition(ctx, dims, a.nsub, synth.gauge(dims, seed=1001))
+        ld = dd.local_dims()
+        vloc = int(np.prod(ld))
+        aos = torch.from_numpy(synth.spinor(dims, seed=2001).view(np.float64).reshape(-1).copy()).cuda()
+        ins, outs = [], []
+        for k in range(a.nsub):
+            f = wd.alloc_field(ld, wd.SITES_FULL, prec)
+            wd.pack(ctx, ld, wd.SITES_FULL, prec, aos[k * vloc * 24:(k + 1) * vloc * 24], f)
+            ins.append(f)
+            outs.append(wd.alloc_field(ld, wd.SITES_FULL, prec))
+        for _ in range(a.launches):
+            dd.dslash(outs, ins, 0.1, prec=prec, recon=a.recon, halo_prec=hp)
+        torch.cuda.synchronize()
+        print(f"case: dd {a.prec} halo {a.halo} {a.dims} nsub={a.nsub} launches={a.launches} ok")
+        return 0
+    g = wd.Gauge(ctx, dims, synth.gauge(dims, seed=1001))
+    if a.op == "solve":
+        b = synth.spinor(dims, seed=3201)
+        fb = wd.alloc_field(dims, wd.SITES_FULL, wd.F64)
+        wd.pack(ctx, dims, wd.SITES_FULL, wd.F64, torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
+        fx = wd.alloc_field(dims, wd.SITES_FULL, wd.F64)
+        for _ in range(a.launches):
+            st = wd.wilson_solve(ctx, g, 0.1, fx, fb, tol=1e-10, solver=wd.SOLVER_BICGSTAB, inner_prec=prec,
+                                 inner_recon=a.recon, reliable=True, delta=0.01)
+        torch.cuda.synchronize()
+        print(f"case: solve bicgstab {a.prec} {a.dims} solves={a.launches} iters={st['iters']} "
+              f"updates={st['reliable_updates']} seconds={st['seconds']:.4f} ok")
+        return 0
+    if a.op == "cg":
+        b = synth.even_spinor(dims, seed=3001)
+        fb = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+        wd.pack(ctx, dims, wd.SITES_EVEN, wd.F64, torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
+        fx = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+        for _ in range(a.launches):
+            st = wd.cg_solve(ctx, g, 0.1, fx, fb, tol=1e-10, inner_prec=prec, inner_recon=a.recon, reliable=True,
+                             delta=0.01, use_graph=a.graph)
+        torch.cuda.synchronize()
+        print(f"case: cg {a.prec} r{a.recon} {a.dims} solves={a.launches} iters={st['iters']} "
+              f"updates={st['reliable_updates']} seconds={st['seconds']:.4f} ok")
+        return 0
+    g.prepare(prec, a.recon)
+    full = a.op == "full"
+    if a.threads and a.variant >= 0:
+        wd.tune_set_dslash(ctx, g, prec, a.recon, full, False, a.nrhs, a.threads, a.variant)
+    aos = torch.from_numpy(synth.spinor(dims, seed=2001).view(np.float64).reshape(-1).copy()).cuda()
+    one = wd.alloc_field(dims, wd.SITES_FULL, prec)
+    wd.pack(ctx, dims, wd.SITES_FULL, prec, aos, one)
+    if full:
+        fin = one.repeat(a.nrhs)
+        fout = wd.alloc_field(dims, wd.SITES_FULL, prec, a.nrhs)
+    else:
+        half = wd.field_bytes(dims, wd.SITES_ODD, prec)
+        fin = one[half:].repeat(a.nrhs)
+        fout = wd.alloc_field(dims, wd.SITES_EVEN, prec, a.nrhs)
+    for _ in range(a.launches):
+        if full:
+            wd.dslash_apply(ctx, g, fout, fin, 0.1, nrhs=a.nrhs, prec=prec, recon=a.recon)
+        else:
+            wd.dslash_eo_apply(ctx, g, fout, fin, None, wd.EVEN, 0.0, 1.0, nrhs=a.nrhs, prec=prec, recon=a.recon)
+    torch.cuda.synchronize()
+    print(f"case: {a.op} {a.prec} r{a.recon} {a.dims} nrhs={a.nrhs} launches={a.launches} ok")
+    return 0
+
 
 
 def main():
@@ -1126,8 +1325,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-oracle-cg", action="store_true", help="skip the full FP64 oracle CG solve on the host")
     ap.add_argument("--launch", default="", help="THREADS,VARIANT: pin the headline launch shape instead of tuning")
+    ap.add_argument("--detail-out", default=os.path.join("gpurun_out", "bench_detail.json"),
+                    help="file for the full detail sections (the stdout line carries the headline only)")
+    ap.add_argument("--case", nargs=argparse.REMAINDER, default=None,
+                    help="run one operator case for profiling instead of the benchmark (see run_case)")
     args = ap.parse_args()
+    if args.case is not None:
+        return run_case(args.case)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -262,20 +262,21 @@ int wd_convert(wd_ctx *ctx, const int dims[4], int sites, int prec_out, void *ou
                const void *in, void *stream);                  /* out = in, new storage precision */
 
 /* |x|^2 like wd_norm2, for callers that cannot allocate device memory and so
- * cannot create a wd_ctx: code running while a CUDA graph is being captured
- * in global mode (cudaMalloc is illegal then), components whose host owns all
- * device memory through a pooling allocator, and latency-critical loops that
- * cannot afford cudaMalloc's implicit synchronisation.  The paper has no
- * counterpart; this is an interface convenience.
+ * cannot create a wd_ctx: plug-ins whose host framework owns all device
+ * memory through a pooling allocator and forbids raw cudaMalloc, and
+ * latency-critical loops that cannot afford cudaMalloc's implicit device
+ * synchronisation.  The paper has no counterpart; this is an interface
+ * convenience.
  * The reduction scratch is a fixed 64 KB array in the library's device code
  * (held by every GPU that loads the library until the process exits); fields
  * of more than 2,097,152 sites (e.g. a full 32^3 x 64 field is the largest
  * such lattice) are rejected with WD_EINVAL.  No cudaMalloc/cudaFree or other
- * allocating call is made.  The first call on a device looks up the array's
- * device address (on the current device); make that first call before any
- * stream capture.  All calls share the one array: calls that overlap on the
- * GPU (other streams, other threads) race and give wrong results.  Results
- * equal wd_norm2's up to FP64 summation order.  `result` is device memory. */
+ * allocating call is made.  The first call on a device (and the first after
+ * its context was reset) looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array: calls that overlap on the GPU (other streams, other
+ * threads) race and give wrong results.  Results equal wd_norm2's up to FP64
+ * summation order.  `result` is device memory. */
 int wd_norm2_noalloc(const int dims[4], int sites, int prec, const void *x, double *result,
                      void *stream);
 

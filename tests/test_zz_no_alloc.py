@@ -1,8 +1,8 @@
 """wd_norm2_noalloc: the norm for callers that cannot allocate device memory.
 
-Such callers (code running during another component's global-mode graph
-capture, plug-ins whose host owns all device memory, latency-critical loops)
-cannot create a context, whose scratch is allocated.  The entry point keeps its
+Such callers (plug-ins whose host framework owns all device memory and
+forbids raw cudaMalloc, latency-critical loops that cannot afford cudaMalloc's
+implicit synchronisation) cannot create a context, whose scratch is allocated.  The entry point keeps its
 scratch in a fixed array inside the library.  This test calls it through the C
 ABI twice in a row and checks each result against wd_norm2's, and checks that a
 field too large for the fixed scratch is refused.  It lives in a file that
