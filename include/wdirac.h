@@ -200,9 +200,7 @@ typedef struct {
 int wd_device_info(const wd_ctx *ctx, wd_device_props *out);
 
 /* Asynchronous device-side status of the context: a kernel whose bounded wait
- * gave up (the bulk-copy staged operator kernel waits at most about a second
- * for its copies) records WD_ETIMEOUT in a context-owned word and skips its
- * output.  wd_device_status waits for all work on the context's device,
+ * gave up records WD_ETIMEOUT in a context-owned word and skips its output.  wd_device_status waits for all work on the context's device,
  * stores that word (WD_OK if nothing was recorded) in *code and clears it.
  * Returns WD_OK, or WD_ECUDA if the device could not be synchronised. */
 int wd_device_status(wd_ctx *ctx, int *code);
@@ -218,11 +216,7 @@ int wd_device_status(wd_ctx *ctx, int *code);
  * 8, 4, which shortens the reuse distance of t-neighbours in L2); and the
  * search's other two dimensions: 8: as 1 with each block's window of nearby
  * neighbour spinors staged in shared memory (tiling on), 9: as 1 with two
- * sites per thread, 10: as 1 with each block's forward links, t-forward
- * neighbours and x term copied into shared memory by bulk (TMA) copies that
- * complete on an mbarrier while the backward directions run; 10 applies when
- * the block size divides Lx/2*Ly*Lz and every plane is 16-byte aligned, and
- * is schedule 1 otherwise; 11, 12: schedules 0 and 1 with the links loaded
+ * sites per thread; 11, 12: schedules 0 and 1 with the links loaded
  * without L1 allocation, which suits even-odd hops, where each link is read
  * once per call).
  * wd_tune_dslash times every candidate for one problem shape (full = 1: the

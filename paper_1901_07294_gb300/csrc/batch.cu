@@ -50,7 +50,8 @@ struct PSolve {
     int block0, nblocks;
     int barrier_target;    // blocks that must arrive at each barrier
     unsigned *bar;         // [0] arrivals, [32] generation (separate lines)
-    double *part;          // 2 buffers x nblocks x 2 partial sums
+    double *part;          // 2 buffers x nchunk x 8 warps x 2 partial sums
+    int nchunk;            // 256-site chunks of a half field: ceil(vh / 256)
     int *out_int;          // [0] status, [1] iterations, [2] reliable updates
     double *out_rel;       // true relative residual
 };
@@ -100,12 +101,47 @@ __device__ bool group_sync(GroupCtx &g)
     return s_fail == 0;
 }
 
-// Deterministic group sum of NR values: block sums to partials, barrier, then
-// every thread adds the partials in block order (same result in all blocks).
-template <int NR> __device__ bool group_sum(GroupCtx &g, double (&v)[NR])
+// Group reductions whose result does not depend on the group size: a half
+// field is cut into chunks of 256 sites (chunk c = sites 256c .. 256c+255, one
+// block-sized pass of the group's loops); each warp's 32 per-site values of a
+// chunk are summed by a fixed shuffle tree and stored as one partial, and the
+// total adds the nchunk x 8 partials in a fixed order.  So a solve gives the
+// same bits whatever group of blocks the batch gives it.
+template <int NR> __device__ __forceinline__ double *group_part(const GroupCtx &g)
+{
+    return g.S->part + (size_t)(g.red & 1) * g.S->nchunk * 8 * 2;
+}
+
+// Stores chunk c's partials of the per-site values v (this thread's site).
+template <int NR> __device__ void chunk_put(const GroupCtx &g, int c, double (&v)[NR])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    if (lane == 0) {
+        double *buf = group_part<NR>(g);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) buf[((size_t)c * 8 + warp) * 2 + k] = v[k];
+    }
+}
+
+// Barrier, then every block adds all partials in the same fixed order (thread t
+// takes entries t, t + 256, ...; then a fixed tree), so all blocks agree.
+template <int NR> __device__ bool group_total(GroupCtx &g, double (&v)[NR])
 {
     __shared__ double sm[8][NR];
+    if (!group_sync(g)) return false;
+    const double *buf = group_part<NR>(g);
+    g.red++;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = g.S->nchunk * 8;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) v[k] = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NR; ++k) v[k] += __ldcg(buf + (size_t)j * 2 + k);
 #pragma unroll
     for (int k = 0; k < NR; ++k)
 #pragma unroll
@@ -114,22 +150,13 @@ template <int NR> __device__ bool group_sum(GroupCtx &g, double (&v)[NR])
 #pragma unroll
         for (int k = 0; k < NR; ++k) sm[warp][k] = v[k];
     __syncthreads();
-    double *buf = g.S->part + (size_t)(g.red & 1) * g.G * 2;
-    g.red++;
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w][k];
-            buf[g.gb * 2 + k] = s;
-        }
-    if (!group_sync(g)) return false;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
-        double s = 0.0;
-        for (int b = 0; b < g.G; ++b) s += __ldcg(buf + b * 2 + k);
-        v[k] = s;
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w][k];
+        v[k] = t;
     }
+    __syncthreads();
     return true;
 }
 
@@ -187,64 +214,78 @@ __global__ void __launch_bounds__(256, 1) cg_persistent_kernel(const PSolve *__r
     const int i0 = g.gb * blockDim.x + threadIdx.x, stride = g.G * blockDim.x;
 
     // |b|^2, then x = 0, r = b, rs = ps = (FP32) b, xs = 0 on this block's sites
-    double v[2] = {0.0, 0.0};
-    for (int i = i0; i < vh; i += stride) {
-        double bv[24];
-        fb.load(i, bv);
-        double s = 0.0;
-        for (int k = 0; k < 24; ++k) s = fma(bv[k], bv[k], s);
-        v[0] += s;
-        fr.store(i, bv);
-        float f[24];
-        for (int k = 0; k < 24; ++k) f[k] = (float)bv[k];
-        frs.store(i, f);
-        fps.store(i, f);
-        for (int k = 0; k < 24; ++k) { bv[k] = 0.0; f[k] = 0.0f; }
-        fx.store(i, bv);
-        fxs.store(i, f);
+    for (int c = g.gb; c < S->nchunk; c += g.G) {
+        const int i = c * 256 + threadIdx.x;
+        double v[1] = {0.0};
+        if (i < vh) {
+            double bv[24];
+            fb.load(i, bv);
+            double s = 0.0;
+            for (int k = 0; k < 24; ++k) s = fma(bv[k], bv[k], s);
+            v[0] = s;
+            fr.store(i, bv);
+            float f[24];
+            for (int k = 0; k < 24; ++k) f[k] = (float)bv[k];
+            frs.store(i, f);
+            fps.store(i, f);
+            for (int k = 0; k < 24; ++k) { bv[k] = 0.0; f[k] = 0.0f; }
+            fx.store(i, bv);
+            fxs.store(i, f);
+        }
+        chunk_put(g, c, v);
     }
-    double one[1] = {v[0]};
-    if (!group_sum(g, one)) return;
+    double one[1];
+    if (!group_total(g, one)) return;
     const double b2 = one[0];
     int status = WD_OK, it = 0, nupd = 0, it_update = 0;
     double r2t = b2;
     if (b2 > 0.0) {
-        const double stop2 = S->tol * S->tol * b2;
+        const double stop2 = SOLVE_TARGET * SOLVE_TARGET * S->tol * S->tol * b2;
         double r2 = b2, maxr = sqrt(b2);
         bool converged = false;
         while (it < S->maxiter) {
             if (!group_mdagm<P>(g, S->hs, S->mass, S->ps, S->aps, S->tso, S->tse)) return;
-            double pap[1] = {0.0};
-            for (int i = i0; i < vh; i += stride) {
-                float pv[24], av[24];
-                fps.load(i, pv);
-                faps.load(i, av);
-                float t = 0.0f;
-                for (int k = 0; k < 24; ++k) t = fmaf(pv[k], av[k], t);
-                pap[0] += (double)t;
+            double pap[1];
+            for (int c = g.gb; c < S->nchunk; c += g.G) {
+                const int i = c * 256 + threadIdx.x;
+                double v[1] = {0.0};
+                if (i < vh) {
+                    float pv[24], av[24];
+                    fps.load(i, pv);
+                    faps.load(i, av);
+                    float t = 0.0f;
+                    for (int k = 0; k < 24; ++k) t = fmaf(pv[k], av[k], t);
+                    v[0] = (double)t;
+                }
+                chunk_put(g, c, v);
             }
-            if (!group_sum(g, pap)) return;
+            if (!group_total(g, pap)) return;
             if (!(pap[0] > 0.0)) { status = WD_ENOCONV; break; }
             const double alpha = r2 / pap[0];
-            double rr[1] = {0.0};
-            for (int i = i0; i < vh; i += stride) {
-                float rv[24], av[24], pv[24], xv[24];
-                frs.load(i, rv);
-                faps.load(i, av);
-                fps.load(i, pv);
-                fxs.load(i, xv);
-                const float af = (float)alpha;
-                float t = 0.0f;
-                for (int k = 0; k < 24; ++k) {
-                    rv[k] = fmaf(-af, av[k], rv[k]);
-                    t = fmaf(rv[k], rv[k], t);
-                    xv[k] = fmaf(af, pv[k], xv[k]);
+            double rr[1];
+            for (int c = g.gb; c < S->nchunk; c += g.G) {
+                const int i = c * 256 + threadIdx.x;
+                double v[1] = {0.0};
+                if (i < vh) {
+                    float rv[24], av[24], pv[24], xv[24];
+                    frs.load(i, rv);
+                    faps.load(i, av);
+                    fps.load(i, pv);
+                    fxs.load(i, xv);
+                    const float af = (float)alpha;
+                    float t = 0.0f;
+                    for (int k = 0; k < 24; ++k) {
+                        rv[k] = fmaf(-af, av[k], rv[k]);
+                        t = fmaf(rv[k], rv[k], t);
+                        xv[k] = fmaf(af, pv[k], xv[k]);
+                    }
+                    frs.store(i, rv);
+                    fxs.store(i, xv);
+                    v[0] = (double)t;
                 }
-                frs.store(i, rv);
-                fxs.store(i, xv);
-                rr[0] += (double)t;
+                chunk_put(g, c, v);
             }
-            if (!group_sum(g, rr)) return;
+            if (!group_total(g, rr)) return;
             ++it;
             double r2new = rr[0];
             const double rn = sqrt(r2new);
@@ -263,23 +304,28 @@ __global__ void __launch_bounds__(256, 1) cg_persistent_kernel(const PSolve *__r
                 }
                 if (!group_sync(g)) return;
                 if (!group_mdagm<PREC_F64>(g, S->hd, S->mass, S->x, S->ax, S->to64, S->te64)) return;
-                double t2[1] = {0.0};
-                for (int i = i0; i < vh; i += stride) {
-                    double bv[24], av[24];
-                    fb.load(i, bv);
-                    fax.load(i, av);
-                    double s = 0.0;
-                    float f[24];
-                    for (int k = 0; k < 24; ++k) {
-                        bv[k] -= av[k];
-                        s = fma(bv[k], bv[k], s);
-                        f[k] = (float)bv[k];
+                double t2[1];
+                for (int c = g.gb; c < S->nchunk; c += g.G) {
+                    const int i = c * 256 + threadIdx.x;
+                    double v[1] = {0.0};
+                    if (i < vh) {
+                        double bv[24], av[24];
+                        fb.load(i, bv);
+                        fax.load(i, av);
+                        double s = 0.0;
+                        float f[24];
+                        for (int k = 0; k < 24; ++k) {
+                            bv[k] -= av[k];
+                            s = fma(bv[k], bv[k], s);
+                            f[k] = (float)bv[k];
+                        }
+                        fr.store(i, bv);
+                        frs.store(i, f);
+                        v[0] = s;
                     }
-                    fr.store(i, bv);
-                    frs.store(i, f);
-                    t2[0] += s;
+                    chunk_put(g, c, v);
                 }
-                if (!group_sum(g, t2)) return;
+                if (!group_total(g, t2)) return;
                 ++nupd;
                 r2t = t2[0];
                 if (r2t <= stop2) { converged = true; break; }
@@ -391,7 +437,7 @@ int run_persistent(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stat
             off[k] = bytes;
             bytes += 4 * ((size_t)vh * 192 + 256) + 5 * (half_field_bytes(vh, inner) + 256) + ((size_t)vh * 96 + 256) +
                      256 + 4096 +
-                     (size_t)nb[k] * 32 + 256;
+                     (size_t)((vh + 255) / 256) * 8 * 2 * 2 * sizeof(double) + 256;
         }
         DevBuf work, meta;
         if (cudaMalloc(&work.p, bytes) != cudaSuccess) {
@@ -430,7 +476,8 @@ int run_persistent(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stat
             P.bar = (unsigned *)take(256);
             P.out_int = (int *)take(64);
             P.out_rel = (double *)take(64);
-            P.part = (double *)take((size_t)nb[k] * 32);
+            P.nchunk = (vh + 255) / 256;
+            P.part = (double *)take((size_t)P.nchunk * 8 * 2 * 2 * sizeof(double));
             P.mass = dk.mass;
             P.tol = dk.tol;
             P.delta = dk.opts.delta;

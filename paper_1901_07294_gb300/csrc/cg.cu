@@ -91,7 +91,7 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
     WD_CUDA_TRY(cudaMemcpyAsync(ps, rs, hs, cudaMemcpyDeviceToDevice, s));
     WD_CUDA_TRY(cudaMemsetAsync(xs, 0, hx, s));
 
-    const double stop2 = tol * tol * b2;
+    const double stop2 = SOLVE_TARGET * SOLVE_TARGET * tol * tol * b2;
     // plain FP64 CG: the iterated residual is already FP64, so the true
     // residual is recomputed only to confirm convergence
     const bool reliable = PS == PREC_F64 ? true : o.reliable != 0;

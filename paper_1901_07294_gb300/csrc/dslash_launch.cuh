@@ -2,7 +2,6 @@
 // variant) to the single-field kernel or the multi right-hand-side kernel.
 #pragma once
 
-#include "dslash_bulk.cuh"
 #include "dslash_impl.cuh"
 #include "dslash_mrhs.cuh"
 #include "dslash_variants.cuh"
@@ -14,7 +13,7 @@ constexpr int HOP_MRHS_VARIANT = 3;   // variant index of the shared-link multi-
 constexpr int HOP_OCC_VARIANT = 4;    // schedule 1 compiled for 3 blocks of 256 threads per SM
 constexpr int HOP_TILE_VARIANT = 8;   // schedule 1 with the neighbour window staged in shared memory
 constexpr int HOP_2SITE_VARIANT = 9;  // schedule 1 with two sites per thread
-constexpr int HOP_BULK_VARIANT = 10;  // schedule 1 with the block's contiguous data staged by bulk copies
+constexpr int HOP_RETIRED_VARIANT = 10;  // unused (a bulk-copy staged kernel, measured slower and removed): schedule 1
 constexpr int HOP_NA0_VARIANT = 11;   // schedule 0 with the links loaded without L1 allocation
 constexpr int HOP_NA1_VARIANT = 12;   // schedule 1 with the links loaded without L1 allocation
 constexpr int HOP_MAX_VARIANT = 12;   // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
@@ -30,7 +29,7 @@ __host__ __device__ constexpr int hop_mrhs_strip(int v)
 // (pf = HOP_MRHS_VARIANT and 5..7: the shared-link multi-RHS kernel, threads/32
 // fields at a time, in the site order hop_mrhs_strip(pf) names;
 // HOP_TILE_VARIANT and HOP_2SITE_VARIANT: the kernels of dslash_variants.cuh;
-// HOP_BULK_VARIANT: the kernel of dslash_bulk.cuh; HOP_NA0_VARIANT and
+// HOP_NA0_VARIANT and
 // HOP_NA1_VARIANT: schedules 0 and 1 with the links loaded without L1
 // allocation, for even-odd hops, which read every link exactly once).
 template <int P>
@@ -67,21 +66,7 @@ cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int th
         }
     }
     cudaError_t e = cudaSuccess;
-    if (pf == HOP_BULK_VARIANT) {
-        bool ok = false;
-        switch (key) {
-        case 0: ok = launch_hop_bulk<P, 18, false, false>(B, grid, threads, s, e); break;
-        case 1: ok = launch_hop_bulk<P, 18, false, true>(B, grid, threads, s, e); break;
-        case 2: ok = launch_hop_bulk<P, 18, true, false>(B, grid, threads, s, e); break;
-        case 3: ok = launch_hop_bulk<P, 18, true, true>(B, grid, threads, s, e); break;
-        case 4: ok = launch_hop_bulk<P, 12, false, false>(B, grid, threads, s, e); break;
-        case 5: ok = launch_hop_bulk<P, 12, false, true>(B, grid, threads, s, e); break;
-        case 6: ok = launch_hop_bulk<P, 12, true, false>(B, grid, threads, s, e); break;
-        case 7: ok = launch_hop_bulk<P, 12, true, true>(B, grid, threads, s, e); break;
-        }
-        if (ok) return e;
-        pf = 1;   // a block would straddle a t-slice, an address is misaligned, or an open-boundary pass
-    }
+    if (pf == HOP_RETIRED_VARIANT) pf = 1;
     if (pf == HOP_TILE_VARIANT) {
         bool ok = false;
         if (!A.topen) {

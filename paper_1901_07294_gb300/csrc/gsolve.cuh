@@ -252,7 +252,7 @@ inline int gs_setup(const wd_ctx *ctx, GSolve &q)
 inline void gs_start(GSolve &q)
 {
     q.b2 = q.h[0];
-    q.stop2 = q.tol * q.tol * q.b2;
+    q.stop2 = SOLVE_TARGET * SOLVE_TARGET * q.tol * q.tol * q.b2;
     q.maxr = std::sqrt(q.b2);
     if (!(q.b2 > 0.0)) {
         q.active = false;

@@ -102,7 +102,7 @@ int bicg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b
     };
     WD_TRY(restart());
 
-    const double stop2 = tol * tol * b2;
+    const double stop2 = SOLVE_TARGET * SOLVE_TARGET * tol * tol * b2;
     const bool reliable = PS == PREC_F64 ? true : o.reliable != 0;
     const double delta = PS == PREC_F64 ? 0.0 : o.delta;
     double maxr = std::sqrt(b2), r2_restart = b2, r2_true = b2;
@@ -230,7 +230,7 @@ int cgne_schur(wd_ctx *ctx, const wd_gauge *g, double mass, char *x_e, const cha
     WD_CUDA_TRY(cudaMemsetAsync(x_e, 0, h64, s));
     WD_CUDA_TRY(cudaMemcpyAsync(rh, bh, h64, cudaMemcpyDeviceToDevice, s));
     double r2 = bh2, tol_ne = tol;
-    const double target2 = tol * tol * bh2;
+    const double target2 = SOLVE_TARGET * SOLVE_TARGET * tol * tol * bh2;
     st.iters = 0;
     st.reliable_updates = 0;
     for (int pass = 0; pass < 8; ++pass) {

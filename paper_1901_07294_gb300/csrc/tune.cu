@@ -46,7 +46,8 @@ void load_tune_file(wd_ctx *ctx)
         std::string key;
         std::getline(ss, key);
         if (!key.empty() && key[0] == ' ') key.erase(0, 1);
-        if (threads >= 32 && threads <= 256 && !(threads & 31) && variant >= 0 && variant <= HOP_MAX_VARIANT)
+        if (threads >= 32 && threads <= 256 && !(threads & 31) && variant >= 0 && variant <= HOP_MAX_VARIANT &&
+            variant != HOP_RETIRED_VARIANT)
             ctx->tuned[key] = {threads, variant};
     }
 }
@@ -114,6 +115,7 @@ int wd_tune_dslash(wd_ctx *ctx, const wd_gauge *g, int prec, int recon, int full
             const int zs = hop_mrhs_strip(v);
             if (zs >= 0 && nrhs == 1) continue;
             if (zs > 0 && zs >= A.L[2]) continue;   // same as natural order
+            if (v == HOP_RETIRED_VARIANT) continue;
             for (int w = 0; w < 2 && rc == WD_OK; ++w) rc = hop_launch_cfg(A, prec, recon, 0, nrhs, th, v, s);
             const int reps = 10;
             cudaEventRecord(e0, s);
@@ -160,7 +162,8 @@ int wd_tune_set_dslash(wd_ctx *ctx, const wd_gauge *g, int prec, int recon, int 
 {
     clear_error();
     if (!ctx || !g) return set_error(WD_EINVAL, "NULL argument");
-    if (threads < 32 || threads > 256 || (threads & 31) || variant < 0 || variant > HOP_MAX_VARIANT)
+    if (threads < 32 || threads > 256 || (threads & 31) || variant < 0 || variant > HOP_MAX_VARIANT ||
+        variant == HOP_RETIRED_VARIANT)
         return set_error(WD_EINVAL, "bad hop launch configuration (%d threads, variant %d)", threads, variant);
     HopArgs A{};
     WD_TRY(hop_setup(g, prec, recon, A));

@@ -32,6 +32,15 @@ void clear_error();
         if (s_ != WD_OK) return s_; \
     } while (0)
 
+// The solvers stop when their own FP64 true residual |b - A x| / |b| is at most
+// SOLVE_TARGET * tol.  Another FP64 evaluation of the same residual (other
+// summation order, no FMA) differs from the solver's by the rounding of the
+// products in A x, of order u |A| |x| (u = 2^-53, |A| <= 25 for these
+// operators).  The 10 % margin covers that whenever u |A| |x| / |b| is well
+// below 0.1 tol, so a solve reported converged also meets tol under such a
+// re-evaluation.
+constexpr double SOLVE_TARGET = 0.9;
+
 struct Geometry {
     int L[4];
     int64_t V;

@@ -1,9 +1,10 @@
 """Batched solves of uneven volumes: sequential, CUDA-graph and persistent-kernel modes.
 
 Each solve is judged by its true residual computed with the oracle operator on
-the GPU solution, and every solve's result in the mix must agree with the same
-solve run alone (within the solver tolerance: solutions agree to about
-cond(A) * tol).
+the GPU solution, and every solve's result in the mix must equal, bit for bit,
+the same solve run alone: a solve's kernels and reductions do not depend on
+the other solves of the batch (the persistent kernel's reductions use fixed
+256-site chunks, whatever group of blocks a solve gets).
 """
 import numpy as np
 import pytest
@@ -54,16 +55,17 @@ def test_batch_converges_and_matches_alone(mode):
         assert st["status"] == 0, (k, st)
         assert st["true_rel_resid"] <= 1e-10, (k, st)
         rel, x = _true_rel(ctx, host[k], probs[k]["x"])
-        assert rel <= 1.05e-10, (k, rel)
+        assert rel <= 1e-10, (k, rel)
         xs_mix.append(x)
-    # the same solve alone (a batch of one) gives the same solution within tolerance
-    for k in (0, 4):
+    # every solve alone (a batch of one) gives the same bits
+    for k in range(len(probs)):
         one = [dict(probs[k])]
         one[0]["x"] = wd.alloc_field(host[k][0], wd.SITES_EVEN, wd.F64)
         st = wd.cg_solve_batch(ctx, one, mode=mode)[0]
         assert st["status"] == 0
+        assert st["iters"] == stats[k]["iters"], (k, st, stats[k])
         _, x_alone = _true_rel(ctx, host[k], one[0]["x"])
-        assert rel_max_err(xs_mix[k], x_alone) < 1e-7
+        assert np.array_equal(xs_mix[k], x_alone), (k, rel_max_err(xs_mix[k], x_alone))
 
 
 @pytest.mark.parametrize("mode,prec", [(wd.BATCH_GRAPH, wd.F16), (wd.BATCH_PERSISTENT, wd.F16),
@@ -78,7 +80,7 @@ def test_batch_16bit_inner(mode, prec):
     stats = wd.cg_solve_batch(ctx, probs, mode=mode)
     for k, st in enumerate(stats):
         assert st["status"] == 0 and st["true_rel_resid"] <= 1e-10
-        assert _true_rel(ctx, host[k], probs[k]["x"])[0] <= 1.05e-10
+        assert _true_rel(ctx, host[k], probs[k]["x"])[0] <= 1e-10
 
 
 def test_persistent_rejects_unsupported_options():
@@ -110,4 +112,4 @@ def test_persistent_barrier_timeout_reports_etimeout(monkeypatch):
     monkeypatch.delenv("WD_FAULT")
     stats = wd.cg_solve_batch(ctx, probs, mode=wd.BATCH_PERSISTENT)
     assert all(s["status"] == 0 for s in stats)
-    assert _true_rel(ctx, host[0], probs[0]["x"])[0] <= 1.05e-10
+    assert _true_rel(ctx, host[0], probs[0]["x"])[0] <= 1e-10

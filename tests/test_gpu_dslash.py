@@ -254,7 +254,7 @@ def test_argument_errors(ctx):
 
 
 @pytest.mark.parametrize("prec", ALL_PREC)
-@pytest.mark.parametrize("variant", [0, 1, 2, 8, 9, 10, 11, 12])
+@pytest.mark.parametrize("variant", [0, 1, 2, 8, 9, 11, 12])
 @pytest.mark.parametrize("threads", [64, 192, 256])
 def test_every_launch_variant_matches_oracle(prec, variant, threads):
     """Each memory schedule and block size the autotuner may pick computes the same operator."""
@@ -287,12 +287,14 @@ def test_autotuner_table_and_choice():
     U, _ = _inputs(dims)
     g = wd.Gauge(ctx, dims, U)
     table = wd.tune_dslash(ctx, g, wd.F32, 18, full=True)
-    # 4 block sizes x 9 single-field variants: schedules 0, 1, 2, the high-occupancy build 4,
-    # the shared-memory neighbour window 8, two sites per thread 9, the bulk-copy staging 10
-    # and schedules 0 and 1 with links loaded without L1 allocation (11, 12)
-    assert len(table) == 36
-    assert {t["variant"] for t in table} == {0, 1, 2, 4, 8, 9, 10, 11, 12}
+    # 4 block sizes x 8 single-field variants: schedules 0, 1, 2, the high-occupancy build 4,
+    # the shared-memory neighbour window 8, two sites per thread 9 and schedules 0 and 1 with
+    # links loaded without L1 allocation (11, 12); 10 is retired
+    assert len(table) == 32
+    assert {t["variant"] for t in table} == {0, 1, 2, 4, 8, 9, 11, 12}
     assert all(t["ms"] > 0 for t in table)
+    with pytest.raises(wd.WdError):
+        wd.tune_set_dslash(ctx, g, wd.F32, 18, True, True, 1, 64, 10)
 
 
 @pytest.mark.parametrize("prec", ALL_PREC)

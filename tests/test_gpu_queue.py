@@ -64,14 +64,15 @@ def test_queue_results_and_same_alone_as_in_mix():
     for (p, host), r in zip(reqs, res):
         assert r["status"] == 0, r
         rel, x = _true_rel(ctx, host, p["x"])
-        assert rel <= 1.05 * p["tol"], (rel, p["tol"])
+        assert rel <= p["tol"], (rel, p["tol"])
         assert r["t_submit"] <= r["t_admit"] <= r["t_start"] <= r["t_finish"]
         mixed_x.append(x)
     st = q.stats()
     assert st["completed"] == 12 and st["mean_running"] > 1.0
     q.close()
-    # each request alone in a fresh queue gives the same solution
-    for k in (0, 5, 9):
+    # every request alone in a fresh one-slot queue gives the same bits: a request's
+    # kernels and reductions do not depend on what else the queue runs
+    for k in range(len(reqs)):
         p, host = reqs[k]
         alone = dict(p)
         alone["x"] = wd.alloc_field(host[0], wd.SITES_EVEN, wd.F64)
@@ -79,8 +80,9 @@ def test_queue_results_and_same_alone_as_in_mix():
         r = q1.wait(q1.submit(alone), timeout_ms=60000)
         q1.close()
         assert r["status"] == 0
+        assert r["cg_iters"] == res[k]["cg_iters"], (k, r, res[k])
         _, xa = _true_rel(ctx, host, alone["x"])
-        assert rel_max_err(mixed_x[k], xa) < max(1e-7, 1e3 * p["tol"])
+        assert np.array_equal(mixed_x[k], xa), (k, rel_max_err(mixed_x[k], xa))
 
 
 def test_requests_join_while_others_run():
@@ -165,7 +167,7 @@ def test_injected_allocation_failure(monkeypatch):
     res = [q.wait(t, timeout_ms=60000) for t in ts]
     q.close()
     assert [r["status"] for r in res] == [0, wd.WD_ENOMEM, 0, 0]
-    assert _true_rel(ctx, reqs[2][1], reqs[2][0]["x"])[0] <= 1.05e-10
+    assert _true_rel(ctx, reqs[2][1], reqs[2][0]["x"])[0] <= 1e-10
 
 
 @pytest.mark.parametrize("prec", [wd.F16, wd.BF16])
@@ -185,4 +187,4 @@ def test_hard_solves_with_small_delta(prec):
     q.close()
     for (p, host), r in zip(reqs, res):
         assert r["status"] == 0, r
-        assert _true_rel(ctx, host, p["x"])[0] <= 1.05e-12
+        assert _true_rel(ctx, host, p["x"])[0] <= 1e-12
