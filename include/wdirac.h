@@ -218,7 +218,10 @@ int wd_device_status(wd_ctx *ctx, int *code);
  * neighbour spinors staged in shared memory (tiling on), 9: as 1 with two
  * sites per thread; 11, 12: schedules 0 and 1 with the links loaded
  * without L1 allocation, which suits even-odd hops, where each link is read
- * once per call).
+ * once per call; 13, 14 (FP16 and BF16 fields only): schedules 1 and 0 (the
+ * latter with links loaded without L1 allocation) with the two spin
+ * components of each projected half spinor carried as a pair through
+ * Blackwell's paired FP32 instructions; variant 10 is retired and refused).
  * wd_tune_dslash times every candidate for one problem shape (full = 1: the
  * dslash_apply shape; full = 0: dslash_eo_apply with (with_x = 1) or without
  * the x term) on private scratch fields (allocated and freed by the call),

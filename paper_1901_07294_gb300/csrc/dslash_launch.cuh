@@ -4,6 +4,7 @@
 
 #include "dslash_impl.cuh"
 #include "dslash_mrhs.cuh"
+#include "dslash_pair.cuh"
 #include "dslash_variants.cuh"
 
 namespace wd {
@@ -16,7 +17,9 @@ constexpr int HOP_2SITE_VARIANT = 9;  // schedule 1 with two sites per thread
 constexpr int HOP_RETIRED_VARIANT = 10;  // unused (a bulk-copy staged kernel, measured slower and removed): schedule 1
 constexpr int HOP_NA0_VARIANT = 11;   // schedule 0 with the links loaded without L1 allocation
 constexpr int HOP_NA1_VARIANT = 12;   // schedule 1 with the links loaded without L1 allocation
-constexpr int HOP_MAX_VARIANT = 12;   // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
+constexpr int HOP_SP1_VARIANT = 13;   // 16-bit formats: schedule 1 with spin-paired FP32 arithmetic
+constexpr int HOP_SP0_VARIANT = 14;   // 16-bit formats: schedule 0, spin-paired, links without L1 allocation
+constexpr int HOP_MAX_VARIANT = 14;   // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
 
 // Multi-RHS variants and their z-strip width (0: natural order); -1 if v is not one.
 __host__ __device__ constexpr int hop_mrhs_strip(int v)
@@ -29,9 +32,11 @@ __host__ __device__ constexpr int hop_mrhs_strip(int v)
 // (pf = HOP_MRHS_VARIANT and 5..7: the shared-link multi-RHS kernel, threads/32
 // fields at a time, in the site order hop_mrhs_strip(pf) names;
 // HOP_TILE_VARIANT and HOP_2SITE_VARIANT: the kernels of dslash_variants.cuh;
-// HOP_NA0_VARIANT and
-// HOP_NA1_VARIANT: schedules 0 and 1 with the links loaded without L1
-// allocation, for even-odd hops, which read every link exactly once).
+// HOP_NA0_VARIANT and HOP_NA1_VARIANT: schedules 0 and 1 with the links
+// loaded without L1 allocation, for even-odd hops, which read every link
+// exactly once; HOP_SP1_VARIANT and HOP_SP0_VARIANT: the spin-paired kernel
+// of dslash_pair.cuh for FP16 and BF16 storage, schedules 1 and 0 for FP32,
+// FP64 and open-boundary passes).
 template <int P>
 cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int threads, int pf, cudaStream_t s)
 {
@@ -65,6 +70,23 @@ cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int th
         default: return launch_hop_2site<P, 12, true, true>(B, nrhs, threads, s);
         }
     }
+    if constexpr (Prec<P>::scaled) {
+        if ((pf == HOP_SP1_VARIANT || pf == HOP_SP0_VARIANT) && !A.topen) {
+            const int spf = pf == HOP_SP1_VARIANT ? 1 : 0;
+            switch (key) {
+            case 0: return launch_hop_sp<P, 18, false, false>(B, grid, threads, spf, s);
+            case 1: return launch_hop_sp<P, 18, false, true>(B, grid, threads, spf, s);
+            case 2: return launch_hop_sp<P, 18, true, false>(B, grid, threads, spf, s);
+            case 3: return launch_hop_sp<P, 18, true, true>(B, grid, threads, spf, s);
+            case 4: return launch_hop_sp<P, 12, false, false>(B, grid, threads, spf, s);
+            case 5: return launch_hop_sp<P, 12, false, true>(B, grid, threads, spf, s);
+            case 6: return launch_hop_sp<P, 12, true, false>(B, grid, threads, spf, s);
+            default: return launch_hop_sp<P, 12, true, true>(B, grid, threads, spf, s);
+            }
+        }
+    }
+    if (pf == HOP_SP1_VARIANT) pf = 1;   // FP32, FP64, or an open-boundary pass
+    if (pf == HOP_SP0_VARIANT) pf = 0;
     cudaError_t e = cudaSuccess;
     if (pf == HOP_RETIRED_VARIANT) pf = 1;
     if (pf == HOP_TILE_VARIANT) {
