@@ -311,6 +311,44 @@ int wd_dd_dslash(wd_dd *dd, void *const *out, const void *const *in, double mass
                  int halo_prec, void *stream);
 int wd_dd_destroy(wd_dd *dd);
 
+/* ---- One slab per process (Sec. II-A: one sub-lattice per process) ---------
+ * The decomposition of wd_dd with each slab in its own process (on its own
+ * GPU): the process creates the wd_slab for its slab index k of nsub, from
+ * its own slice of the canonical links (local dims = global dims with
+ * L_t / nsub, the k-th contiguous slice of the global array; host or device
+ * memory as links_on_host says; the slab keeps its own copy).  One
+ * application of D to the global lattice is then, in every process:
+ *   wd_slab_gather(in -> send_fwd, send_bwd)   faces into caller-owned device
+ *       buffers of wd_slab_face_bytes bytes each: send_fwd (the sites at local
+ *       t = 0, (1 - gamma_t) projected) goes to slab k-1, send_bwd (the sites
+ *       at local t = T-1, U_t^dagger (1 + gamma_t) projected, times this
+ *       slab's own link) goes to slab k+1 (indices mod nsub);
+ *   the transport (e.g. NCCL send/recv) delivers them into the neighbours'
+ *       own buffers: recv_fwd from slab k+1, recv_bwd from slab k-1;
+ *   wd_slab_interior(out = D_local in with the t boundary open), which may
+ *       run while the faces are in flight;
+ *   wd_slab_boundary(out += the halo terms from recv_fwd, recv_bwd), after
+ *       both.
+ * Halos as for wd_dd_dslash (WD_F64, WD_F32, WD_F16 with a per-site scale);
+ * the face format is private to the library, so both ends must use the same
+ * halo_prec.  Antiperiodic t (wd_slab_set_boundary(-1)): the faces that cross
+ * the global boundary change sign (slab 0's forward face, slab nsub-1's
+ * backward face).  Fields are local full fields (wd_pack with the local
+ * dims); every pointer 16-byte aligned; asynchronous on `stream`. */
+typedef struct wd_slab wd_slab;
+
+int wd_slab_create(wd_ctx *ctx, const int dims[4], int nsub, int k, const double *links, int links_on_host,
+                   wd_slab **out);
+int wd_slab_local_dims(const wd_slab *sl, int dims_out[4]);
+int wd_slab_set_boundary(wd_slab *sl, int t_sign);
+int wd_slab_face_bytes(const wd_slab *sl, int halo_prec, size_t *out);
+int wd_slab_gather(wd_slab *sl, const void *in, int prec, int recon, int halo_prec, void *send_fwd, void *send_bwd,
+                   void *stream);
+int wd_slab_interior(wd_slab *sl, void *out, const void *in, double mass, int prec, int recon, void *stream);
+int wd_slab_boundary(wd_slab *sl, void *out, const void *recv_fwd, const void *recv_bwd, int prec, int recon,
+                     int halo_prec, void *stream);
+int wd_slab_destroy(wd_slab *sl);
+
 /* ---- Element-wise products (Sec. IV examples; Sec. III-D complex forms) ----
  * z_i = f(x_i, y_i[, z_i]) for i < n on device arrays of FP64:
  *   WD_STREAM_REAL_MUL        z = x y        n reals (Sec. IV, real arithmetic)

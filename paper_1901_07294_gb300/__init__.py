@@ -60,6 +60,14 @@ _SIGS = {
     "wd_dd_halo_bytes": (_ip, [_vp, _ip, ctypes.POINTER(_sz)]),
     "wd_dd_dslash": (_ip, [_vp, _vp, _vp, _dp, _ip, _ip, _ip, _vp]),
     "wd_dd_destroy": (_ip, [_vp]),
+    "wd_slab_create": (_ip, [_vp, _DIMS, _ip, _ip, _vp, _ip, ctypes.POINTER(_vp)]),
+    "wd_slab_local_dims": (_ip, [_vp, _DIMS]),
+    "wd_slab_set_boundary": (_ip, [_vp, _ip]),
+    "wd_slab_face_bytes": (_ip, [_vp, _ip, ctypes.POINTER(_sz)]),
+    "wd_slab_gather": (_ip, [_vp, _vp, _ip, _ip, _ip, _vp, _vp, _vp]),
+    "wd_slab_interior": (_ip, [_vp, _vp, _vp, _dp, _ip, _ip, _vp]),
+    "wd_slab_boundary": (_ip, [_vp, _vp, _vp, _vp, _ip, _ip, _ip, _vp]),
+    "wd_slab_destroy": (_ip, [_vp]),
     "wd_gauge_set_boundary": (_ip, [_vp, _ip]),
     "wd_gauge_bytes": (_ip, [_vp, _ip, _ip, ctypes.POINTER(_sz)]),
     "wd_gauge_destroy": (_ip, [_vp]),
@@ -419,6 +427,64 @@ class DomainDecomposition:
     def close(self):
         if self._h:
             load().wd_dd_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Slab:
+    """One process's slab k of the lattice `dims` split along t into `nsub` slabs (wd_slab):
+    the face gather, interior pass and boundary pass of one operator application, with the
+    faces exchanged by the caller (see ddrank.SlabOperator)."""
+
+    def __init__(self, ctx: Context, dims, nsub: int, k: int, links):
+        import numpy as np
+        self.ctx = ctx
+        self.dims = tuple(int(d) for d in dims)
+        self.nsub, self.k = int(nsub), int(k)
+        self._h = _vp()
+        if hasattr(links, "data_ptr"):
+            if not links.is_cuda or not links.is_contiguous():
+                raise ValueError("torch links must be a contiguous CUDA tensor (or pass a numpy array)")
+            ptr, on_host = links.data_ptr(), 0
+        else:
+            arr = np.ascontiguousarray(links, dtype=np.complex128)
+            ptr, on_host = arr.ctypes.data, 1
+        _check(load().wd_slab_create(ctx.handle, _dims(self.dims), self.nsub, self.k, ptr, on_host,
+                                     ctypes.byref(self._h)))
+
+    def local_dims(self) -> tuple:
+        d = _DIMS()
+        _check(load().wd_slab_local_dims(self._h, d))
+        return tuple(d)
+
+    def set_boundary(self, t_sign: int) -> None:
+        _check(load().wd_slab_set_boundary(self._h, int(t_sign)))
+
+    def face_bytes(self, halo_prec: int) -> int:
+        out = _sz()
+        _check(load().wd_slab_face_bytes(self._h, int(halo_prec), ctypes.byref(out)))
+        return int(out.value)
+
+    def gather(self, inp, send_fwd, send_bwd, prec: int, recon: int, halo_prec: int, stream=None) -> None:
+        _check(load().wd_slab_gather(self._h, _ptr(inp), int(prec), int(recon), int(halo_prec), _ptr(send_fwd),
+                                     _ptr(send_bwd), _stream(stream)))
+
+    def interior(self, out, inp, mass: float, prec: int, recon: int, stream=None) -> None:
+        _check(load().wd_slab_interior(self._h, _ptr(out), _ptr(inp), float(mass), int(prec), int(recon),
+                                       _stream(stream)))
+
+    def boundary(self, out, recv_fwd, recv_bwd, prec: int, recon: int, halo_prec: int, stream=None) -> None:
+        _check(load().wd_slab_boundary(self._h, _ptr(out), _ptr(recv_fwd), _ptr(recv_bwd), int(prec), int(recon),
+                                       int(halo_prec), _stream(stream)))
+
+    def close(self):
+        if self._h:
+            load().wd_slab_destroy(self._h)
             self._h = _vp()
 
     def __del__(self):

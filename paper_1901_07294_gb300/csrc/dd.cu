@@ -507,3 +507,196 @@ int wd_dd_dslash(wd_dd *d, void *const *out, const void *const *in, double mass,
 }
 
 } // extern "C"
+
+// ---- one slab per process --------------------------------------------------
+// The same three steps for a lattice whose slabs live in different processes
+// (Sec. II-A: one sub-lattice per process): each process holds one wd_slab
+// and its own fields, gathers its two faces into buffers it owns, sends them
+// to its neighbours by whatever transport it uses (NCCL send/recv into the
+// receiver's own buffers), runs the interior pass meanwhile and adds the
+// received halos in the boundary pass.
+struct wd_slab {
+    wd_ctx *ctx = nullptr;
+    int device = 0;
+    int nsub = 0, k = 0;
+    int Ll[4] = {0, 0, 0, 0};
+    int nf = 0, vh = 0;
+    int t_sign = 1;
+    wd_gauge *g = nullptr;
+};
+
+namespace {
+
+int slab_face_args(const wd_slab *sl, const void *field, void *out, int prec, int recon, int halo_prec, FaceArgs &f,
+                   HopArgs &A)
+{
+    A = HopArgs{};
+    WD_TRY(hop_setup(sl->g, prec, recon, A));
+    f = FaceArgs{};
+    f.field = (const char *)field;
+    f.out = (char *)out;
+    f.half_bytes = half_field_bytes(sl->vh, prec);
+    f.gauge[0] = A.gauge[0];
+    f.gauge[1] = A.gauge[1];
+    f.link_blk = A.link_blk;
+    f.face_bytes = face_bytes(halo_prec, sl->nf);
+    f.vh = sl->vh;
+    f.nf = sl->nf;
+    f.lt = sl->Ll[3];
+    f.b = -0.5;
+    return WD_OK;
+}
+
+int slab_check(const wd_slab *sl, int prec, int recon, int halo_prec)
+{
+    if (!sl) return set_error(WD_EINVAL, "NULL slab");
+    if (!valid_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
+    if (!valid_recon(recon)) return set_error(WD_EINVAL, "bad reconstruction %d", recon);
+    if (halo_prec != WD_F64 && halo_prec != WD_F32 && halo_prec != WD_F16)
+        return set_error(WD_EINVAL, "halo precision must be WD_F64, WD_F32 or WD_F16");
+    return WD_OK;
+}
+
+bool misaligned(const void *p) { return ((uintptr_t)p & 15u) != 0; }
+
+} // namespace
+
+extern "C" {
+
+int wd_slab_create(wd_ctx *ctx, const int dims[4], int nsub, int k, const double *links, int links_on_host,
+                   wd_slab **out)
+{
+    clear_error();
+    if (!ctx || !dims || !links || !out) return set_error(WD_EINVAL, "NULL argument");
+    *out = nullptr;
+    Geometry geo;
+    WD_TRY(make_geometry(dims, geo));
+    if (nsub < 1 || dims[3] % nsub != 0)
+        return set_error(WD_EINVAL, "nsub = %d must divide L_t = %d", nsub, dims[3]);
+    if (k < 0 || k >= nsub) return set_error(WD_EINVAL, "slab index %d out of range [0, %d)", k, nsub);
+    const int lt = dims[3] / nsub;
+    if (lt < 2 || (lt & 1)) return set_error(WD_EINVAL, "local L_t = %d must be even and >= 2", lt);
+    DeviceGuard dg(ctx->device);
+    wd_slab *sl = new (std::nothrow) wd_slab();
+    if (!sl) return set_error(WD_ENOMEM, "host allocation failed");
+    sl->ctx = ctx;
+    sl->device = ctx->device;
+    sl->nsub = nsub;
+    sl->k = k;
+    for (int mu = 0; mu < 4; ++mu) sl->Ll[mu] = dims[mu];
+    sl->Ll[3] = lt;
+    sl->nf = dims[0] * dims[1] * dims[2] / 2;
+    sl->vh = sl->nf * lt;
+    const int rc = wd_gauge_create(ctx, sl->Ll, links, links_on_host, &sl->g);
+    if (rc != WD_OK) {
+        delete sl;
+        return rc;
+    }
+    *out = sl;
+    return WD_OK;
+}
+
+int wd_slab_destroy(wd_slab *sl)
+{
+    clear_error();
+    if (!sl) return WD_OK;
+    {
+        DeviceGuard dg(sl->device);
+        if (sl->g) wd_gauge_destroy(sl->g);
+    }
+    delete sl;
+    return WD_OK;
+}
+
+int wd_slab_local_dims(const wd_slab *sl, int dims_out[4])
+{
+    clear_error();
+    if (!sl || !dims_out) return set_error(WD_EINVAL, "NULL argument");
+    for (int mu = 0; mu < 4; ++mu) dims_out[mu] = sl->Ll[mu];
+    return WD_OK;
+}
+
+int wd_slab_set_boundary(wd_slab *sl, int t_sign)
+{
+    clear_error();
+    if (!sl) return set_error(WD_EINVAL, "NULL argument");
+    if (t_sign != 1 && t_sign != -1) return set_error(WD_EINVAL, "t_sign = %d must be +1 or -1", t_sign);
+    sl->t_sign = t_sign;
+    return WD_OK;
+}
+
+int wd_slab_face_bytes(const wd_slab *sl, int halo_prec, size_t *out)
+{
+    clear_error();
+    if (!sl || !out) return set_error(WD_EINVAL, "NULL argument");
+    if (halo_prec != WD_F64 && halo_prec != WD_F32 && halo_prec != WD_F16)
+        return set_error(WD_EINVAL, "halo precision must be WD_F64, WD_F32 or WD_F16");
+    *out = 2 * face_bytes(halo_prec, sl->nf);
+    return WD_OK;
+}
+
+int wd_slab_gather(wd_slab *sl, const void *in, int prec, int recon, int halo_prec, void *send_fwd, void *send_bwd,
+                   void *stream)
+{
+    clear_error();
+    WD_TRY(slab_check(sl, prec, recon, halo_prec));
+    if (!in || !send_fwd || !send_bwd) return set_error(WD_EINVAL, "NULL argument");
+    if (misaligned(in) || misaligned(send_fwd) || misaligned(send_bwd))
+        return set_error(WD_EINVAL, "fields and face buffers must be 16-byte aligned");
+    DeviceGuard dg(sl->device);
+    FaceArgs f;
+    HopArgs A;
+    WD_TRY(slab_face_args(sl, in, nullptr, prec, recon, halo_prec, f, A));
+    f.buf[0] = (char *)send_fwd;
+    f.buf[1] = (char *)send_bwd;
+    f.neg_f = (sl->t_sign < 0 && sl->k == 0) ? 1 : 0;
+    f.neg_b = (sl->t_sign < 0 && sl->k == sl->nsub - 1) ? 1 : 0;
+    cudaError_t e = launch_face_kernels(true, prec, recon, halo_prec, f, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_error(WD_ECUDA, "face gather launch failed: %s", cudaGetErrorString(e));
+    return WD_OK;
+}
+
+int wd_slab_interior(wd_slab *sl, void *out, const void *in, double mass, int prec, int recon, void *stream)
+{
+    clear_error();
+    WD_TRY(slab_check(sl, prec, recon, WD_F64));
+    if (!in || !out) return set_error(WD_EINVAL, "NULL argument");
+    if (misaligned(in) || misaligned(out)) return set_error(WD_EINVAL, "fields must be 16-byte aligned");
+    if (in == out) return set_error(WD_EINVAL, "out must not alias in");
+    DeviceGuard dg(sl->device);
+    HopArgs A{};
+    WD_TRY(hop_setup(sl->g, prec, recon, A));
+    const size_t half = half_field_bytes(sl->vh, prec);
+    for (int p = 0; p < 2; ++p) {
+        A.in[p] = (const char *)in + (size_t)(1 - p) * half;
+        A.x[p] = (const char *)in + (size_t)p * half;
+        A.out[p] = (char *)out + (size_t)p * half;
+    }
+    A.rhs_stride = 2 * half;
+    A.nparity = 2;
+    A.topen = 1;
+    A.a = mass + 4.0;
+    A.b = -0.5;
+    return hop_launch(sl->ctx, A, prec, recon, 0, 1, (cudaStream_t)stream);
+}
+
+int wd_slab_boundary(wd_slab *sl, void *out, const void *recv_fwd, const void *recv_bwd, int prec, int recon,
+                     int halo_prec, void *stream)
+{
+    clear_error();
+    WD_TRY(slab_check(sl, prec, recon, halo_prec));
+    if (!out || !recv_fwd || !recv_bwd) return set_error(WD_EINVAL, "NULL argument");
+    if (misaligned(out) || misaligned(recv_fwd) || misaligned(recv_bwd))
+        return set_error(WD_EINVAL, "fields and face buffers must be 16-byte aligned");
+    DeviceGuard dg(sl->device);
+    FaceArgs f;
+    HopArgs A;
+    WD_TRY(slab_face_args(sl, nullptr, out, prec, recon, halo_prec, f, A));
+    f.buf[0] = (char *)recv_fwd;
+    f.buf[1] = (char *)recv_bwd;
+    cudaError_t e = launch_face_kernels(false, prec, recon, halo_prec, f, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_error(WD_ECUDA, "boundary pass launch failed: %s", cudaGetErrorString(e));
+    return WD_OK;
+}
+
+} // extern "C"
