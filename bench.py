@@ -540,7 +540,7 @@ def run_gpu(args):
     serving = None
     if not args.no_cg and not args.no_serving:
         _log("serving")
-        serving = _serving_section(wd, torch, ctx)
+        serving = _serving_section(wd, torch, ctx, peak)
     solve = None
     if not args.no_cg:
         _log("solve")
@@ -974,7 +974,7 @@ def _batch_section(wd, torch, ctx, peak):
     return out
 
 
-def _serving_section(wd, torch, ctx, n_main=2000, n_sweep=150, warm=100):
+def _serving_section(wd, torch, ctx, peak, n_main=2000, n_sweep=150, warm=100):
     """Serving: Poisson arrivals of CG solve requests (volumes uniform over 8^4, 16^4, 24^3x48,
     32^3x64; masses log-uniform in [0.02, 0.5]; tolerances in {1e-8, 1e-10, 1e-12}) on resident
     smoothed-SU(3) configurations, continuous batching with HBM admission.  Headline at 200 req/s
@@ -1015,7 +1015,7 @@ def _serving_section(wd, torch, ctx, n_main=2000, n_sweep=150, warm=100):
                 t, dims, x, tol = item
                 r = q.wait(t)
                 pools[dims].append(x)
-                results.append((tol, r))
+                results.append((tol, int(np.prod(dims)) // 2, r))
 
         wt = th.Thread(target=waiter)
         wt.start()
@@ -1038,20 +1038,28 @@ def _serving_section(wd, torch, ctx, n_main=2000, n_sweep=150, warm=100):
         return results, st
 
     def summarise(results, st, rate, skip):
-        tols = [t for t, _ in results][skip:]
-        res = [r for _, r in results][skip:]
+        tols = [t for t, _, _ in results][skip:]
+        vhs = [v for _, v, _ in results][skip:]
+        res = [r for _, _, r in results][skip:]
         lat = np.array([r["t_finish"] - r["t_submit"] for r in res])
         span = max(r["t_finish"] for r in res) - min(r["t_submit"] for r in res)
         ok = sum(1 for r in res if r["status"] == 0)
+        # iteration bytes as if every request moved its own links (the single-field model);
+        # the groups share link loads, so the bytes actually moved are fewer
+        it_bytes = sum(r["cg_iters"] * vh * _cg_iteration_bytes(wd.F16, 18) for vh, r in zip(vhs, res))
         return {"offered_per_s": rate, "requests": len(res), "converged": ok,
                 "achieved_per_s": round(len(res) / span, 2), "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 2),
                 "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 2), "mean_running": round(st["mean_running"], 2),
                 "admission_stalls": int(st["admission_stalls"]),
+                "group_launches": int(st["group_launches"]), "mean_group_size": round(st["mean_group_size"], 2),
+                "iterations": int(sum(r["cg_iters"] for r in res)), "reliable_updates": int(sum(r["cg_reliable_updates"] for r in res)),
+                "iter_model_gbs": round(it_bytes / span / 1e9, 1), "frac_hbm": round(it_bytes / span / 1e9 / peak, 4),
                 "max_true_resid_over_tol": round(max(r["cg_true_rel_resid"] / t for t, r in zip(tols, res)), 4)}
 
     out = {"volumes": [list(v) for v in vols], "inner": "fp16 storage, fp32 compute, fp64 reliable updates",
-           "queue": {"hbm_budget_gb": 48, "max_slots": 32, "max_iterations_per_launch": 32,
-                     "scheduling": "each request advanced when its own stream is idle"}}
+           "queue": {"hbm_budget_gb": 48, "max_slots": 32, "max_iterations_per_group_launch": 16,
+                     "scheduling": "requests grouped by gauge: one shared-link hop launch per hop for a "
+                                   "group's ready members; FP64 reliable updates on the members' own streams"}}
     results, st = run(200.0, n_main + warm, 5001)
     out["rate_200"] = summarise(results, st, 200.0, warm)
     out["sweep"] = []

@@ -489,13 +489,21 @@ int cg_solve_batch(wd_ctx *ctx, int n, const wd_solve_desc *descs, int mode, wd_
  * are the caller's device buffers and must stay valid until the request's
  * result has been taken.  The scheduler admits waiting requests while fewer
  * than max_slots run and their workspace fits hbm_budget_bytes (first come
- * first served, a request that fits may pass one that does not).  Each running
- * request has its own stream and a graph whose device-side loop runs CG
- * iterations until a reliable update is due (at most 32 per launch).  The
- * scheduler polls the streams and advances each idle request on its own:
- * it enqueues the FP64 reliable update, or relaunches the loop, or retires
- * the converged request.  No request waits for another, and requests join
- * and leave at any time.
+ * first served, a request that fits may pass one that does not).  Each
+ * admitted request has its own workspace and stream and joins the request
+ * group of its gauge, inner precision and inner link format (up to 32
+ * members; another group opens when one is full).  A group runs the
+ * low-precision CG iterations of its ready members together in a graph whose
+ * device-side loop launches each of the four even-odd hops once for all of
+ * them, with the links of each block's sites loaded once and applied to every
+ * member's field (each member with its own mass, tolerance and scalars), and
+ * stops when any member needs its FP64 reliable update or after 16
+ * iterations.  The scheduler then enqueues those updates on the members' own
+ * streams, relaunches the group with the others, and lets members join or
+ * rejoin (after their update) at the next launch.  A member's results do not
+ * depend on the other members: alone and in any mix it gets the same bits.
+ * Groups of different gauges and the updates run concurrently on their own
+ * streams.
  *   rq_submit: non-blocking, thread-safe; copies the descriptor; WD_ENOMEM if
  *              the request alone exceeds the budget.
  *   rq_poll:   WD_EBUSY while running; otherwise fills the result and forgets
@@ -516,10 +524,12 @@ typedef struct {
 } wd_solve_result;
 
 typedef struct {
-    uint64_t submitted, completed, admission_stalls, steps;   /* steps: device-loop launches */
+    uint64_t submitted, completed, admission_stalls, steps;   /* steps: group launches + reliable updates */
     double mean_running;     /* running requests, averaged over the time any request runs */
     int waiting, running;
     size_t hbm_in_use;
+    uint64_t group_launches; /* launches of group loops (each one shared by its members) */
+    double mean_group_size;  /* members per group launch, averaged over the launches */
 } rq_counters;
 
 /* Device workspace bytes one queued (or graph-batched) solve on this lattice

@@ -578,7 +578,7 @@ class RqCounters(ctypes.Structure):
     """rq_counters"""
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("admission_stalls", ctypes.c_uint64),
                 ("steps", ctypes.c_uint64), ("mean_running", _dp), ("waiting", _ip), ("running", _ip),
-                ("hbm_in_use", _sz)]
+                ("hbm_in_use", _sz), ("group_launches", ctypes.c_uint64), ("mean_group_size", _dp)]
 
 
 def _desc(p: dict) -> SolveDesc:

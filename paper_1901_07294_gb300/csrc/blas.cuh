@@ -41,8 +41,10 @@ template <int P> struct FieldRef {
     }
 };
 
-template <typename Op>
-__global__ void __launch_bounds__(BLAS_THREADS) blas_kernel(const Op op, const int nsite, const RedScratch rs)
+// The site loop and the deterministic reduction of one BLAS operation over a
+// grid of blocks along x (shared by blas_kernel and the per-member kernels of
+// a request group, which run one operation per blockIdx.y).
+template <typename Op> __device__ __forceinline__ void blas_body(const Op &op, const int nsite, const RedScratch &rs)
 {
     constexpr int NR = Op::NR;
     double acc[NR > 0 ? NR : 1];
@@ -100,6 +102,12 @@ __global__ void __launch_bounds__(BLAS_THREADS) blas_kernel(const Op op, const i
             }
         }
     }
+}
+
+template <typename Op>
+__global__ void __launch_bounds__(BLAS_THREADS) blas_kernel(const Op op, const int nsite, const RedScratch rs)
+{
+    blas_body(op, nsite, rs);
 }
 
 // ---- operations -----------------------------------------------------------

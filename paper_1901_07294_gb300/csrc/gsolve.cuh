@@ -31,11 +31,12 @@ constexpr int GS_LAUNCH_CAP = 32;   // iterations at most per graph launch
 // total, s[12] tol^2 |b|^2, s[13] delta, s[14] maxiter, s[15] GS_LAUNCH_CAP.
 constexpr int GS_NSCAL = 16;
 
-// The loop condition of the WHILE node, evaluated after each iteration.
-template <int UNUSED = 0>
-__global__ void gs_control_kernel(double *s, cudaGraphConditionalHandle cond)
+// One solve's bookkeeping after an iteration: max |r| since the last update,
+// the iteration counts, and whether its loop must stop (breakdown, a residual
+// that is not finite, an update due, convergence, maxiter, RELIABLE_MAX_GAP
+// iterations without an update, or the per-launch cap s[15]).
+__device__ __forceinline__ bool gs_member_step(double *s)
 {
-    if (threadIdx.x != 0) return;
     const double r2 = s[0];
     const double rn = sqrt(r2);
     double maxr = s[8];
@@ -46,9 +47,16 @@ __global__ void gs_control_kernel(double *s, cudaGraphConditionalHandle cond)
     s[10] = n_gap;
     s[11] = n_total;
     const bool finite = r2 == r2 && r2 < 1e300;
-    const bool stop = s[6] != 0.0 || !finite || rn < s[13] * maxr || r2 <= s[12] || n_total >= s[14] ||
-                      n_gap >= (double)RELIABLE_MAX_GAP || n_launch >= s[15];
-    cudaGraphSetConditional(cond, stop ? 0u : 1u);
+    return s[6] != 0.0 || !finite || rn < s[13] * maxr || r2 <= s[12] || n_total >= s[14] ||
+           n_gap >= (double)RELIABLE_MAX_GAP || n_launch >= s[15];
+}
+
+// The loop condition of the WHILE node, evaluated after each iteration.
+template <int UNUSED = 0>
+__global__ void gs_control_kernel(double *s, cudaGraphConditionalHandle cond)
+{
+    if (threadIdx.x != 0) return;
+    cudaGraphSetConditional(cond, gs_member_step(s) ? 0u : 1u);
 }
 
 struct GSolve {
@@ -137,7 +145,7 @@ template <int PS> int reliable_update(const wd_ctx *ctx, GSolve &q)
     return WD_OK;
 }
 
-template <int PS> int init(const wd_ctx *ctx, GSolve &q)
+template <int PS> int init(const wd_ctx *ctx, GSolve &q, bool with_graph)
 {
     const int vh = q.vh;
     auto F64 = [&](const void *p) { return field_ref<PREC_F64>(p, vh); };
@@ -151,6 +159,7 @@ template <int PS> int init(const wd_ctx *ctx, GSolve &q)
     static const double inf = INFINITY;   // s[4] = inf: the first direction update gives p = r
     WD_CUDA_TRY(cudaMemcpyAsync(q.scal + 4, &inf, sizeof(double), cudaMemcpyHostToDevice, q.s));
     WD_CUDA_TRY(cudaMemcpyAsync(q.h, q.scal, sizeof(double), cudaMemcpyDeviceToHost, q.s));
+    if (!with_graph) return WD_OK;
     // build the graph node by node (no stream capture): a WHILE node whose
     // body is one iteration and the control kernel
     cudaGraph_t graph;
@@ -213,9 +222,10 @@ inline int gs_alloc(GSolve &q)
 }
 
 // Lays the solve's fields out in its workspace (from gs_alloc, or reused from
-// an earlier solve with the same footprint), enqueues the initial state and
-// builds the graph.  Allocates no device memory.
-inline int gs_bind(const wd_ctx *ctx, GSolve &q)
+// an earlier solve with the same footprint), enqueues the initial state and,
+// with graph = true, builds the solve's own graph (a member of a request group
+// runs in its group's graph instead).  Allocates no device memory.
+inline int gs_bind(const wd_ctx *ctx, GSolve &q, bool graph = true)
 {
     q.vh = q.gauge->geo.Vh;
     q.prec = q.opts.inner_prec;
@@ -237,7 +247,7 @@ inline int gs_bind(const wd_ctx *ctx, GSolve &q)
     q.scal = (double *)take(256);
     q.red.ticket = (unsigned *)take(256);
     q.red.partials = (double *)take((size_t)MAX_RED_BLOCKS * MAX_NR * 8);
-    WD_GS_DISPATCH(q.prec, gs_detail::init<PS>(ctx, q));
+    WD_GS_DISPATCH(q.prec, gs_detail::init<PS>(ctx, q, graph));
 }
 
 // gs_alloc + gs_bind.
@@ -248,8 +258,10 @@ inline int gs_setup(const wd_ctx *ctx, GSolve &q)
 }
 
 // After gs_bind's work has finished: reads |b|^2, prepares the test and
-// enqueues the loop's constants (s[8..15]).
-inline void gs_start(GSolve &q)
+// enqueues the loop's constants (s[8..15]); launch_cap: iterations at most per
+// launch of the solve's own graph (a group member passes no limit: its group
+// counts the iterations of a launch).
+inline void gs_start(GSolve &q, double launch_cap = (double)GS_LAUNCH_CAP)
 {
     q.b2 = q.h[0];
     q.stop2 = SOLVE_TARGET * SOLVE_TARGET * q.tol * q.tol * q.b2;
@@ -266,7 +278,7 @@ inline void gs_start(GSolve &q)
     c[4] = q.stop2;
     c[5] = q.opts.delta;
     c[6] = (double)q.opts.maxiter;
-    c[7] = (double)GS_LAUNCH_CAP;
+    c[7] = launch_cap;
     if (cudaMemcpyAsync(q.scal + 8, c, 8 * sizeof(double), cudaMemcpyHostToDevice, q.s) != cudaSuccess ||
         cudaStreamSynchronize(q.s) != cudaSuccess) {
         cudaGetLastError();

@@ -4,15 +4,17 @@
 // host thread and run by one scheduler thread.  In each pass the scheduler
 // admits waiting requests while free slots and the HBM budget allow (first
 // come first served, but a request that fits may pass one that does not),
-// sets up the admitted ones (workspace, stream, a CUDA graph whose
-// device-side loop runs CG iterations until a reliable update is due) and
-// launches their loops, each on its own stream so that all running requests'
-// work overlaps on the GPU.  It then polls the running requests' streams and
-// advances only those that are idle: after a loop has stopped it enqueues the
-// FP64 reliable update (or relaunches the loop); after an update has finished
-// it tests convergence and relaunches or retires the request.  No request
-// waits for another's loop or update, so small and large volumes proceed at
-// their own pace and requests join and leave at any time.
+// sets up the admitted ones (workspace, stream, initial state) and puts each
+// into the request group of its gauge, inner precision and inner link format
+// (ggroup.cuh).  A group runs the low-precision iterations of all its ready
+// members together, one shared-link hop launch per hop for all of them, in a
+// device-side loop that stops when any member needs its FP64 reliable update.
+// The scheduler then enqueues those updates on the members' own streams, and
+// the group's next launch goes on with the others; a member rejoins when its
+// update has finished, and newly admitted requests join at the next launch.
+// Groups of different gauges run on their own streams, and updates overlap
+// the groups' iterations, so all work in flight shares the GPU.  No request
+// waits for another's update, and requests join and leave at any launch.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -24,20 +26,36 @@
 #include <unordered_map>
 #include <vector>
 
-#include "gsolve.cuh"
+#include "ggroup.cuh"
 
 namespace {
 
 using clk = std::chrono::steady_clock;
+
+// Scheduler-side state of an admitted request.
+enum ReqState { R_INIT, R_READY, R_ACTIVE, R_UPDATING };
 
 struct Req {
     uint64_t ticket = 0;
     wd_solve_desc d{};
     size_t foot = 0;
     bool cancel = false, done = false;
-    bool updating = false;   // its FP64 reliable update is in flight (scheduler thread only)
+    int state = R_INIT;      // scheduler thread only
+    int group = -1, slot = -1;
+    cudaEvent_t ev = nullptr;   // recorded on its stream when it rejoins after an update
+    bool ev_pending = false;
     wd_solve_result res{};
     wd::GSolve gs;
+};
+
+// A request group and its members (scheduler thread only).
+struct QGroup {
+    wd::GGroup g;
+    Req *member[wd::GG_MAX] = {};
+    int n_members = 0;
+    int active[wd::GG_MAX] = {};
+    int n_active = 0;
+    bool in_flight = false;
 };
 
 } // namespace
@@ -71,6 +89,8 @@ struct rq_queue {
     };
     std::vector<Idle> pool;
     size_t pool_bytes = 0;
+    std::vector<QGroup *> groups;
+    uint64_t group_launches = 0, group_members = 0;
 };
 
 namespace wd {
@@ -143,49 +163,177 @@ void park(rq_queue *q, Req *r)
     r->gs.s = nullptr;
 }
 
-// Ends a running request whose stream is idle: returns its workspace to the
-// pool (or frees it after a CUDA error) and publishes the result.
+// Ends a running request whose work has finished: leaves its group, returns
+// its workspace to the pool (or frees it after a CUDA error) and publishes the
+// result.
 void retire(rq_queue *q, Req *r, int rc)
 {
+    if (r->group >= 0) {
+        QGroup *G = q->groups[r->group];
+        G->member[r->slot] = nullptr;
+        G->n_members--;
+        r->group = r->slot = -1;
+    }
+    if (r->ev) {
+        cudaEventDestroy(r->ev);
+        r->ev = nullptr;
+    }
     if (rc == WD_ECUDA) gs_release(r->gs);
     else park(q, r);
     finish(q, r, rc != WD_OK ? rc : r->gs.status);
 }
 
-// Advances one running request whose stream has gone idle.  Returns true if it
-// keeps running (a new launch or its reliable update is in flight).
-bool advance(rq_queue *q, Req *r)
+// A group for the request's gauge, inner precision and inner links with a free
+// member slot (a new one if none has): sets r->group and r->slot.
+int join_group(rq_queue *q, Req *r)
+{
+    const int prec = r->d.opts.inner_prec, recon = r->d.opts.inner_recon;
+    int gi = -1;
+    for (size_t k = 0; k < q->groups.size(); ++k) {
+        const QGroup *G = q->groups[k];
+        if (G->g.gauge == r->d.gauge && G->g.prec == prec && G->g.recon == recon && G->n_members < GG_MAX) {
+            gi = (int)k;
+            break;
+        }
+    }
+    if (gi < 0) {
+        QGroup *G = new (std::nothrow) QGroup();
+        if (!G) return set_error(WD_ENOMEM, "host allocation failed");
+        G->g.gauge = r->d.gauge;
+        G->g.prec = prec;
+        G->g.recon = recon;
+        const int rc = gg_create(q->ctx, G->g);
+        if (rc != WD_OK) {
+            gg_destroy(G->g);
+            delete G;
+            return rc;
+        }
+        q->groups.push_back(G);
+        gi = (int)q->groups.size() - 1;
+    }
+    QGroup *G = q->groups[gi];
+    int slot = 0;
+    while (G->member[slot]) ++slot;
+    G->member[slot] = r;
+    G->n_members++;
+    G->g.h_table->m[slot] = gg_member(r->gs);
+    r->group = gi;
+    r->slot = slot;
+    return WD_OK;
+}
+
+// Advances a request that is not in a group launch and whose own stream is
+// idle: initialisation or FP64 update finished, or a cancellation.  Returns
+// true if it keeps running.
+bool advance_own(rq_queue *q, Req *r)
 {
     bool cancel;
     {
         std::lock_guard<std::mutex> lk(q->mu);
         cancel = r->cancel;
     }
-    int rc = WD_OK;
-    if (cancel) rc = WD_ECANCELLED;
-    else if (r->gs.status == WD_OK) {
-        if (r->updating) {           // its FP64 reliable update has finished
-            r->updating = false;
-            rc = gs_after_update(r->gs);
-        } else {                     // its device loop has stopped
-            bool pending = false;
-            rc = gs_after_begin(q->ctx, r->gs, pending);
-            if (rc == WD_OK && pending) {
-                r->updating = true;
-                return true;
-            }
-        }
+    if (cancel) {
+        retire(q, r, WD_ECANCELLED);
+        return false;
     }
-    if (rc == WD_OK && r->gs.active && r->gs.status == WD_OK) {
-        if (gs_launch(r->gs) == WD_OK) {
+    if (r->state == R_INIT) {
+        gs_start(r->gs, 1e300);
+        r->res.t_start = now_s(q);
+        if (!r->gs.active) {
+            retire(q, r, WD_OK);
+            return false;
+        }
+        r->state = R_READY;
+        return true;
+    }
+    if (r->state == R_UPDATING) {
+        const int rc = gs_after_update(r->gs);
+        if (rc != WD_OK || !r->gs.active || r->gs.status != WD_OK) {
+            retire(q, r, rc);
+            return false;
+        }
+        // the restart scalars are still being copied on its stream: the group's
+        // next launch waits for them
+        if (!r->ev && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            retire(q, r, set_error(WD_ECUDA, "event creation failed"));
+            return false;
+        }
+        if (cudaEventRecord(r->ev, r->gs.s) != cudaSuccess) {
+            retire(q, r, set_error(WD_ECUDA, "event record failed"));
+            return false;
+        }
+        r->ev_pending = true;
+        r->state = R_READY;
+        return true;
+    }
+    return true;   // R_READY: waits for its group's next launch
+}
+
+// After a group launch has finished: each member's scalars are handed back;
+// members that need their reliable update (or the convergence test) get it
+// enqueued on their own streams, the others stay ready for the next launch.
+void group_done(rq_queue *q, QGroup *G)
+{
+    G->in_flight = false;
+    for (int t = 0; t < G->n_active; ++t) {
+        Req *r = G->member[G->active[t]];
+        if (!r || r->state != R_ACTIVE) continue;
+        std::memcpy(r->gs.h, G->g.h_hs + (size_t)t * GS_NSCAL, sizeof(double) * GS_NSCAL);
+        bool cancel;
+        {
+            std::lock_guard<std::mutex> lk(q->mu);
+            cancel = r->cancel;
+        }
+        if (cancel) {
+            retire(q, r, WD_ECANCELLED);
+            continue;
+        }
+        bool pending = false;
+        const int rc = gs_after_begin(q->ctx, r->gs, pending);
+        if (rc != WD_OK) {
+            retire(q, r, rc);
+            continue;
+        }
+        r->state = pending ? R_UPDATING : R_READY;
+        if (pending) {
             std::lock_guard<std::mutex> lk(q->mu);
             q->steps++;
-            return true;
         }
-        rc = WD_ECUDA;
     }
-    retire(q, r, rc);
-    return false;
+    G->n_active = 0;
+}
+
+// Starts a group launch with its ready members.  Returns true if one started.
+bool group_start(rq_queue *q, QGroup *G)
+{
+    int n = 0;
+    for (int k = 0; k < GG_MAX; ++k) {
+        Req *r = G->member[k];
+        if (r && r->state == R_READY) G->active[n++] = k;
+    }
+    if (n == 0) return false;
+    int rc = WD_OK;
+    for (int t = 0; t < n && rc == WD_OK; ++t) {
+        Req *r = G->member[G->active[t]];
+        if (r->ev_pending) {
+            if (cudaStreamWaitEvent(G->g.s, r->ev, 0) != cudaSuccess) rc = set_error(WD_ECUDA, "stream wait failed");
+            r->ev_pending = false;
+        }
+    }
+    if (rc == WD_OK) rc = gg_launch(G->g, G->active, n);
+    if (rc != WD_OK) {
+        for (int t = 0; t < n; ++t) retire(q, G->member[G->active[t]], WD_ECUDA);
+        return false;
+    }
+    for (int t = 0; t < n; ++t) G->member[G->active[t]]->state = R_ACTIVE;
+    G->n_active = n;
+    G->in_flight = true;
+    std::lock_guard<std::mutex> lk(q->mu);
+    q->steps++;
+    q->group_launches++;
+    q->group_members += (uint64_t)n;
+    return true;
 }
 
 void scheduler(rq_queue *q)
@@ -213,33 +361,22 @@ void scheduler(rq_queue *q)
             }
             if (stalled) q->stalls++;
         }
-        // set up the admitted requests outside the lock and start their loops
+        // set up the admitted requests outside the lock: workspace, initial
+        // state on their own streams, a member slot in their group
         for (Req *r : admit) {
             r->res.t_admit = now_s(q);
             q->admitted++;
             const bool inject = q->fault_alloc_at > 0 && (int)q->admitted == q->fault_alloc_at;
             int rc = inject ? set_error(WD_ENOMEM, "injected allocation failure (WD_FAULT=alloc)") : acquire(q, r);
-            if (rc == WD_OK) rc = gs_bind(q->ctx, r->gs);
-            if (rc == WD_OK && cudaStreamSynchronize(r->gs.s) != cudaSuccess) rc = set_error(WD_ECUDA, "set-up failed");
+            if (rc == WD_OK) rc = gs_bind(q->ctx, r->gs, false);
+            if (rc == WD_OK) rc = join_group(q, r);
             if (rc != WD_OK) {
                 gs_release(r->gs);
                 finish(q, r, rc);
                 continue;
             }
-            gs_start(r->gs);
-            r->res.t_start = now_s(q);
-            if (!r->gs.active) {
-                park(q, r);
-                finish(q, r, r->gs.status);
-                continue;
-            }
-            if (gs_launch(r->gs) != WD_OK) {
-                gs_release(r->gs);
-                finish(q, r, WD_ECUDA);
-                continue;
-            }
+            r->state = R_INIT;
             std::lock_guard<std::mutex> lk(q->mu);
-            q->steps++;
             q->running.push_back(r);
         }
         std::vector<Req *> running;
@@ -257,25 +394,52 @@ void scheduler(rq_queue *q)
             q->busy_s += dt;
             q->occupancy_sum += dt * (double)running.size();
         }
-        // advance every request whose stream is idle; the others keep running
         bool progress = !admit.empty();
-        std::vector<Req *> keep;
-        for (Req *r : running) {
-            const cudaError_t qe = cudaStreamQuery(r->gs.s);
-            if (qe == cudaErrorNotReady) {
-                keep.push_back(r);
+        // finished group launches
+        for (QGroup *G : q->groups) {
+            if (!G->in_flight) continue;
+            const cudaError_t ge = cudaStreamQuery(G->g.s);
+            if (ge == cudaErrorNotReady) continue;
+            progress = true;
+            if (ge != cudaSuccess) {
+                cudaGetLastError();
+                G->in_flight = false;
+                for (int k = 0; k < G->n_active; ++k)
+                    if (G->member[G->active[k]]) retire(q, G->member[G->active[k]], WD_ECUDA);
+                G->n_active = 0;
                 continue;
             }
+            group_done(q, G);
+        }
+        // requests between group launches whose own streams are idle
+        for (Req *r : running) {
+            if (r->done || r->state == R_ACTIVE) continue;
+            if (r->state == R_READY) {
+                bool cancel;
+                {
+                    std::lock_guard<std::mutex> lk(q->mu);
+                    cancel = r->cancel;
+                }
+                if (!cancel) continue;
+            }
+            const cudaError_t qe = cudaStreamQuery(r->gs.s);
+            if (qe == cudaErrorNotReady) continue;
             progress = true;
             if (qe != cudaSuccess) {
                 cudaGetLastError();
                 retire(q, r, WD_ECUDA);
                 continue;
             }
-            if (advance(q, r)) keep.push_back(r);
+            advance_own(q, r);
         }
+        // next launches of the groups that are idle
+        for (QGroup *G : q->groups)
+            if (!G->in_flight && group_start(q, G)) progress = true;
         {
             std::lock_guard<std::mutex> lk(q->mu);
+            std::vector<Req *> keep;
+            for (Req *r : q->running)
+                if (!r->done) keep.push_back(r);
             q->running.swap(keep);
         }
         // nothing finished: wait briefly, or until a new request arrives
@@ -285,6 +449,11 @@ void scheduler(rq_queue *q)
                                 [q] { return q->stop || (!q->waiting.empty() && (int)q->running.size() < q->max_slots); });
         }
     }
+    for (QGroup *G : q->groups) {
+        gg_destroy(G->g);
+        delete G;
+    }
+    q->groups.clear();
     for (auto &e : q->pool) free_idle(e);
     q->pool.clear();
     q->pool_bytes = 0;
@@ -444,6 +613,8 @@ int rq_stats(rq_queue *q, rq_counters *out)
     out->waiting = (int)q->waiting.size();
     out->running = (int)q->running.size();
     out->hbm_in_use = q->in_use;
+    out->group_launches = q->group_launches;
+    out->mean_group_size = q->group_launches ? (double)q->group_members / (double)q->group_launches : 0.0;
     return WD_OK;
 }
 

@@ -188,3 +188,21 @@ def test_hard_solves_with_small_delta(prec):
     for (p, host), r in zip(reqs, res):
         assert r["status"] == 0, r
         assert _true_rel(ctx, host, p["x"])[0] <= 1e-12
+
+
+def test_requests_on_one_gauge_share_group_launches():
+    """Requests on the same gauge, inner precision and links iterate in one group: each
+    launch of the group's loop serves several of them (mean group size > 1), and every
+    result still meets its tolerance by the oracle."""
+    ctx = _ctx()
+    q = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=8)
+    reqs = [_request(ctx, k, dims=(8, 8, 8, 8), tol=1e-10) for k in range(8)]
+    tickets = [q.submit(p) for p, _ in reqs]
+    res = [q.wait(t, timeout_ms=120000) for t in tickets]
+    st = q.stats()
+    q.close()
+    for (p, host), r in zip(reqs, res):
+        assert r["status"] == 0, r
+        assert _true_rel(ctx, host, p["x"])[0] <= p["tol"]
+    assert st["group_launches"] > 0
+    assert st["mean_group_size"] > 1.5, st
