@@ -453,9 +453,12 @@ int wilson_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x, const voi
  * Modes:
  *   WD_BATCH_SEQUENTIAL  cg_solve on each descriptor in turn (any options);
  *   WD_BATCH_GRAPH       mixed-precision reliable-update solves (inner_prec
- *                        WD_F32/WD_F16/WD_BF16, the same for all), each a
- *                        CUDA graph with a device-side iteration loop on a
- *                        stream per solve; FP64 reliable updates and the
+ *                        WD_F32/WD_F16/WD_BF16) run as the request groups of
+ *                        the serving queue (rq_*): the solves of one gauge,
+ *                        inner precision and inner link format iterate in one
+ *                        CUDA graph with a device-side loop and one
+ *                        shared-link launch per hop for all of them; FP64
+ *                        reliable updates on each solve's own stream, the
  *                        convergence test on the host between launches;
  *   WD_BATCH_PERSISTENT  one cooperative kernel: each solve runs on its own
  *                        group of thread blocks (sized by volume), steps

@@ -4,12 +4,14 @@
 // reliable-update scheme of cg.cu (low-precision iterated residual, FP64
 // solution, true residual and inner products):
 //   WD_BATCH_SEQUENTIAL  one cg_solve after another;
-//   WD_BATCH_GRAPH       each solve's iteration (4 hop launches and 3 BLAS
-//                        kernels whose scalars stay in device memory) is the
-//                        body of a device-side WHILE loop in a CUDA graph per
-//                        solve; the graphs of all active solves run on their
-//                        own streams until a reliable update is due, and the
-//                        host does the FP64 updates between launches;
+//   WD_BATCH_GRAPH       the solves of one gauge run as a request group of
+//                        the serving queue: one CUDA graph per group whose
+//                        device-side WHILE loop runs their iterations with
+//                        one shared-link launch per hop for all of them (4 hop
+//                        launches and 3 BLAS kernels, scalars in device
+//                        memory) until one needs its reliable update, which
+//                        the host enqueues on that solve's own stream while
+//                        the group goes on;
 //   WD_BATCH_PERSISTENT  one cooperative launch (all solves with the same
 //                        inner precision): each solve owns a group of
 //                        thread blocks (sized in proportion to its volume)
@@ -524,52 +526,36 @@ int run_persistent(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stat
 }
 
 // ---------------------------------------------------------------------------
-// graph mode (per-solve graphs, see gsolve.cuh)
+// graph mode: the serving queue with every solve submitted at once, so that
+// the solves on one gauge run as one request group (one shared-link hop launch
+// per hop for all of them, in the group's device-side graph loop; ggroup.cuh)
+// and the groups and the FP64 reliable updates run concurrently.
 // ---------------------------------------------------------------------------
 int run_graph(wd_ctx *ctx, int n, const wd_solve_desc *d, wd_cg_stats *stats)
 {
-    std::vector<GSolve> q(n);
-    int rc = WD_OK;
-    for (int k = 0; k < n && rc == WD_OK; ++k) {
-        q[k].gauge = d[k].gauge;
-        q[k].mass = d[k].mass;
-        q[k].tol = d[k].tol;
-        q[k].x = d[k].x_e;
-        q[k].b = d[k].b_e;
-        q[k].opts = d[k].opts;
-        rc = gs_setup(ctx, q[k]);
-    }
-    for (int k = 0; k < n && rc == WD_OK; ++k) {
-        if (cudaStreamSynchronize(q[k].s) != cudaSuccess) rc = set_error(WD_ECUDA, "batch set-up failed");
-        else gs_start(q[k]);
-    }
-    while (rc == WD_OK) {
-        bool any = false;
-        for (int k = 0; k < n && rc == WD_OK; ++k)
-            if (q[k].active) {
-                any = true;
-                rc = gs_launch(q[k]);
-            }
-        if (!any) break;
-        for (int k = 0; k < n && rc == WD_OK; ++k)
-            if (q[k].active) {
-                if (cudaStreamSynchronize(q[k].s) != cudaSuccess) rc = set_error(WD_ECUDA, "graph replay failed");
-                else rc = gs_after(ctx, q[k]);
-            }
-    }
-    int first_bad = -1;
-    for (int k = 0; k < n; ++k) {
+    size_t budget = 0;
+    for (int k = 0; k < n; ++k) budget += gs_footprint(d[k].gauge->geo.Vh, d[k].opts.inner_prec);
+    rq_queue *q = nullptr;
+    WD_TRY(rq_create(ctx, budget > 0 ? budget : 1, n > 0 ? n : 1, &q));
+    std::vector<uint64_t> tickets(n, 0);
+    int rc = WD_OK, submitted = 0;
+    for (int k = 0; k < n && rc == WD_OK; ++k, ++submitted) rc = rq_submit(q, &d[k], &tickets[k]);
+    int first_bad = -1, bad_status = WD_OK;
+    for (int k = 0; k < submitted; ++k) {
+        wd_solve_result res{};
+        if (rq_wait(q, tickets[k], -1, &res) != WD_OK && rc == WD_OK) rc = WD_ECUDA;
         if (stats) {
-            stats[k].status = rc ? rc : q[k].status;
-            stats[k].iters = q[k].iters;
-            stats[k].reliable_updates = q[k].updates;
-            stats[k].true_rel_resid = q[k].rel;
+            stats[k] = res.stats;
+            stats[k].status = res.status;
         }
-        if (q[k].status != WD_OK && first_bad < 0) first_bad = k;
-        gs_release(q[k]);
+        if (res.status != WD_OK && first_bad < 0) {
+            first_bad = k;
+            bad_status = res.status;
+        }
     }
-    if (rc) return rc;
-    if (first_bad >= 0) return set_error(q[first_bad].status, "solve %d of the batch failed", first_bad);
+    rq_destroy(q);
+    if (rc != WD_OK) return rc;
+    if (first_bad >= 0) return set_error(bad_status, "solve %d of the batch failed", first_bad);
     return WD_OK;
 }
 
