@@ -1213,6 +1213,7 @@ def run_case(argv) -> int:
         python bench.py --case --op stream --kind 1 --n 16777216 --launches 3
         python bench.py --case --op dd --nsub 4 --halo f16 --launches 3
         python bench.py --case --op solve --prec f16 --dims 24,24,24,48 --launches 1
+        python bench.py --case --op batch --prec f16 --dims 24,24,24,48 --nrhs 8 --launches 1
 
     Inputs are the seeded synthetic gauge field and source of the benchmark.  With
     --threads/--variant the launch shape is pinned; otherwise the library default
@@ -1223,9 +1224,11 @@ def run_case(argv) -> int:
     kind --kind on --n elements of N(0,1) arrays.  --op dd applies the operator
     `launches` times to the lattice split into --nsub slabs (field precision
     --prec, halos --halo).  --op solve runs `launches` full-system solves
-    D x = b by BiCGStab (inner precision --prec, delta 0.01, tol 1e-10, mass 0.1)."""
+    D x = b by BiCGStab (inner precision --prec, delta 0.01, tol 1e-10, mass 0.1).
+    --op batch runs `launches` graph-mode batches of --nrhs solves on one gauge
+    (one request group: shared-link hops), masses 0.1, 0.15, ..., tol 1e-10."""
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["full", "eo", "cg", "stream", "dd", "solve"], default="full")
+    ap.add_argument("--op", choices=["full", "eo", "cg", "stream", "dd", "solve", "batch"], default="full")
     ap.add_argument("--nsub", type=int, default=2)
     ap.add_argument("--halo", choices=["f64", "f32", "f16"], default="f32")
     ap.add_argument("--kind", type=int, default=1)
@@ -1274,6 +1277,20 @@ def run_case(argv) -> int:
         print(f"case: dd {a.prec} halo {a.halo} {a.dims} nsub={a.nsub} launches={a.launches} ok")
         return 0
     g = wd.Gauge(ctx, dims, synth.gauge(dims, seed=1001))
+    if a.op == "batch":   # --nrhs solves on this gauge as one request group (graph batch mode)
+        probs = []
+        for k in range(a.nrhs):
+            b = synth.even_spinor(dims, seed=3400 + k)
+            fb = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+            wd.pack(ctx, dims, wd.SITES_EVEN, wd.F64,
+                    torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
+            probs.append(dict(gauge=g, mass=0.1 + 0.05 * k, tol=1e-10, b=fb, x=wd.alloc_field(dims, wd.SITES_EVEN, wd.F64),
+                              inner_prec=prec, delta=0.01))
+        for _ in range(a.launches):
+            st = wd.cg_solve_batch(ctx, probs, mode=wd.BATCH_GRAPH)
+        torch.cuda.synchronize()
+        print(f"case: batch {a.prec} {a.dims} solves={a.nrhs} iters={[s_['iters'] for s_ in st]} ok")
+        return 0
     if a.op == "solve":
         b = synth.spinor(dims, seed=3201)
         fb = wd.alloc_field(dims, wd.SITES_FULL, wd.F64)
