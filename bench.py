@@ -385,15 +385,16 @@ def run_gpu(args):
     def step():
         wd.dslash_apply(ctx, g, fout, fin, MASS, prec=prec, recon=recon, stream=stream)
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-
     events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
+    # the sampler starts (and waits for its first samples) before the warm-up, so that the
+    # GPU does not sit idle between the warm-up and the timed steps
     with ClockSampler(dev) as clk:
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
         events[0].record(stream)
         for k in range(args.steps):
             step()
