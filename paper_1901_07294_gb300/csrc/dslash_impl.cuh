@@ -77,9 +77,32 @@ __device__ __forceinline__ void project(const T (&v)[24], cpx<T> (&h0)[3], cpx<T
 
 // acc += (1 + S gamma_MU) applied in the projected form: spins 0,1 get w0,w1
 // and spins 2,3 are the fixed multiples of w0,w1 that the projector implies.
-template <int MU, int S, typename T>
+// FIRST: the first direction of a site, whose terms are assigned instead of
+// added to zeros (the same values, without 24 additions).
+template <int MU, int S, bool FIRST = false, typename T>
 __device__ __forceinline__ void accumulate(cpx<T> (&acc)[4][3], const cpx<T> (&w0)[3], const cpx<T> (&w1)[3])
 {
+    if constexpr (FIRST) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            acc[0][c] = w0[c];
+            acc[1][c] = w1[c];
+            if constexpr (MU == 0) {        // spin2 = -S i w1, spin3 = -S i w0
+                acc[2][c] = {S * w1[c].im, -S * w1[c].re};
+                acc[3][c] = {S * w0[c].im, -S * w0[c].re};
+            } else if constexpr (MU == 1) { // spin2 = S w1, spin3 = -S w0
+                acc[2][c] = {S * w1[c].re, S * w1[c].im};
+                acc[3][c] = {-S * w0[c].re, -S * w0[c].im};
+            } else if constexpr (MU == 2) { // spin2 = -S i w0, spin3 = S i w1
+                acc[2][c] = {S * w0[c].im, -S * w0[c].re};
+                acc[3][c] = {-S * w1[c].im, S * w1[c].re};
+            } else {                        // spin2 = S w0, spin3 = S w1
+                acc[2][c] = {S * w0[c].re, S * w0[c].im};
+                acc[3][c] = {S * w1[c].re, S * w1[c].im};
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         acc[0][c].re += w0[c].re; acc[0][c].im += w0[c].im;
@@ -123,7 +146,7 @@ __device__ __forceinline__ void su3_mul(const cpx<T> (&U)[3][3], const cpx<T> (&
 // stored reals.  neg: the hop crosses an antiperiodic boundary, U h changes
 // sign (done here rather than in the stored links, whose 12-real form
 // rebuilds row 3 assuming det U = 1).
-template <int P, int RECON, int MU, int S, bool FWD, bool LNA = false>
+template <int P, int RECON, int MU, int S, bool FWD, bool LNA = false, bool FIRST = false>
 __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh, int nb, int li, bool neg,
                                         cpx<typename Prec<P>::real> (&acc)[4][3])
 {
@@ -153,7 +176,7 @@ __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh
             }
         }
     }
-    accumulate<MU, S>(acc, w0, w1);
+    accumulate<MU, S, FIRST>(acc, w0, w1);
 }
 
 // PF selects the memory schedule (chosen per problem by the autotuner):
@@ -205,15 +228,11 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
     constexpr int SB = -SF;             // backward projector
     const size_t lb = A.link_blk;
 
-    cpx<T> acc[4][3];
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc[s][c] = {T(0), T(0)};
+    cpx<T> acc[4][3];   // set by the first direction (x, taken in every pass)
 
     using LK = Link<link_prec(P), RECON>;
-    if constexpr (PF == 0) {
-        hop_dir<P, RECON, 0, SF, true, LNA>(in, gf + 0 * lb, vh, xf, i, false, acc);
+    if constexpr (PF == 0 || PF == 5) {
+        hop_dir<P, RECON, 0, SF, true, LNA, true>(in, gf + 0 * lb, vh, xf, i, false, acc);
         hop_dir<P, RECON, 0, SB, false, LNA>(in, gb + 0 * lb, vh, xb, xb, false, acc);
         hop_dir<P, RECON, 1, SF, true, LNA>(in, gf + 1 * lb, vh, yf, i, false, acc);
         hop_dir<P, RECON, 1, SB, false, LNA>(in, gb + 1 * lb, vh, yb, yb, false, acc);
@@ -231,7 +250,7 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
             LK::prefetch(gb + 2 * lb, vh, zb);
             LK::prefetch(gb + 3 * lb, vh, tb);
         }
-        hop_dir<P, RECON, 0, SB, false, LNA>(in, gb + 0 * lb, vh, xb, xb, false, acc);
+        hop_dir<P, RECON, 0, SB, false, LNA, true>(in, gb + 0 * lb, vh, xb, xb, false, acc);
         hop_dir<P, RECON, 1, SB, false, LNA>(in, gb + 1 * lb, vh, yb, yb, false, acc);
         hop_dir<P, RECON, 2, SB, false, LNA>(in, gb + 2 * lb, vh, zb, zb, false, acc);
         if (dtb) hop_dir<P, RECON, 3, SB, false, LNA>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
@@ -252,6 +271,14 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
                 o[6 * s + 2 * c] = a * o[6 * s + 2 * c] + b * acc[s][c].re;
                 o[6 * s + 2 * c + 1] = a * o[6 * s + 2 * c + 1] + b * acc[s][c].im;
             }
+    } else if (A.b == 1.0) {   // the bare hopping term: no scaling
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o[6 * s + 2 * c] = acc[s][c].re;
+                o[6 * s + 2 * c + 1] = acc[s][c].im;
+            }
     } else {
 #pragma unroll
         for (int s = 0; s < 4; ++s)
@@ -266,9 +293,12 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
 
 // PF 4 is schedule 1 compiled for 3 resident blocks of 256 threads per SM
 // (at most 85 registers): more warps to hide latency, at the price of
-// registers the compiler would otherwise use to hoist loads.
+// registers the compiler would otherwise use to hoist loads.  PF 5 is
+// schedule 0 compiled for one block of 256 per SM: the FP64 kernel, bound by
+// the FP64 pipe rather than by latency, then needs no spill stores (at the
+// 128-register cap of two blocks it spills 200-550 bytes per thread).
 template <int P, int RECON, bool DAG, bool HAS_X, int PF, bool TOPEN = false, bool LNA = false>
-__global__ void __launch_bounds__(256, PF == 4 ? 3 : 2) hop_kernel(const HopArgs A)
+__global__ void __launch_bounds__(256, PF == 4 ? 3 : PF == 5 ? 1 : 2) hop_kernel(const HopArgs A)
 {
     int p, blk;
     if (A.nparity == 2) { p = blockIdx.x & 1; blk = blockIdx.x >> 1; }
@@ -290,6 +320,9 @@ cudaError_t launch_hop_pf(const HopArgs &A, dim3 grid, int threads, int pf, bool
     case 0: return wd_launch(hop_kernel<P, RECON, DAG, HX, 0>, grid, dim3(threads), 0, s, A);
     case 1: return wd_launch(hop_kernel<P, RECON, DAG, HX, 1>, grid, dim3(threads), 0, s, A);
     case 2: return wd_launch(hop_kernel<P, RECON, DAG, HX, 2>, grid, dim3(threads), 0, s, A);
+    case 5:
+        if constexpr (P == PREC_F64) return wd_launch(hop_kernel<P, RECON, DAG, HX, 5>, grid, dim3(threads), 0, s, A);
+        else return wd_launch(hop_kernel<P, RECON, DAG, HX, 0>, grid, dim3(threads), 0, s, A);
     default: return wd_launch(hop_kernel<P, RECON, DAG, HX, 4>, grid, dim3(threads), 0, s, A);
     }
 }

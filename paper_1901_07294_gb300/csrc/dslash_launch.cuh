@@ -19,7 +19,8 @@ constexpr int HOP_NA0_VARIANT = 11;   // schedule 0 with the links loaded withou
 constexpr int HOP_NA1_VARIANT = 12;   // schedule 1 with the links loaded without L1 allocation
 constexpr int HOP_SP1_VARIANT = 13;   // 16-bit formats: schedule 1 with spin-paired FP32 arithmetic
 constexpr int HOP_SP0_VARIANT = 14;   // 16-bit formats: schedule 0, spin-paired, links without L1 allocation
-constexpr int HOP_MAX_VARIANT = 14;   // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
+constexpr int HOP_F64_1B_VARIANT = 15;// FP64: schedule 0 built for one block of 256 per SM (no spills); else schedule 0
+constexpr int HOP_MAX_VARIANT = 15;   // 5, 6, 7: the multi-RHS kernel in z-strips of 16, 8, 4
 
 // Multi-RHS variants and their z-strip width (0: natural order); -1 if v is not one.
 __host__ __device__ constexpr int hop_mrhs_strip(int v)
@@ -87,6 +88,7 @@ cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int th
     }
     if (pf == HOP_SP1_VARIANT) pf = 1;   // FP32, FP64, or an open-boundary pass
     if (pf == HOP_SP0_VARIANT) pf = 0;
+    if (pf == HOP_F64_1B_VARIANT) pf = 5;   // launch_hop_pf: schedule 0 outside FP64
     cudaError_t e = cudaSuccess;
     if (pf == HOP_RETIRED_VARIANT) pf = 1;
     if (pf == HOP_TILE_VARIANT) {

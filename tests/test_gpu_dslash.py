@@ -254,7 +254,7 @@ def test_argument_errors(ctx):
 
 
 @pytest.mark.parametrize("prec", ALL_PREC)
-@pytest.mark.parametrize("variant", [0, 1, 2, 8, 9, 11, 12, 13, 14])
+@pytest.mark.parametrize("variant", [0, 1, 2, 8, 9, 11, 12, 13, 14, 15])
 @pytest.mark.parametrize("threads", [64, 192, 256])
 def test_every_launch_variant_matches_oracle(prec, variant, threads):
     """Each memory schedule and block size the autotuner may pick computes the same operator."""
@@ -289,8 +289,8 @@ def test_autotuner_table_and_choice():
     table = wd.tune_dslash(ctx, g, wd.F32, 18, full=True)
     # 4 block sizes x 8 single-field variants: schedules 0, 1, 2, the high-occupancy build 4,
     # the shared-memory neighbour window 8, two sites per thread 9 and schedules 0 and 1 with
-    # links loaded without L1 allocation (11, 12); 10 is retired, and the spin-paired kernels
-    # 13, 14 exist for the 16-bit formats only
+    # links loaded without L1 allocation (11, 12); 10 is retired, the spin-paired kernels
+    # 13, 14 exist for the 16-bit formats only and the one-block-per-SM build 15 for FP64
     assert len(table) == 32
     assert {t["variant"] for t in table} == {0, 1, 2, 4, 8, 9, 11, 12}
     assert all(t["ms"] > 0 for t in table)
@@ -333,7 +333,7 @@ def test_high_occupancy_variant_matches_oracle(prec, dims, threads):
 
 @pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 2, 6), (6, 2, 2, 2), (2, 2, 10, 2)])
 @pytest.mark.parametrize("prec", ALL_PREC)
-@pytest.mark.parametrize("threads,variant", [(32, 0), (64, 1), (256, 2), (192, 4), (32, 8), (128, 8), (64, 9), (96, 9), (64, 11), (128, 12), (32, 13), (64, 13), (96, 14), (128, 14)])
+@pytest.mark.parametrize("threads,variant", [(32, 0), (64, 1), (256, 2), (192, 4), (32, 8), (128, 8), (64, 9), (96, 9), (64, 11), (128, 12), (32, 13), (64, 13), (96, 14), (128, 14), (128, 15), (256, 15)])
 def test_degenerate_extents_and_ragged_tails(dims, prec, threads, variant):
     """L_mu = 2 (x+mu and x-mu are the same site, both terms added) and half-lattice sizes far
     below or not a multiple of the block size."""
