@@ -123,6 +123,80 @@ __device__ __forceinline__ void accumulate(cpx<T> (&acc)[4][3], const cpx<T> (&w
     }
 }
 
+// project for 16-bit storage, from the twelve storage words: each of the 12
+// outputs is one stored value plus or minus another, widened and added in
+// one rounding (the result of project on the widened values, bit for bit).
+template <int P, int MU, int S>
+__device__ __forceinline__ void project_words(const unsigned (&u)[12], cpx<float> (&h0)[3], cpx<float> (&h1)[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const unsigned p0 = u[c], p1 = u[3 + c], p2 = u[6 + c], p3 = u[9 + c];
+        if constexpr (MU == 0) {        // h0 = p0 + S i p3, h1 = p1 + S i p2
+            h0[c] = {h16_pm<P, 0, 1, -S>(p0, p3), h16_pm<P, 1, 0, S>(p0, p3)};
+            h1[c] = {h16_pm<P, 0, 1, -S>(p1, p2), h16_pm<P, 1, 0, S>(p1, p2)};
+        } else if constexpr (MU == 1) { // h0 = p0 - S p3, h1 = p1 + S p2
+            h0[c] = {h16_pm<P, 0, 0, -S>(p0, p3), h16_pm<P, 1, 1, -S>(p0, p3)};
+            h1[c] = {h16_pm<P, 0, 0, S>(p1, p2), h16_pm<P, 1, 1, S>(p1, p2)};
+        } else if constexpr (MU == 2) { // h0 = p0 + S i p2, h1 = p1 - S i p3
+            h0[c] = {h16_pm<P, 0, 1, -S>(p0, p2), h16_pm<P, 1, 0, S>(p0, p2)};
+            h1[c] = {h16_pm<P, 0, 1, S>(p1, p3), h16_pm<P, 1, 0, -S>(p1, p3)};
+        } else {                        // h0 = p0 + S p2, h1 = p1 + S p3
+            h0[c] = {h16_pm<P, 0, 0, S>(p0, p2), h16_pm<P, 1, 1, S>(p0, p2)};
+            h1[c] = {h16_pm<P, 0, 0, S>(p1, p3), h16_pm<P, 1, 1, S>(p1, p3)};
+        }
+    }
+}
+
+// accumulate with every term weighted by f (the neighbour's scale times the
+// hop coefficient): the weight rides on the additions as FMAs instead of
+// costing 12 multiplications of U h per direction and 24 of the sum.
+template <int MU, int S, bool FIRST = false>
+__device__ __forceinline__ void accumulate_f(cpx<float> (&acc)[4][3], const cpx<float> (&w0)[3], const cpx<float> (&w1)[3],
+                                             const float f)
+{
+    const float g = S * f;
+    if constexpr (FIRST) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            acc[0][c] = {f * w0[c].re, f * w0[c].im};
+            acc[1][c] = {f * w1[c].re, f * w1[c].im};
+            if constexpr (MU == 0) {        // spin2 = -S i w1, spin3 = -S i w0
+                acc[2][c] = {g * w1[c].im, -g * w1[c].re};
+                acc[3][c] = {g * w0[c].im, -g * w0[c].re};
+            } else if constexpr (MU == 1) { // spin2 = S w1, spin3 = -S w0
+                acc[2][c] = {g * w1[c].re, g * w1[c].im};
+                acc[3][c] = {-g * w0[c].re, -g * w0[c].im};
+            } else if constexpr (MU == 2) { // spin2 = -S i w0, spin3 = S i w1
+                acc[2][c] = {g * w0[c].im, -g * w0[c].re};
+                acc[3][c] = {-g * w1[c].im, g * w1[c].re};
+            } else {                        // spin2 = S w0, spin3 = S w1
+                acc[2][c] = {g * w0[c].re, g * w0[c].im};
+                acc[3][c] = {g * w1[c].re, g * w1[c].im};
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[0][c].re = fmaf(f, w0[c].re, acc[0][c].re); acc[0][c].im = fmaf(f, w0[c].im, acc[0][c].im);
+        acc[1][c].re = fmaf(f, w1[c].re, acc[1][c].re); acc[1][c].im = fmaf(f, w1[c].im, acc[1][c].im);
+        if constexpr (MU == 0) {
+            acc[2][c].re = fmaf(g, w1[c].im, acc[2][c].re); acc[2][c].im = fmaf(-g, w1[c].re, acc[2][c].im);
+            acc[3][c].re = fmaf(g, w0[c].im, acc[3][c].re); acc[3][c].im = fmaf(-g, w0[c].re, acc[3][c].im);
+        } else if constexpr (MU == 1) {
+            acc[2][c].re = fmaf(g, w1[c].re, acc[2][c].re); acc[2][c].im = fmaf(g, w1[c].im, acc[2][c].im);
+            acc[3][c].re = fmaf(-g, w0[c].re, acc[3][c].re); acc[3][c].im = fmaf(-g, w0[c].im, acc[3][c].im);
+        } else if constexpr (MU == 2) {
+            acc[2][c].re = fmaf(g, w0[c].im, acc[2][c].re); acc[2][c].im = fmaf(-g, w0[c].re, acc[2][c].im);
+            acc[3][c].re = fmaf(-g, w1[c].im, acc[3][c].re); acc[3][c].im = fmaf(g, w1[c].re, acc[3][c].im);
+        } else {
+            acc[2][c].re = fmaf(g, w0[c].re, acc[2][c].re); acc[2][c].im = fmaf(g, w0[c].im, acc[2][c].im);
+            acc[3][c].re = fmaf(g, w1[c].re, acc[3][c].re); acc[3][c].im = fmaf(g, w1[c].im, acc[3][c].im);
+        }
+    }
+}
+
 // w = U h (FWD) or U^dagger h.
 template <bool FWD, typename T>
 __device__ __forceinline__ void su3_mul(const cpx<T> (&U)[3][3], const cpx<T> (&h)[3], cpx<T> (&w)[3])
@@ -141,18 +215,33 @@ __device__ __forceinline__ void su3_mul(const cpx<T> (&U)[3][3], const cpx<T> (&
     }
 }
 
-// One direction.  For 16-bit storage the neighbour's per-site scale is applied
-// to the 12 reals of U h (the operation is linear) rather than to its 24
-// stored reals.  neg: the hop crosses an antiperiodic boundary, U h changes
-// sign (done here rather than in the stored links, whose 12-real form
-// rebuilds row 3 assuming det U = 1).
+// One direction.  For 16-bit storage the projection reads the stored words,
+// and the neighbour's per-site scale times wt (the hop coefficient, applied
+// here instead of to the sum) weights the accumulated terms: the operation is
+// linear, so neither the 24 stored reals nor the 12 of U h are scaled on
+// their own.  neg: the hop crosses an antiperiodic boundary, U h changes sign
+// (done here rather than in the stored links, whose 12-real form rebuilds
+// row 3 assuming det U = 1).
 template <int P, int RECON, int MU, int S, bool FWD, bool LNA = false, bool FIRST = false>
 __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh, int nb, int li, bool neg,
-                                        cpx<typename Prec<P>::real> (&acc)[4][3])
+                                        cpx<typename Prec<P>::real> (&acc)[4][3], const float wt = 1.0f)
 {
     using T = typename Prec<P>::real;
+    if constexpr (Prec<P>::scaled) {
+        unsigned u[12];
+        const float sc = Spinor<P>::load_words(in, vh, nb, u);
+        cpx<float> h0[3], h1[3];
+        project_words<P, MU, S>(u, h0, h1);
+        cpx<float> U[3][3];
+        Link<link_prec(P), RECON>::template load<LNA>(lblk, vh, li, U);
+        cpx<float> w0[3], w1[3];
+        su3_mul<FWD>(U, h0, w0);
+        su3_mul<FWD>(U, h1, w1);
+        accumulate_f<MU, S, FIRST>(acc, w0, w1, (neg ? -sc : sc) * wt);
+        return;
+    }
     T psi[24];
-    const float sc = Spinor<P>::load_unscaled(in, vh, nb, psi);
+    Spinor<P>::load(in, vh, nb, psi);
     cpx<T> h0[3], h1[3];
     project<MU, S>(psi, h0, h1);
     cpx<T> U[3][3];
@@ -160,23 +249,44 @@ __device__ __forceinline__ void hop_dir(const char *in, const char *lblk, int vh
     cpx<T> w0[3], w1[3];
     su3_mul<FWD>(U, h0, w0);
     su3_mul<FWD>(U, h1, w1);
-    if constexpr (Prec<P>::scaled) {
-        const T f = neg ? -sc : sc;
+    if (neg) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            w0[c].re *= f; w0[c].im *= f;
-            w1[c].re *= f; w1[c].im *= f;
-        }
-    } else {
-        if (neg) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                w0[c].re = -w0[c].re; w0[c].im = -w0[c].im;
-                w1[c].re = -w1[c].re; w1[c].im = -w1[c].im;
-            }
+            w0[c].re = -w0[c].re; w0[c].im = -w0[c].im;
+            w1[c].re = -w1[c].re; w1[c].im = -w1[c].im;
         }
     }
     accumulate<MU, S, FIRST>(acc, w0, w1);
+}
+
+// 16-bit storage: out = a x + acc at site i, with acc the sum already
+// weighted by the hop coefficient (hop_dir's wt); x is read as stored and its
+// per-site scale folded into a.
+template <int P, bool HAS_X>
+__device__ __forceinline__ void store_weighted(const char *x, char *out, int vh, int i, float a,
+                                               const cpx<float> (&acc)[4][3])
+{
+    float o[24];
+    if constexpr (HAS_X) {
+        unsigned u[12];
+        const float ax = a * Spinor<P>::load_words(x, vh, i, u);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o[6 * s + 2 * c] = fmaf(ax, h16_f32<P, 0>(u[3 * s + c]), acc[s][c].re);
+                o[6 * s + 2 * c + 1] = fmaf(ax, h16_f32<P, 1>(u[3 * s + c]), acc[s][c].im);
+            }
+    } else {
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o[6 * s + 2 * c] = acc[s][c].re;
+                o[6 * s + 2 * c + 1] = acc[s][c].im;
+            }
+    }
+    Spinor<P>::store(out, vh, i, o);
 }
 
 // PF selects the memory schedule (chosen per problem by the autotuner):
@@ -229,17 +339,19 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
     const size_t lb = A.link_blk;
 
     cpx<T> acc[4][3];   // set by the first direction (x, taken in every pass)
+    // 16-bit storage: the hop coefficient b weights the accumulated terms
+    const float wt = Prec<P>::scaled ? (float)A.b : 1.0f;
 
     using LK = Link<link_prec(P), RECON>;
     if constexpr (PF == 0 || PF == 5) {
-        hop_dir<P, RECON, 0, SF, true, LNA, true>(in, gf + 0 * lb, vh, xf, i, false, acc);
-        hop_dir<P, RECON, 0, SB, false, LNA>(in, gb + 0 * lb, vh, xb, xb, false, acc);
-        hop_dir<P, RECON, 1, SF, true, LNA>(in, gf + 1 * lb, vh, yf, i, false, acc);
-        hop_dir<P, RECON, 1, SB, false, LNA>(in, gb + 1 * lb, vh, yb, yb, false, acc);
-        hop_dir<P, RECON, 2, SF, true, LNA>(in, gf + 2 * lb, vh, zf, i, false, acc);
-        hop_dir<P, RECON, 2, SB, false, LNA>(in, gb + 2 * lb, vh, zb, zb, false, acc);
-        if (dtf) hop_dir<P, RECON, 3, SF, true, LNA>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
-        if (dtb) hop_dir<P, RECON, 3, SB, false, LNA>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
+        hop_dir<P, RECON, 0, SF, true, LNA, true>(in, gf + 0 * lb, vh, xf, i, false, acc, wt);
+        hop_dir<P, RECON, 0, SB, false, LNA>(in, gb + 0 * lb, vh, xb, xb, false, acc, wt);
+        hop_dir<P, RECON, 1, SF, true, LNA>(in, gf + 1 * lb, vh, yf, i, false, acc, wt);
+        hop_dir<P, RECON, 1, SB, false, LNA>(in, gb + 1 * lb, vh, yb, yb, false, acc, wt);
+        hop_dir<P, RECON, 2, SF, true, LNA>(in, gf + 2 * lb, vh, zf, i, false, acc, wt);
+        hop_dir<P, RECON, 2, SB, false, LNA>(in, gb + 2 * lb, vh, zb, zb, false, acc, wt);
+        if (dtf) hop_dir<P, RECON, 3, SF, true, LNA>(in, gf + 3 * lb, vh, tf, i, ntf, acc, wt);
+        if (dtb) hop_dir<P, RECON, 3, SB, false, LNA>(in, gb + 3 * lb, vh, tb, tb, ntb, acc, wt);
     } else {
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) LK::prefetch(gf + mu * lb, vh, i);
@@ -250,19 +362,23 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
             LK::prefetch(gb + 2 * lb, vh, zb);
             LK::prefetch(gb + 3 * lb, vh, tb);
         }
-        hop_dir<P, RECON, 0, SB, false, LNA, true>(in, gb + 0 * lb, vh, xb, xb, false, acc);
-        hop_dir<P, RECON, 1, SB, false, LNA>(in, gb + 1 * lb, vh, yb, yb, false, acc);
-        hop_dir<P, RECON, 2, SB, false, LNA>(in, gb + 2 * lb, vh, zb, zb, false, acc);
-        if (dtb) hop_dir<P, RECON, 3, SB, false, LNA>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
-        hop_dir<P, RECON, 0, SF, true, LNA>(in, gf + 0 * lb, vh, xf, i, false, acc);
-        hop_dir<P, RECON, 1, SF, true, LNA>(in, gf + 1 * lb, vh, yf, i, false, acc);
-        hop_dir<P, RECON, 2, SF, true, LNA>(in, gf + 2 * lb, vh, zf, i, false, acc);
-        if (dtf) hop_dir<P, RECON, 3, SF, true, LNA>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
+        hop_dir<P, RECON, 0, SB, false, LNA, true>(in, gb + 0 * lb, vh, xb, xb, false, acc, wt);
+        hop_dir<P, RECON, 1, SB, false, LNA>(in, gb + 1 * lb, vh, yb, yb, false, acc, wt);
+        hop_dir<P, RECON, 2, SB, false, LNA>(in, gb + 2 * lb, vh, zb, zb, false, acc, wt);
+        if (dtb) hop_dir<P, RECON, 3, SB, false, LNA>(in, gb + 3 * lb, vh, tb, tb, ntb, acc, wt);
+        hop_dir<P, RECON, 0, SF, true, LNA>(in, gf + 0 * lb, vh, xf, i, false, acc, wt);
+        hop_dir<P, RECON, 1, SF, true, LNA>(in, gf + 1 * lb, vh, yf, i, false, acc, wt);
+        hop_dir<P, RECON, 2, SF, true, LNA>(in, gf + 2 * lb, vh, zf, i, false, acc, wt);
+        if (dtf) hop_dir<P, RECON, 3, SF, true, LNA>(in, gf + 3 * lb, vh, tf, i, ntf, acc, wt);
     }
 
     const T a = (T)A.a, b = (T)A.b;
     T o[24];
-    if constexpr (HAS_X) {
+    if constexpr (Prec<P>::scaled) {   // acc already carries b
+        store_weighted<P, HAS_X>(HAS_X ? (p ? A.x[1] : A.x[0]) + roff : nullptr, (p ? A.out[1] : A.out[0]) + roff,
+                                 vh, i, (float)A.a, acc);
+        return;
+    } else if constexpr (HAS_X) {
         Spinor<P>::load((p ? A.x[1] : A.x[0]) + roff, vh, i, o);
 #pragma unroll
         for (int s = 0; s < 4; ++s)

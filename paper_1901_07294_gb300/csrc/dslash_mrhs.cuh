@@ -72,12 +72,27 @@ __device__ __forceinline__ void tile_get(const typename LinkTile<T>::V *lk, cpx<
         for (int c = 0; c < 3; ++c) U[a][c] = {r[6 * a + 2 * c], r[6 * a + 2 * c + 1]};
 }
 
+// hop_dir with the link from the shared-memory tile; for 16-bit storage the
+// terms are weighted by the neighbour's scale times wt, as in hop_dir.
 template <int P, int MU, int S, bool FWD>
 __device__ __forceinline__ void hop_dir_smem(const char *in, int vh, int nb,
                                              const typename LinkTile<typename Prec<P>::real>::V *lk, bool neg,
-                                             cpx<typename Prec<P>::real> (&acc)[4][3])
+                                             cpx<typename Prec<P>::real> (&acc)[4][3], const float wt = 1.0f)
 {
     using T = typename Prec<P>::real;
+    if constexpr (Prec<P>::scaled) {
+        unsigned u[12];
+        const float sc = Spinor<P>::load_words(in, vh, nb, u);
+        cpx<float> h0[3], h1[3];
+        project_words<P, MU, S>(u, h0, h1);
+        cpx<float> U[3][3];
+        tile_get<float>(lk, U);
+        cpx<float> w0[3], w1[3];
+        su3_mul<FWD>(U, h0, w0);
+        su3_mul<FWD>(U, h1, w1);
+        accumulate_f<MU, S>(acc, w0, w1, (neg ? -sc : sc) * wt);
+        return;
+    }
     T psi[24];
     Spinor<P>::load(in, vh, nb, psi);
     cpx<T> h0[3], h1[3];
@@ -103,6 +118,11 @@ __device__ __forceinline__ void mrhs_store(const HopArgs &A, int p, int i, size_
                                            const cpx<typename Prec<P>::real> (&acc)[4][3])
 {
     using T = typename Prec<P>::real;
+    if constexpr (Prec<P>::scaled) {   // acc already carries b
+        store_weighted<P, HAS_X>(HAS_X ? (p ? A.x[1] : A.x[0]) + roff : nullptr, (p ? A.out[1] : A.out[0]) + roff,
+                                 A.vh, i, (float)A.a, acc);
+        return;
+    }
     const T a = (T)A.a, b = (T)A.b;
     T o[24];
     if constexpr (HAS_X) {
@@ -214,19 +234,20 @@ __global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 3) hop_mrhs_kernel(co
     for (int rhs = threadIdx.y; rhs < nrhs; rhs += blockDim.y) {
         const size_t roff = (size_t)rhs * A.rhs_stride;
         const char *in = (p ? A.in[1] : A.in[0]) + roff;
+        const float wt = Prec<P>::scaled ? (float)A.b : 1.0f;   // 16-bit: b weights the terms
         cpx<T> acc[4][3];
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc[sp][c] = {T(0), T(0)};
-        hop_dir_smem<P, 0, SB, false>(in, vh, nb[128], &lk[4][0][s], false, acc);
-        hop_dir_smem<P, 1, SB, false>(in, vh, nb[160], &lk[5][0][s], false, acc);
-        hop_dir_smem<P, 2, SB, false>(in, vh, nb[192], &lk[6][0][s], false, acc);
-        hop_dir_smem<P, 3, SB, false>(in, vh, nb[224], &lk[7][0][s], A.tneg && nb[224] > i, acc);
-        hop_dir_smem<P, 0, SF, true>(in, vh, nb[0], &lk[0][0][s], false, acc);
-        hop_dir_smem<P, 1, SF, true>(in, vh, nb[32], &lk[1][0][s], false, acc);
-        hop_dir_smem<P, 2, SF, true>(in, vh, nb[64], &lk[2][0][s], false, acc);
-        hop_dir_smem<P, 3, SF, true>(in, vh, nb[96], &lk[3][0][s], A.tneg && nb[96] < i, acc);
+        hop_dir_smem<P, 0, SB, false>(in, vh, nb[128], &lk[4][0][s], false, acc, wt);
+        hop_dir_smem<P, 1, SB, false>(in, vh, nb[160], &lk[5][0][s], false, acc, wt);
+        hop_dir_smem<P, 2, SB, false>(in, vh, nb[192], &lk[6][0][s], false, acc, wt);
+        hop_dir_smem<P, 3, SB, false>(in, vh, nb[224], &lk[7][0][s], A.tneg && nb[224] > i, acc, wt);
+        hop_dir_smem<P, 0, SF, true>(in, vh, nb[0], &lk[0][0][s], false, acc, wt);
+        hop_dir_smem<P, 1, SF, true>(in, vh, nb[32], &lk[1][0][s], false, acc, wt);
+        hop_dir_smem<P, 2, SF, true>(in, vh, nb[64], &lk[2][0][s], false, acc, wt);
+        hop_dir_smem<P, 3, SF, true>(in, vh, nb[96], &lk[3][0][s], A.tneg && nb[96] < i, acc, wt);
         mrhs_store<P, HAS_X>(A, p, i, roff, acc);
     }
 }

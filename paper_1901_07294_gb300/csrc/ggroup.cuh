@@ -106,19 +106,25 @@ __global__ void __launch_bounds__(128, P == PREC_F64 ? 1 : 6)
     for (int r = threadIdx.y; r < n; r += blockDim.y) {
         const GMember &m = T->m[T->idx[r]];
         const char *in = m.f[fi];
+        // 16-bit: the member's hop coefficient weights the terms
+        const float wt = Prec<P>::scaled && HAS_X ? (float)m.mc : 1.0f;
         cpx<T_> acc[4][3];
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
             for (int c = 0; c < 3; ++c) acc[sp][c] = {T_(0), T_(0)};
-        hop_dir_smem<P, 0, SB, false>(in, vh, nb[128], &lk[4][0][s], false, acc);
-        hop_dir_smem<P, 1, SB, false>(in, vh, nb[160], &lk[5][0][s], false, acc);
-        hop_dir_smem<P, 2, SB, false>(in, vh, nb[192], &lk[6][0][s], false, acc);
-        hop_dir_smem<P, 3, SB, false>(in, vh, nb[224], &lk[7][0][s], A.tneg && nb[224] > i, acc);
-        hop_dir_smem<P, 0, SF, true>(in, vh, nb[0], &lk[0][0][s], false, acc);
-        hop_dir_smem<P, 1, SF, true>(in, vh, nb[32], &lk[1][0][s], false, acc);
-        hop_dir_smem<P, 2, SF, true>(in, vh, nb[64], &lk[2][0][s], false, acc);
-        hop_dir_smem<P, 3, SF, true>(in, vh, nb[96], &lk[3][0][s], A.tneg && nb[96] < i, acc);
+        hop_dir_smem<P, 0, SB, false>(in, vh, nb[128], &lk[4][0][s], false, acc, wt);
+        hop_dir_smem<P, 1, SB, false>(in, vh, nb[160], &lk[5][0][s], false, acc, wt);
+        hop_dir_smem<P, 2, SB, false>(in, vh, nb[192], &lk[6][0][s], false, acc, wt);
+        hop_dir_smem<P, 3, SB, false>(in, vh, nb[224], &lk[7][0][s], A.tneg && nb[224] > i, acc, wt);
+        hop_dir_smem<P, 0, SF, true>(in, vh, nb[0], &lk[0][0][s], false, acc, wt);
+        hop_dir_smem<P, 1, SF, true>(in, vh, nb[32], &lk[1][0][s], false, acc, wt);
+        hop_dir_smem<P, 2, SF, true>(in, vh, nb[64], &lk[2][0][s], false, acc, wt);
+        hop_dir_smem<P, 3, SF, true>(in, vh, nb[96], &lk[3][0][s], A.tneg && nb[96] < i, acc, wt);
+        if constexpr (Prec<P>::scaled) {
+            store_weighted<P, HAS_X>(HAS_X ? m.f[fx] : nullptr, m.f[fo], vh, i, (float)m.ma, acc);
+            continue;
+        }
         T_ o[24];
         if constexpr (HAS_X) {
             const T_ a = (T_)m.ma, b = (T_)m.mc;

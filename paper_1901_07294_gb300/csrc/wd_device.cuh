@@ -108,6 +108,57 @@ template <> __device__ __forceinline__ void unpack16<PREC_BF16>(uint4 w, float *
     }
 }
 
+// ---- 16-bit values read straight from their 32-bit storage words ----------
+// H selects the low (0: the real part) or high (1: the imaginary part) half of
+// a word that holds two 16-bit values.  h16_f32 converts one exactly; h16_add
+// and h16_sub take one operand as stored: sm_100 and later have FP32 additions
+// with a 16-bit operand (exact widening, one rounding), so x + y and x - y
+// cost one instruction where a conversion and an addition took two, with the
+// same result bit for bit.
+template <int P, int H> __device__ __forceinline__ float h16_f32(unsigned w)
+{
+    if constexpr (P == PREC_BF16) return __uint_as_float(H ? (w & 0xffff0000u) : (w << 16));
+    else {
+        float r;
+        if constexpr (H) asm("{.reg .b16 l, h; mov.b32 {l, h}, %1; cvt.f32.f16 %0, h;}" : "=f"(r) : "r"(w));
+        else asm("{.reg .b16 l, h; mov.b32 {l, h}, %1; cvt.f32.f16 %0, l;}" : "=f"(r) : "r"(w));
+        return r;
+    }
+}
+// value(H of w) + c
+template <int P, int H> __device__ __forceinline__ float h16_add(unsigned w, float c)
+{
+    float r;
+    if constexpr (P == PREC_BF16) {
+        if constexpr (H) asm("{.reg .b16 l, h; mov.b32 {l, h}, %1; add.rn.f32.bf16 %0, h, %2;}" : "=f"(r) : "r"(w), "f"(c));
+        else asm("{.reg .b16 l, h; mov.b32 {l, h}, %1; add.rn.f32.bf16 %0, l, %2;}" : "=f"(r) : "r"(w), "f"(c));
+    } else {
+        if constexpr (H) asm("{.reg .b16 l, h; mov.b32 {l, h}, %1; add.rn.f32.f16 %0, h, %2;}" : "=f"(r) : "r"(w), "f"(c));
+        else asm("{.reg .b16 l, h; mov.b32 {l, h}, %1; add.rn.f32.f16 %0, l, %2;}" : "=f"(r) : "r"(w), "f"(c));
+    }
+    return r;
+}
+// value(H of w) - c
+template <int P, int H> __device__ __forceinline__ float h16_sub(unsigned w, float c)
+{
+    float r;
+    if constexpr (P == PREC_BF16) {
+        if constexpr (H) asm("{.reg .b16 l, h; mov.b32 {l, h}, %1; sub.rn.f32.bf16 %0, h, %2;}" : "=f"(r) : "r"(w), "f"(c));
+        else asm("{.reg .b16 l, h; mov.b32 {l, h}, %1; sub.rn.f32.bf16 %0, l, %2;}" : "=f"(r) : "r"(w), "f"(c));
+    } else {
+        if constexpr (H) asm("{.reg .b16 l, h; mov.b32 {l, h}, %1; sub.rn.f32.f16 %0, h, %2;}" : "=f"(r) : "r"(w), "f"(c));
+        else asm("{.reg .b16 l, h; mov.b32 {l, h}, %1; sub.rn.f32.f16 %0, l, %2;}" : "=f"(r) : "r"(w), "f"(c));
+    }
+    return r;
+}
+// u + SIGMA v for u = half HU of wu and v = half HV of wv (SIGMA = +1 or -1):
+// the widened operand is the one the instruction cannot take as stored.
+template <int P, int HU, int HV, int SIGMA> __device__ __forceinline__ float h16_pm(unsigned wu, unsigned wv)
+{
+    if constexpr (SIGMA > 0) return h16_add<P, HV>(wv, h16_f32<P, HU>(wu));
+    else return h16_sub<P, HU>(wu, h16_f32<P, HV>(wv));
+}
+
 template <int P> __device__ __forceinline__ uint4 pack16(const typename Prec<P>::real *r, float inv_scale);
 template <> __device__ __forceinline__ uint4 pack16<PREC_F64>(const double *r, float)
 {
@@ -166,6 +217,20 @@ template <int P> struct Spinor {
         for (int k = 0; k < nplane; ++k) {
             uint4 w = ldg16(f + ((size_t)k * vh + i) * 16);
             unpack16<P>(w, v + k * Prec<P>::per16, 1.0f);
+        }
+        return s;
+    }
+
+    // 16-bit types: the twelve storage words (spin s, colour c in word 3s+c,
+    // real part low) and the per-site scale.
+    __device__ static __forceinline__ float load_words(const char *f, int vh, int i, unsigned (&u)[12])
+    {
+        static_assert(Prec<P>::scaled, "16-bit storage only");
+        const float s = __ldg(reinterpret_cast<const float *>(f + (size_t)nplane * vh * 16) + i);
+#pragma unroll
+        for (int k = 0; k < nplane; ++k) {
+            const uint4 w = ldg16(f + ((size_t)k * vh + i) * 16);
+            u[4 * k] = w.x; u[4 * k + 1] = w.y; u[4 * k + 2] = w.z; u[4 * k + 3] = w.w;
         }
         return s;
     }
