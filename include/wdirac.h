@@ -33,6 +33,9 @@
  *     WD_F16, WD_BF16 : 3 planes of 8 halves, then one plane of FP32
  *               per-site scales (stored value = real / scale, scale =
  *               max |real| over the site's 24 reals).
+ *     WD_DF  : 12 planes of float4 (hi0, lo0, hi1, lo1): each real is the
+ *               unevaluated sum hi + lo of two FP32 numbers with
+ *               hi = RN(hi + lo), 48 significand bits.
  * A full field is the even half followed by the odd half.  nrhs > 1 means
  * nrhs fields stored one after another.
  *
@@ -66,7 +69,9 @@ typedef enum {
     WD_EBUSY = -7        /* result not ready yet */
 } wd_status;
 
-typedef enum { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2, WD_BF16 = 3 } wd_prec;   /* storage precision */
+/* storage precision; WD_DF (double-word FP32) is a field and operator
+ * format, not a solver inner precision or a halo format */
+typedef enum { WD_F64 = 0, WD_F32 = 1, WD_F16 = 2, WD_BF16 = 3, WD_DF = 4 } wd_prec;
 typedef enum { WD_RECON_18 = 18, WD_RECON_12 = 12 } wd_recon;               /* reals stored per link */
 typedef enum { WD_EVEN = 0, WD_ODD = 1 } wd_parity;
 typedef enum { WD_SITES_FULL = 0, WD_SITES_EVEN = 1, WD_SITES_ODD = 2 } wd_sites;
@@ -147,7 +152,10 @@ int wd_gauge_destroy(wd_gauge *g);
  * fields).  WD_F64 computes in FP64 on FP64 links; WD_F32, WD_F16 and
  * WD_BF16 compute in FP32 on links stored in the field's precision, except
  * that WD_BF16 fields use FP16 links (link entries are bounded by 1, so FP16's
- * 3 extra mantissa bits cost no range).  out must not alias in.
+ * 3 extra mantissa bits cost no range).  WD_DF computes in double-word FP32
+ * on double-word links (errors of order 2^-48 times the magnitudes of the
+ * terms, FP32 instructions only: on a part whose FP64 rate is 1/64 of its
+ * FP32 rate it replaces FP64 where 48 bits suffice).  out must not alias in.
  * Flop count: 1320 per site for H (Eq. (1): 8 directions of spin projection,
  * SU(3) x half-spinor and reconstruction).
  */
@@ -270,7 +278,7 @@ int wd_convert(wd_ctx *ctx, const int dims[4], int sites, int prec_out, void *ou
  * such lattice) are rejected with WD_EINVAL.  No cudaMalloc/cudaFree or other
  * allocating call is made.  The first call on a device (and the first after
  * its context was reset) looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls
+ * device current (a host-side lookup, made once per device).  All calls
  * share the one array: calls that overlap on the GPU (other streams, other
  * threads) race and give wrong results.  Results equal wd_norm2's up to FP64
  * summation order.  `result` is device memory. */
@@ -390,7 +398,7 @@ int wd_stream_mul(wd_ctx *ctx, int kind, size_t n, const double *x, const double
 typedef struct {
     int inner_prec;    /* wd_prec of the inner operator and vectors */
     int inner_recon;   /* 18 or 12: links of the inner operator */
-    int outer_recon;   /* 18 or 12: links of the FP64 operator */
+    int outer_recon;   /* 18 or 12: links of the reliable updates' operator */
     int reliable;      /* 1 reliable updates, 0 iterative refinement */
     double delta;      /* see above; ignored for inner_prec = WD_F64 */
     int maxiter;       /* limit on inner iterations */
@@ -399,6 +407,13 @@ typedef struct {
                           loop runs iterations (CG scalars on the device) until a reliable
                           update is due, or 32 of them; the host does the FP64 updates
                           between launches */
+    int outer_prec;    /* WD_F64 (0) or WD_DF: arithmetic of the operator that recomputes
+                          the true residual at a reliable update (mixed precision only;
+                          ignored for inner_prec = WD_F64).  x, b, the residual and all
+                          inner products stay FP64.  WD_DF applies A in double-word FP32
+                          (errors of order 2^-48 |A| |x|), about 3 times faster than FP64
+                          on a part whose FP64 rate is 1/64 of its FP32 rate; it suits
+                          tolerances down to about 1e-12 (|x| / |b| <= 10^2). */
 } wd_cg_opts;
 
 typedef struct {

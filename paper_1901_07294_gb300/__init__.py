@@ -18,8 +18,8 @@ import threading
 
 from . import _build
 
-F64, F32, F16, BF16 = 0, 1, 2, 3
-PREC_NAMES = {F64: "f64", F32: "f32", F16: "f16", BF16: "bf16"}
+F64, F32, F16, BF16, DF = 0, 1, 2, 3, 4   # DF: double-word FP32 (hi + lo)
+PREC_NAMES = {F64: "f64", F32: "f32", F16: "f16", BF16: "bf16", DF: "df"}
 SITES_FULL, SITES_EVEN, SITES_ODD = 0, 1, 2
 EVEN, ODD = 0, 1
 
@@ -106,7 +106,7 @@ class TuneEntry(ctypes.Structure):
 class CgOpts(ctypes.Structure):
     """wd_cg_opts"""
     _fields_ = [("inner_prec", _ip), ("inner_recon", _ip), ("outer_recon", _ip), ("reliable", _ip),
-                ("delta", _dp), ("maxiter", _ip), ("autotune", _ip), ("use_graph", _ip)]
+                ("delta", _dp), ("maxiter", _ip), ("autotune", _ip), ("use_graph", _ip), ("outer_prec", _ip)]
 
 
 class CgStats(ctypes.Structure):
@@ -323,11 +323,12 @@ def convert(ctx: Context, dims, sites: int, prec_out: int, out, prec_in: int, in
 def cg_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-10, inner_prec: int = F64,
              inner_recon: int = 18, outer_recon: int = 18, reliable: bool = True, delta: float = 0.01,
              maxiter: int = 20000, autotune: bool = False, use_graph: bool = False, stream=None,
-             check: bool = True) -> dict:
-    """Solve Mhat^dagger Mhat x = b on even half fields (FP64).  Returns the solve statistics;
-    raises WdError on failure unless check=False (then 'status' carries the code)."""
-    opts = CgOpts(int(inner_prec), int(inner_recon), int(outer_recon), int(bool(reliable)), float(delta),
-                  int(maxiter), int(bool(autotune)), int(bool(use_graph)))
+             check: bool = True, outer_prec: int = F64) -> dict:
+    """Solve Mhat^dagger Mhat x = b on even half fields (FP64).  outer_prec (F64 or DF) is the
+    arithmetic of the reliable updates' operator.  Returns the solve statistics; raises WdError
+    on failure unless check=False (then 'status' carries the code)."""
+    opts = _solve_opts(inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune, use_graph,
+                       outer_prec)
     st = CgStats()
     rc = load().cg_solve(ctx.handle, gauge.handle, float(mass), _ptr(x), _ptr(b), float(tol), ctypes.byref(opts),
                          ctypes.byref(st), _stream(stream))
@@ -341,17 +342,19 @@ def cg_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-10, 
 SOLVER_CGNE, SOLVER_BICGSTAB = 0, 1
 
 
-def _solve_opts(inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune, use_graph):
+def _solve_opts(inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune, use_graph,
+                outer_prec=F64):
     return CgOpts(int(inner_prec), int(inner_recon), int(outer_recon), int(bool(reliable)), float(delta),
-                  int(maxiter), int(bool(autotune)), int(bool(use_graph)))
+                  int(maxiter), int(bool(autotune)), int(bool(use_graph)), int(outer_prec))
 
 
 def bicgstab_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-10, inner_prec: int = F64,
                    inner_recon: int = 18, outer_recon: int = 18, reliable: bool = True, delta: float = 0.01,
-                   maxiter: int = 20000, autotune: bool = False, stream=None, check: bool = True) -> dict:
+                   maxiter: int = 20000, autotune: bool = False, stream=None, check: bool = True,
+                   outer_prec: int = F64) -> dict:
     """Solve Mhat x = b on even half fields (FP64) by BiCGStab.  Returns the solve statistics;
     raises WdError on failure unless check=False (then 'status' carries the code)."""
-    opts = _solve_opts(inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune, False)
+    opts = _solve_opts(inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune, False, outer_prec)
     st = CgStats()
     rc = load().bicgstab_solve(ctx.handle, gauge.handle, float(mass), _ptr(x), _ptr(b), float(tol),
                                ctypes.byref(opts), ctypes.byref(st), _stream(stream))
@@ -365,11 +368,12 @@ def bicgstab_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1
 def wilson_solve(ctx: Context, gauge: Gauge, mass: float, x, b, tol: float = 1e-10, solver: int = SOLVER_BICGSTAB,
                  inner_prec: int = F64, inner_recon: int = 18, outer_recon: int = 18, reliable: bool = True,
                  delta: float = 0.01, maxiter: int = 20000, autotune: bool = False, use_graph: bool = False,
-                 stream=None, check: bool = True) -> dict:
+                 stream=None, check: bool = True, outer_prec: int = F64) -> dict:
     """Solve D x = b on full fields (FP64) by even-odd reduction; solver SOLVER_BICGSTAB
     (BiCGStab on Mhat) or SOLVER_CGNE (CG on the normal equations).  Returns the solve
     statistics (true_rel_resid = |b - D x| / |b|)."""
-    opts = _solve_opts(inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune, use_graph)
+    opts = _solve_opts(inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune, use_graph,
+                       outer_prec)
     st = CgStats()
     rc = load().wilson_solve(ctx.handle, gauge.handle, float(mass), _ptr(x), _ptr(b), float(tol), int(solver),
                              ctypes.byref(opts), ctypes.byref(st), _stream(stream))
@@ -506,11 +510,10 @@ def stream_mul(ctx: Context, kind: int, n: int, x, y, z, stream=None) -> None:
 def norm2_noalloc(dims, sites: int, prec: int, x, result, stream=None) -> None:
     """result[0] = |x|^2 without any device allocation and without a context.
 
-    For callers that must not allocate (inside a global-mode graph capture of
-    another component, under a host framework that owns all device memory, or in
-    latency-critical loops).  Uses a fixed scratch array in the library; fields
-    larger than 2,097,152 sites are rejected; concurrent calls race.  The first
-    call on a device does a one-time address lookup: make it before any capture."""
+    For callers that must not allocate (under a host framework that owns all device
+    memory, or in latency-critical loops).  Uses a fixed scratch array in the library;
+    fields larger than 2,097,152 sites are rejected; concurrent calls race.  The first
+    call on a device does a one-time host-side address lookup."""
     _check(load().wd_norm2_noalloc(_dims(dims), int(sites), int(prec), _ptr(x), _ptr(result), _stream(stream)))
 
 
@@ -537,6 +540,12 @@ def tune_clear(ctx: Context) -> None:
 BATCH_SEQUENTIAL, BATCH_GRAPH, BATCH_PERSISTENT = 0, 1, 2
 
 
+def _problem_opts(p: dict, inner_default: int) -> CgOpts:
+    return _solve_opts(p.get("inner_prec", inner_default), p.get("inner_recon", 18), p.get("outer_recon", 18),
+                       p.get("reliable", True), p.get("delta", 0.01), p.get("maxiter", 20000),
+                       p.get("autotune", False), p.get("use_graph", False), p.get("outer_prec", F64))
+
+
 class SolveDesc(ctypes.Structure):
     """wd_solve_desc"""
     _fields_ = [("gauge", _vp), ("mass", _dp), ("tol", _dp), ("x_e", _vp), ("b_e", _vp), ("opts", CgOpts)]
@@ -545,13 +554,11 @@ class SolveDesc(ctypes.Structure):
 def cg_solve_batch(ctx: Context, problems: list[dict], mode: int = BATCH_SEQUENTIAL, stream=None,
                    check: bool = True) -> list[dict]:
     """Run many solves.  Each problem: dict(gauge, mass, tol, x, b, and optional cg_solve options
-    inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune)."""
+    inner_prec, inner_recon, outer_recon, reliable, delta, maxiter, autotune, outer_prec)."""
     n = len(problems)
     descs = (SolveDesc * max(n, 1))()
     for k, p in enumerate(problems):
-        o = CgOpts(int(p.get("inner_prec", F32)), int(p.get("inner_recon", 18)), int(p.get("outer_recon", 18)),
-                   int(bool(p.get("reliable", True))), float(p.get("delta", 0.01)), int(p.get("maxiter", 20000)),
-                   int(bool(p.get("autotune", False))), int(bool(p.get("use_graph", False))))
+        o = _problem_opts(p, F32)
         descs[k] = SolveDesc(p["gauge"].handle, float(p["mass"]), float(p["tol"]), _ptr(p["x"]), _ptr(p["b"]), o)
     stats = (CgStats * max(n, 1))()
     rc = load().cg_solve_batch(ctx.handle, n, descs, int(mode), stats, _stream(stream))
@@ -582,9 +589,7 @@ class RqCounters(ctypes.Structure):
 
 
 def _desc(p: dict) -> SolveDesc:
-    o = CgOpts(int(p.get("inner_prec", F16)), int(p.get("inner_recon", 18)), int(p.get("outer_recon", 18)),
-               int(bool(p.get("reliable", True))), float(p.get("delta", 0.01)), int(p.get("maxiter", 20000)),
-               int(bool(p.get("autotune", False))), int(bool(p.get("use_graph", False))))
+    o = _problem_opts(p, F16)
     return SolveDesc(p["gauge"].handle, float(p["mass"]), float(p["tol"]), _ptr(p["x"]), _ptr(p["b"]), o)
 
 

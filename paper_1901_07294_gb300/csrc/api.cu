@@ -29,9 +29,10 @@ void clear_error()
 }
 
 bool valid_prec(int prec) { return prec >= WD_F64 && prec <= WD_BF16; }
+bool valid_field_prec(int prec) { return valid_prec(prec) || prec == WD_DF; }
 bool valid_recon(int recon) { return recon == WD_RECON_18 || recon == WD_RECON_12; }
 
-static int storage_bytes(int prec) { return prec == WD_F64 ? 8 : prec == WD_F32 ? 4 : 2; }
+static int storage_bytes(int prec) { return (prec == WD_F64 || prec == WD_DF) ? 8 : prec == WD_F32 ? 4 : 2; }
 
 size_t half_field_bytes(int vh, int prec)
 {
@@ -322,7 +323,7 @@ int ctx_aux_workspace(wd_ctx *ctx, size_t bytes, char **out)
 int gauge_layout(const wd_gauge *gc, int prec, int recon, const char **out)
 {
     wd_gauge *g = const_cast<wd_gauge *>(gc);
-    if (!valid_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
+    if (!valid_field_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
     if (!valid_recon(recon)) return set_error(WD_EINVAL, "bad reconstruction %d (use 18 or 12)", recon);
     prec = link_prec(prec);   // BF16 fields use FP16 links
     std::lock_guard<std::mutex> lk(g->mu);
@@ -358,6 +359,8 @@ int gauge_layout(const wd_gauge *gc, int prec, int recon, const char **out)
     case WD_F32 * 100 + 12: WD_PACK_LINKS(PREC_F32, 12); break;
     case WD_F16 * 100 + 18: WD_PACK_LINKS(PREC_F16, 18); break;
     case WD_F16 * 100 + 12: WD_PACK_LINKS(PREC_F16, 12); break;
+    case WD_DF * 100 + 18: WD_PACK_LINKS(PREC_DF, 18); break;
+    case WD_DF * 100 + 12: WD_PACK_LINKS(PREC_DF, 12); break;
     }
 #undef WD_PACK_LINKS
     cudaError_t e = cudaGetLastError();
@@ -441,7 +444,7 @@ int wd_field_bytes(const int dims[4], int sites, int prec, int nrhs, size_t *out
     clear_error();
     Geometry g;
     WD_TRY(make_geometry(dims, g));
-    if (!valid_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
+    if (!valid_field_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
     if (nrhs < 1) return set_error(WD_EINVAL, "nrhs = %d must be >= 1", nrhs);
     if (!out) return set_error(WD_EINVAL, "out is NULL");
     size_t half = half_field_bytes(g.Vh, prec);
@@ -489,7 +492,7 @@ static int pack_common(wd_ctx *ctx, const int dims[4], int sites, int prec, cons
 {
     if (!ctx) return set_error(WD_EINVAL, "ctx is NULL");
     WD_TRY(make_geometry(dims, g));
-    if (!valid_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
+    if (!valid_field_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
     if (!a || !b) return set_error(WD_EINVAL, "NULL field pointer");
     if (!aligned16(a) || !aligned16(b)) return set_error(WD_EINVAL, "field pointers must be 16-byte aligned");
     return sites_to_map(g, sites, prec, m);
@@ -518,6 +521,7 @@ static int pack_impl(wd_ctx *ctx, const int dims[4], int sites, int prec, const 
         case WD_F32: pack_lex_kernel<PREC_F32, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
         case WD_F16: pack_lex_kernel<PREC_F16, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
         case WD_BF16: pack_lex_kernel<PREC_BF16, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
+        case WD_DF: pack_lex_kernel<PREC_DF, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
         }
         WD_CUDA_TRY(cudaGetLastError());
         return WD_OK;
@@ -529,6 +533,7 @@ static int pack_impl(wd_ctx *ctx, const int dims[4], int sites, int prec, const 
     case WD_F32: pack_spinor_kernel<PREC_F32, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
     case WD_F16: pack_spinor_kernel<PREC_F16, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
     case WD_BF16: pack_spinor_kernel<PREC_BF16, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
+    case WD_DF: pack_spinor_kernel<PREC_DF, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
     }
     WD_CUDA_TRY(cudaGetLastError());
     return WD_OK;
@@ -553,6 +558,7 @@ static int unpack_impl(wd_ctx *ctx, const int dims[4], int sites, int prec, cons
         case WD_F32: unpack_lex_kernel<PREC_F32, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
         case WD_F16: unpack_lex_kernel<PREC_F16, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
         case WD_BF16: unpack_lex_kernel<PREC_BF16, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
+        case WD_DF: unpack_lex_kernel<PREC_DF, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
         }
         WD_CUDA_TRY(cudaGetLastError());
         return WD_OK;
@@ -564,6 +570,7 @@ static int unpack_impl(wd_ctx *ctx, const int dims[4], int sites, int prec, cons
     case WD_F32: unpack_spinor_kernel<PREC_F32, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
     case WD_F16: unpack_spinor_kernel<PREC_F16, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
     case WD_BF16: unpack_spinor_kernel<PREC_BF16, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
+    case WD_DF: unpack_spinor_kernel<PREC_DF, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
     }
     WD_CUDA_TRY(cudaGetLastError());
     return WD_OK;
@@ -643,7 +650,7 @@ int wd_gauge_bytes(const wd_gauge *g, int prec, int recon, size_t *out)
 {
     clear_error();
     if (!g || !out) return set_error(WD_EINVAL, "NULL argument");
-    if (!valid_prec(prec) || !valid_recon(recon)) return set_error(WD_EINVAL, "bad precision or reconstruction");
+    if (!valid_field_prec(prec) || !valid_recon(recon)) return set_error(WD_EINVAL, "bad precision or reconstruction");
     *out = 8 * link_block_bytes(g->geo.Vh, link_prec(prec), recon);
     return WD_OK;
 }

@@ -373,10 +373,13 @@ int check_desc(const wd_solve_desc &d, int mode)
     if (!valid_prec(d.opts.inner_prec)) return set_error(WD_EINVAL, "bad inner precision");
     if (!valid_recon(d.opts.inner_recon) || !valid_recon(d.opts.outer_recon))
         return set_error(WD_EINVAL, "bad link reconstruction");
+    if (d.opts.outer_prec != WD_F64 && d.opts.outer_prec != WD_DF)
+        return set_error(WD_EINVAL, "outer precision must be WD_F64 or WD_DF");
     if (mode == WD_BATCH_PERSISTENT) {
-        if (d.opts.inner_prec == WD_F64 || d.opts.inner_recon != 18 || d.opts.outer_recon != 18 || !d.opts.reliable)
+        if (d.opts.inner_prec == WD_F64 || d.opts.inner_recon != 18 || d.opts.outer_recon != 18 || !d.opts.reliable ||
+            d.opts.outer_prec != WD_F64)
             return set_error(WD_EINVAL, "the persistent batch runs mixed-precision reliable-update CG "
-                                        "(FP32, FP16 or BF16 inner) with 18-real links only");
+                                        "(FP32, FP16 or BF16 inner) with 18-real links and FP64 updates only");
         if (!(d.opts.delta > 0.0 && d.opts.delta < 1.0)) return set_error(WD_EINVAL, "delta must be in (0, 1)");
     }
     if (mode == WD_BATCH_GRAPH && (d.opts.inner_prec == WD_F64 || !d.opts.reliable))
@@ -589,11 +592,11 @@ extern "C" int cg_solve_batch(wd_ctx *ctx, int n, const wd_solve_desc *descs, in
     DeviceGuard dg(ctx->device);
     for (int k = 0; k < n; ++k) {
         const wd_solve_desc &d = descs[k];
-        WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(d.gauge), WD_F64, d.opts.outer_recon));
+        WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(d.gauge), outer_prec_of(d.opts), d.opts.outer_recon));
         WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(d.gauge), d.opts.inner_prec, d.opts.inner_recon));
         if (d.opts.autotune && mode == WD_BATCH_GRAPH)
             for (int with_x = 0; with_x < 2; ++with_x) {
-                WD_TRY(hop_ensure_tuned(ctx, d.gauge, WD_F64, d.opts.outer_recon, 0, with_x));
+                WD_TRY(hop_ensure_tuned(ctx, d.gauge, outer_prec_of(d.opts), d.opts.outer_recon, 0, with_x));
                 WD_TRY(hop_ensure_tuned(ctx, d.gauge, d.opts.inner_prec, d.opts.inner_recon, 0, with_x));
             }
     }

@@ -21,6 +21,7 @@ static int blas_sites(const int dims[4], int sites, Geometry &g)
     case WD_F32: { constexpr int P = PREC_F32; __VA_ARGS__; } break; \
     case WD_F16: { constexpr int P = PREC_F16; __VA_ARGS__; } break; \
     case WD_BF16: { constexpr int P = PREC_BF16; __VA_ARGS__; } break; \
+    case WD_DF: { constexpr int P = PREC_DF; __VA_ARGS__; } break; \
     default: return set_error(WD_EINVAL, "bad precision %d", prec); \
     }
 
@@ -87,7 +88,7 @@ int wd_convert(wd_ctx *ctx, const int dims[4], int sites, int prec_out, void *ou
     Geometry g;
     const int n = blas_sites(dims, sites, g);
     if (n < 0) return n;
-    if (!valid_prec(prec_in)) return set_error(WD_EINVAL, "bad precision %d", prec_in);
+    if (!valid_field_prec(prec_in)) return set_error(WD_EINVAL, "bad precision %d", prec_in);
     WD_PREC_SWITCH(prec_out, {
         constexpr int PD = P;
         WD_PREC_SWITCH(prec_in, {

@@ -214,20 +214,25 @@ template <int PX, int PR> struct OpCgUpdate {
     __device__ __forceinline__ void finish(const double (&s)[1]) const { out[0] = s[0]; }
 };
 
-// r = b - y; returns |r|^2 (used for the true residual, FP64).
-template <int P> struct OpXmyNorm {
+// r = b - y; returns |r|^2 (used for the true residual, FP64; y may be a
+// double-word field, widened exactly to FP64 first).
+template <int P, int PY = P> struct OpXmyNorm {
     static constexpr int NR = 1;
-    FieldRef<P> b, y, r;
+    FieldRef<P> b;
+    FieldRef<PY> y;
+    FieldRef<P> r;
     double *out;
     __device__ __forceinline__ void site(int j, double (&acc)[1]) const
     {
-        typename Prec<P>::real bv[24], yv[24];
+        using T = typename Prec<P>::real;
+        T bv[24];
+        typename Prec<PY>::real yv[24];
         b.load(j, bv);
         y.load(j, yv);
-        typename Prec<P>::real s = 0;
+        T s = 0;
 #pragma unroll
         for (int k = 0; k < 24; ++k) {
-            bv[k] -= yv[k];
+            bv[k] -= (T)yv[k];
             s = fma(bv[k], bv[k], s);
         }
         r.store(j, bv);

@@ -36,4 +36,32 @@ template <typename Op> int run_blas(const wd_ctx *ctx, const Op &op, int nsite, 
     return WD_OK;
 }
 
+// Arithmetic of the operator that recomputes the true residual at a reliable
+// update: double-word FP32 when a mixed-precision solve asks for it
+// (outer_prec = WD_DF), else FP64.  The solution, source, residual and norms
+// stay FP64 either way.
+inline int outer_prec_of(const wd_cg_opts &o)
+{
+    return (o.inner_prec != WD_F64 && o.outer_prec == WD_DF) ? WD_DF : WD_F64;
+}
+
+// r = b - A x and |r|^2 -> *out for FP64 even half fields x, b, r; ax is
+// scratch for A x.  apply(prec, in, out) applies A in precision prec;
+// blas(op) launches a BLAS operation on the caller's stream and scratch.  In
+// double-word arithmetic x is first converted into r's buffer (r is written
+// only by the last step), and A x is widened exactly to FP64 in the difference.
+template <typename Apply, typename Blas>
+int true_residual(int op, int vh, const char *x, const char *b, char *r, char *ax, double *out, Apply &&apply,
+                  Blas &&blas)
+{
+    const FieldRef<PREC_F64> fb = field_ref<PREC_F64>(b, vh), fr = field_ref<PREC_F64>(r, vh);
+    if (op == WD_DF) {
+        WD_TRY(blas(OpConvert<PREC_DF, PREC_F64>{field_ref<PREC_DF>(r, vh), field_ref<PREC_F64>(x, vh)}));
+        WD_TRY(apply(WD_DF, (const char *)r, ax));
+        return blas(OpXmyNorm<PREC_F64, PREC_DF>{fb, field_ref<PREC_DF>(ax, vh), fr, out});
+    }
+    WD_TRY(apply(WD_F64, x, ax));
+    return blas(OpXmyNorm<PREC_F64>{fb, field_ref<PREC_F64>(ax, vh), fr, out});
+}
+
 } // namespace wd

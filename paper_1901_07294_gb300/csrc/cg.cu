@@ -9,8 +9,9 @@
 // Vorst (1996), in the GPU form of Clark et al. (2010): the iterated residual,
 // search direction and operator run in a low storage precision (FP32, FP16
 // or BF16 storage, FP32 arithmetic), while FP64 holds the solution, the true
-// residual b - A x (recomputed with the FP64 operator at every reliable
-// update) and every global inner product.  An update is triggered when the
+// residual b - A x (recomputed at every reliable update with the FP64
+// operator, or with the double-word FP32 one when outer_prec = WD_DF) and
+// every global inner product.  An update is triggered when the
 // iterated residual has fallen by `delta` since the last one, and always
 // before convergence is declared; it folds the low-precision solution
 // increment into x, recomputes r in FP64, re-seeds the low-precision
@@ -74,6 +75,12 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
     auto F64 = [&](const void *p) { return field_ref<PREC_F64>(p, vh); };
     auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
     auto FX = [&](const void *p) { return field_ref<PX>(p, vh); };
+    // the reliable updates' operator (FP64 or double-word) and BLAS launcher
+    const int outer = outer_prec_of(o);
+    auto mdagm_outer = [&](int prec, const char *in, char *out) {
+        return apply_mdagm(g, prec, o.outer_recon, mass, in, out, t_o, t_e, s);
+    };
+    auto blas = [&](const auto &op) { return run_blas(ctx, op, vh, s); };
 
     WD_TRY(run_blas(ctx, OpNorm2<PREC_F64>{F64(b), d + 0}, vh, s));
     WD_TRY(read_scalars(ctx, 0, 1, s));
@@ -125,8 +132,7 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
             // x += x_lo (FP64), then the true residual with the FP64 operator
             WD_TRY(run_blas(ctx, OpAxpby<PX, PREC_F64>{FX(xs), F64(x), 1.0, 1.0}, vh, s));
             WD_CUDA_TRY(cudaMemsetAsync(xs, 0, hx, s));
-            WD_TRY(apply_mdagm(g, WD_F64, o.outer_recon, mass, x, ax, t_o, t_e, s));
-            WD_TRY(run_blas(ctx, OpXmyNorm<PREC_F64>{F64(b), F64(ax), F64(r), d + 4}, vh, s));
+            WD_TRY(true_residual(outer, vh, x, b, r, ax, d + 4, mdagm_outer, blas));
             WD_TRY(read_scalars(ctx, 4, 1, s));
             r2_true = h[4];
             ++st.reliable_updates;
@@ -155,8 +161,7 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
     }
     if (!converged && status == WD_OK) {
         WD_TRY(run_blas(ctx, OpAxpby<PX, PREC_F64>{FX(xs), F64(x), 1.0, 1.0}, vh, s));
-        WD_TRY(apply_mdagm(g, WD_F64, o.outer_recon, mass, x, ax, t_o, t_e, s));
-        WD_TRY(run_blas(ctx, OpXmyNorm<PREC_F64>{F64(b), F64(ax), F64(r), d + 4}, vh, s));
+        WD_TRY(true_residual(outer, vh, x, b, r, ax, d + 4, mdagm_outer, blas));
         WD_TRY(read_scalars(ctx, 4, 1, s));
         r2_true = h[4];
         status = set_error(WD_ENOCONV, "CG did not converge in %d iterations (relative residual %.3e)", it,
@@ -236,17 +241,20 @@ int cg_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x_e, const void 
     if (!valid_prec(opts->inner_prec)) return set_error(WD_EINVAL, "bad inner precision %d", opts->inner_prec);
     if (!valid_recon(opts->inner_recon) || !valid_recon(opts->outer_recon))
         return set_error(WD_EINVAL, "bad link reconstruction");
+    if (opts->outer_prec != WD_F64 && opts->outer_prec != WD_DF)
+        return set_error(WD_EINVAL, "outer precision must be WD_F64 or WD_DF");
     if (opts->maxiter < 1) return set_error(WD_EINVAL, "maxiter must be >= 1");
     if (opts->inner_prec != WD_F64 && !(opts->delta > 0.0 && opts->delta < 1.0))
         return set_error(WD_EINVAL, "delta must be in (0, 1)");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard dg(ctx->device);
     // build the gauge layouts up front so that no allocation happens mid-solve
-    WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), WD_F64, opts->outer_recon));
+    const int outer = outer_prec_of(*opts);
+    WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), outer, opts->outer_recon));
     WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), opts->inner_prec, opts->inner_recon));
     if (opts->autotune) {
         for (int with_x = 0; with_x < 2; ++with_x) {
-            WD_TRY(hop_ensure_tuned(ctx, g, WD_F64, opts->outer_recon, 0, with_x));
+            WD_TRY(hop_ensure_tuned(ctx, g, outer, opts->outer_recon, 0, with_x));
             WD_TRY(hop_ensure_tuned(ctx, g, opts->inner_prec, opts->inner_recon, 0, with_x));
         }
     }

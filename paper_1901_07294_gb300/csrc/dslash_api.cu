@@ -11,6 +11,7 @@ extern template cudaError_t launch_hop<PREC_F64>(const HopArgs &, int, int, int,
 extern template cudaError_t launch_hop<PREC_F32>(const HopArgs &, int, int, int, int, int, cudaStream_t);
 extern template cudaError_t launch_hop<PREC_F16>(const HopArgs &, int, int, int, int, int, cudaStream_t);
 extern template cudaError_t launch_hop<PREC_BF16>(const HopArgs &, int, int, int, int, int, cudaStream_t);
+extern template cudaError_t launch_hop<PREC_DF>(const HopArgs &, int, int, int, int, int, cudaStream_t);
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -31,6 +32,7 @@ std::string hop_key(const wd_ctx *ctx, const HopArgs &A, int prec, int recon, in
 // schedule 0.
 static std::pair<int, int> hop_default(int prec, int nrhs, int nparity)
 {
+    if (prec == WD_DF) return {96, HOP_F64_1B_VARIANT};   // double-word: three threads per site (18-real links)
     if (nrhs > 1) return {128, HOP_MRHS_VARIANT};   // shared-link kernel, 4 fields at a time
     if (prec == WD_F64) return {128, 0};
     return {64, nparity == 1 ? HOP_NA1_VARIANT : 1};
@@ -47,6 +49,7 @@ int hop_launch_cfg(const HopArgs &A, int prec, int recon, int dagger, int nrhs, 
     case WD_F32: e = launch_hop<PREC_F32>(A, recon, dagger, nrhs, threads, variant, s); break;
     case WD_F16: e = launch_hop<PREC_F16>(A, recon, dagger, nrhs, threads, variant, s); break;
     case WD_BF16: e = launch_hop<PREC_BF16>(A, recon, dagger, nrhs, threads, variant, s); break;
+    case WD_DF: e = launch_hop<PREC_DF>(A, recon, dagger, nrhs, threads, variant, s); break;
     }
     if (e != cudaSuccess) return set_error(WD_ECUDA, "hop kernel launch failed: %s", cudaGetErrorString(e));
     return WD_OK;
@@ -62,7 +65,7 @@ int hop_launch(wd_ctx *ctx, const HopArgs &A, int prec, int recon, int dagger, i
 int hop_setup(const wd_gauge *g, int prec, int recon, HopArgs &A)
 {
     if (!g) return set_error(WD_EINVAL, "gauge is NULL");
-    if (!valid_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
+    if (!valid_field_prec(prec)) return set_error(WD_EINVAL, "bad precision %d", prec);
     if (!valid_recon(recon)) return set_error(WD_EINVAL, "bad reconstruction %d", recon);
     const char *base = nullptr;
     WD_TRY(gauge_layout(g, prec, recon, &base));

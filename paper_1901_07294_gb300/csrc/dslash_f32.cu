@@ -1,5 +1,5 @@
 // Hop kernel instantiations for one storage precision (compiled as its own
-// translation unit so the four precisions build in parallel).
+// translation unit so the precisions build in parallel).
 #include "dslash_launch.cuh"
 
 namespace wd {

@@ -79,12 +79,13 @@ __device__ __forceinline__ void project(const T (&v)[24], cpx<T> (&h0)[3], cpx<T
 // and spins 2,3 are the fixed multiples of w0,w1 that the projector implies.
 // FIRST: the first direction of a site, whose terms are assigned instead of
 // added to zeros (the same values, without 24 additions).
-template <int MU, int S, bool FIRST = false, typename T>
-__device__ __forceinline__ void accumulate(cpx<T> (&acc)[4][3], const cpx<T> (&w0)[3], const cpx<T> (&w1)[3])
+// NC: colours held (3; 1 where a thread owns one colour row of the site).
+template <int MU, int S, bool FIRST = false, typename T, int NC>
+__device__ __forceinline__ void accumulate(cpx<T> (&acc)[4][NC], const cpx<T> (&w0)[NC], const cpx<T> (&w1)[NC])
 {
     if constexpr (FIRST) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < NC; ++c) {
             acc[0][c] = w0[c];
             acc[1][c] = w1[c];
             if constexpr (MU == 0) {        // spin2 = -S i w1, spin3 = -S i w0
@@ -104,7 +105,7 @@ __device__ __forceinline__ void accumulate(cpx<T> (&acc)[4][3], const cpx<T> (&w
         return;
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < NC; ++c) {
         acc[0][c].re += w0[c].re; acc[0][c].im += w0[c].im;
         acc[1][c].re += w1[c].re; acc[1][c].im += w1[c].im;
         if constexpr (MU == 0) {        // spin2 += -S i w1, spin3 += -S i w0
@@ -412,9 +413,11 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
 // registers the compiler would otherwise use to hoist loads.  PF 5 is
 // schedule 0 compiled for one block of 256 per SM: the FP64 kernel, bound by
 // the FP64 pipe rather than by latency, then needs no spill stores (at the
-// 128-register cap of two blocks it spills 200-550 bytes per thread).
+// 128-register cap of two blocks it spills 200-550 bytes per thread).  PF 6
+// is schedule 1 compiled the same way (double-word FP32, whose values take
+// two registers like FP64 ones).
 template <int P, int RECON, bool DAG, bool HAS_X, int PF, bool TOPEN = false, bool LNA = false>
-__global__ void __launch_bounds__(256, PF == 4 ? 3 : PF == 5 ? 1 : 2) hop_kernel(const HopArgs A)
+__global__ void __launch_bounds__(256, PF == 4 ? 3 : (PF == 5 || PF == 6) ? 1 : 2) hop_kernel(const HopArgs A)
 {
     int p, blk;
     if (A.nparity == 2) { p = blockIdx.x & 1; blk = blockIdx.x >> 1; }
@@ -441,6 +444,15 @@ cudaError_t launch_hop_pf(const HopArgs &A, dim3 grid, int threads, int pf, bool
         else return wd_launch(hop_kernel<P, RECON, DAG, HX, 0>, grid, dim3(threads), 0, s, A);
     default: return wd_launch(hop_kernel<P, RECON, DAG, HX, 4>, grid, dim3(threads), 0, s, A);
     }
+}
+
+// Double-word FP32 hop: schedule 0 (pf 5) or 1 (pf 6), one block of 256 per
+// SM; no open-boundary pass.
+template <int RECON, bool DAG, bool HX>
+cudaError_t launch_hop_df(const HopArgs &A, dim3 grid, int threads, int pf, cudaStream_t s)
+{
+    if (pf == 6) return wd_launch(hop_kernel<PREC_DF, RECON, DAG, HX, 6>, grid, dim3(threads), 0, s, A);
+    return wd_launch(hop_kernel<PREC_DF, RECON, DAG, HX, 5>, grid, dim3(threads), 0, s, A);
 }
 
 } // namespace wd

@@ -2,6 +2,7 @@
 // variant) to the single-field kernel or the multi right-hand-side kernel.
 #pragma once
 
+#include "dslash_df.cuh"
 #include "dslash_impl.cuh"
 #include "dslash_mrhs.cuh"
 #include "dslash_pair.cuh"
@@ -28,8 +29,9 @@ __host__ __device__ constexpr int hop_mrhs_strip(int v)
     return v == HOP_MRHS_VARIANT ? 0 : v == 5 ? 16 : v == 6 ? 8 : v == 7 ? 4 : -1;
 }
 
-// Launches the hop kernel of precision P for the runtime (recon, dagger,
-// has_x) with `threads` per block (at most 256) and memory schedule `pf`
+// Launches the hop kernel of precision P (FP64, FP32, FP16, BF16) for the
+// runtime link format, dagger and axpy term (`key`, as in launch_hop) with
+// `threads` per block (at most 256) and memory schedule `pf`
 // (pf = HOP_MRHS_VARIANT and 5..7: the shared-link multi-RHS kernel, threads/32
 // fields at a time, in the site order hop_mrhs_strip(pf) names;
 // HOP_TILE_VARIANT and HOP_2SITE_VARIANT: the kernels of dslash_variants.cuh;
@@ -39,10 +41,8 @@ __host__ __device__ constexpr int hop_mrhs_strip(int v)
 // of dslash_pair.cuh for FP16 and BF16 storage, schedules 1 and 0 for FP32,
 // FP64 and open-boundary passes).
 template <int P>
-cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int threads, int pf, cudaStream_t s)
+cudaError_t launch_hop_std(const HopArgs &A, int nrhs, int threads, int pf, int key, cudaStream_t s)
 {
-    const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
-    const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
     const int zs = A.topen ? -1 : hop_mrhs_strip(pf);   // open-boundary passes use the single-field kernel
     if (zs >= 0) {
         switch (key) {
@@ -120,6 +120,45 @@ cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int th
     case 5: return launch_hop_pf<P, 12, false, true>(B, grid, threads, pf, lna, s);
     case 6: return launch_hop_pf<P, 12, true, false>(B, grid, threads, pf, lna, s);
     default: return launch_hop_pf<P, 12, true, true>(B, grid, threads, pf, lna, s);
+    }
+}
+
+// Launches the hop kernel of precision P for the runtime (recon, dagger,
+// has_x); double-word FP32 has kernels of its own (launch_hop_df).
+template <int P>
+cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int threads, int pf, cudaStream_t s)
+{
+    const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
+    const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
+    if constexpr (P == PREC_DF) {
+        // double-word FP32: with 18-real links, variant HOP_F64_1B_VARIANT is
+        // the three-threads-per-site kernel (dslash_df.cuh); otherwise one site
+        // per thread, one block of 256 per SM, schedule 1 for variants 1 and 12
+        // and schedule 0 for the rest
+        if (A.topen) return cudaErrorInvalidValue;
+        if (recon == 18 && pf == HOP_F64_1B_VARIANT) {
+            switch (key) {
+            case 0: return launch_hop_df_row<false, false>(A, nrhs, s);
+            case 1: return launch_hop_df_row<false, true>(A, nrhs, s);
+            case 2: return launch_hop_df_row<true, false>(A, nrhs, s);
+            default: return launch_hop_df_row<true, true>(A, nrhs, s);
+            }
+        }
+        const int per = (A.vh + threads - 1) / threads;
+        const dim3 grid((unsigned)(per * A.nparity), (unsigned)nrhs);
+        const int dpf = (pf == 1 || pf == HOP_NA1_VARIANT) ? 6 : 5;
+        switch (key) {
+        case 0: return launch_hop_df<18, false, false>(A, grid, threads, dpf, s);
+        case 1: return launch_hop_df<18, false, true>(A, grid, threads, dpf, s);
+        case 2: return launch_hop_df<18, true, false>(A, grid, threads, dpf, s);
+        case 3: return launch_hop_df<18, true, true>(A, grid, threads, dpf, s);
+        case 4: return launch_hop_df<12, false, false>(A, grid, threads, dpf, s);
+        case 5: return launch_hop_df<12, false, true>(A, grid, threads, dpf, s);
+        case 6: return launch_hop_df<12, true, false>(A, grid, threads, dpf, s);
+        default: return launch_hop_df<12, true, true>(A, grid, threads, dpf, s);
+        }
+    } else {
+        return launch_hop_std<P>(A, nrhs, threads, pf, key, s);
     }
 }
 

@@ -129,7 +129,8 @@ template <int PS> int iteration(const wd_ctx *ctx, GSolve &q)
     return WD_OK;
 }
 
-// x += x_lo; r = b - A x (FP64); r_lo = r; |r|^2 -> h[7] (asynchronous).
+// x += x_lo; r = b - A x (FP64, A applied in FP64 or double-word FP32); r_lo = r;
+// |r|^2 -> h[7] (asynchronous).
 template <int PS> int reliable_update(const wd_ctx *ctx, GSolve &q)
 {
     const int vh = q.vh;
@@ -138,8 +139,12 @@ template <int PS> int reliable_update(const wd_ctx *ctx, GSolve &q)
     auto FX = [&](const void *p) { return field_ref<PREC_F32>(p, vh); };
     WD_TRY(launch(ctx, OpAxpby<PREC_F32, PREC_F64>{FX(q.xs), F64(q.x), 1.0, 1.0}, vh, q.red, q.s));
     WD_CUDA_TRY(cudaMemsetAsync(q.xs, 0, half_field_bytes(vh, WD_F32), q.s));
-    WD_TRY(mdagm(q.gauge, WD_F64, q.opts.outer_recon, q.mass, (const char *)q.x, q.ax, q.t_o, q.t_e, q.s));
-    WD_TRY(launch(ctx, OpXmyNorm<PREC_F64>{F64(q.b), F64(q.ax), F64(q.r), q.scal + 3}, vh, q.red, q.s));
+    auto apply = [&](int prec, const char *in, char *out) {
+        return mdagm(q.gauge, prec, q.opts.outer_recon, q.mass, in, out, q.t_o, q.t_e, q.s);
+    };
+    auto blas = [&](const auto &op) { return launch(ctx, op, vh, q.red, q.s); };
+    WD_TRY(true_residual(outer_prec_of(q.opts), vh, (const char *)q.x, (const char *)q.b, q.r, q.ax, q.scal + 3,
+                         apply, blas));
     WD_TRY(launch(ctx, OpConvert<PS, PREC_F64>{FS(q.rs), F64(q.r)}, vh, q.red, q.s));
     WD_CUDA_TRY(cudaMemcpyAsync(q.h + 7, q.scal + 3, sizeof(double), cudaMemcpyDeviceToHost, q.s));
     return WD_OK;

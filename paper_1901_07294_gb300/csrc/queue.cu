@@ -469,6 +469,8 @@ int check_request(const wd_solve_desc *d)
         return set_error(WD_EINVAL, "queued solves use mixed precision: inner_prec must be F32, F16 or BF16");
     if (!valid_recon(d->opts.inner_recon) || !valid_recon(d->opts.outer_recon))
         return set_error(WD_EINVAL, "bad link reconstruction");
+    if (d->opts.outer_prec != WD_F64 && d->opts.outer_prec != WD_DF)
+        return set_error(WD_EINVAL, "outer precision must be WD_F64 or WD_DF");
     if (!(d->opts.delta > 0.0 && d->opts.delta < 1.0)) return set_error(WD_EINVAL, "delta must be in (0, 1)");
     return WD_OK;
 }
@@ -509,7 +511,7 @@ int rq_submit(rq_queue *q, const wd_solve_desc *d, uint64_t *ticket)
     WD_TRY(check_request(d));
     const wd_gauge *g = d->gauge;
     // layouts are built here, on the caller's thread, so that the scheduler never allocates them
-    WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), WD_F64, d->opts.outer_recon));
+    WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), outer_prec_of(d->opts), d->opts.outer_recon));
     WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), d->opts.inner_prec, d->opts.inner_recon));
     Req *r = new (std::nothrow) Req();
     if (!r) return set_error(WD_ENOMEM, "host allocation failed");

@@ -80,6 +80,12 @@ int bicg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b
     auto F64 = [&](const void *p) { return field_ref<PREC_F64>(p, vh); };
     auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
     auto FX = [&](const void *p) { return field_ref<PX>(p, vh); };
+    // the reliable updates' operator (FP64 or double-word) and BLAS launcher
+    const int outer = outer_prec_of(o);
+    auto mhat_outer = [&](int prec, const char *in, char *out) {
+        return apply_mhat(g, prec, o.outer_recon, mass, in, out, t_o, 0, s);
+    };
+    auto blas = [&](const auto &op) { return run_blas(ctx, op, vh, s); };
 
     WD_TRY(run_blas(ctx, OpNorm2<PREC_F64>{F64(b), d + 0}, vh, s));
     WD_TRY(read_scal(ctx, 0, 1, s));
@@ -132,8 +138,7 @@ int bicg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b
         // x += x_lo (FP64), then the true residual with the FP64 operator
         WD_TRY(run_blas(ctx, OpAxpby<PX, PREC_F64>{FX(xs), F64(x), 1.0, 1.0}, vh, s));
         WD_CUDA_TRY(cudaMemsetAsync(xs, 0, hx, s));
-        WD_TRY(apply_mhat(g, WD_F64, o.outer_recon, mass, x, ax, t_o, 0, s));
-        WD_TRY(run_blas(ctx, OpXmyNorm<PREC_F64>{F64(b), F64(ax), F64(r), d + 4}, vh, s));
+        WD_TRY(true_residual(outer, vh, x, b, r, ax, d + 4, mhat_outer, blas));
         WD_TRY(read_scal(ctx, 4, 1, s));
         r2_true = h[4];
         ++st.reliable_updates;
@@ -157,8 +162,7 @@ int bicg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b
     }
     if (!converged && status == WD_OK) {
         WD_TRY(run_blas(ctx, OpAxpby<PX, PREC_F64>{FX(xs), F64(x), 1.0, 1.0}, vh, s));
-        WD_TRY(apply_mhat(g, WD_F64, o.outer_recon, mass, x, ax, t_o, 0, s));
-        WD_TRY(run_blas(ctx, OpXmyNorm<PREC_F64>{F64(b), F64(ax), F64(r), d + 4}, vh, s));
+        WD_TRY(true_residual(outer, vh, x, b, r, ax, d + 4, mhat_outer, blas));
         WD_TRY(read_scal(ctx, 4, 1, s));
         r2_true = h[4];
         status = set_error(WD_ENOCONV, "BiCGStab did not converge in %d iterations (relative residual %.3e)", it,
@@ -190,6 +194,8 @@ int check_solve_args(wd_ctx *ctx, const wd_gauge *g, const void *x, const void *
     if (!valid_prec(o->inner_prec)) return set_error(WD_EINVAL, "bad inner precision %d", o->inner_prec);
     if (!valid_recon(o->inner_recon) || !valid_recon(o->outer_recon))
         return set_error(WD_EINVAL, "bad link reconstruction");
+    if (o->outer_prec != WD_F64 && o->outer_prec != WD_DF)
+        return set_error(WD_EINVAL, "outer precision must be WD_F64 or WD_DF");
     if (o->maxiter < 1) return set_error(WD_EINVAL, "maxiter must be >= 1");
     if (o->inner_prec != WD_F64 && !(o->delta > 0.0 && o->delta < 1.0))
         return set_error(WD_EINVAL, "delta must be in (0, 1)");
@@ -198,11 +204,14 @@ int check_solve_args(wd_ctx *ctx, const wd_gauge *g, const void *x, const void *
 
 int prepare_layouts(wd_ctx *ctx, const wd_gauge *g, const wd_cg_opts &o)
 {
+    // FP64 links for the full-system steps; the reliable updates' links if double-word
     WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), WD_F64, o.outer_recon));
+    if (outer_prec_of(o) == WD_DF) WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), WD_DF, o.outer_recon));
     WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), o.inner_prec, o.inner_recon));
     if (o.autotune) {
         for (int with_x = 0; with_x < 2; ++with_x) {
             WD_TRY(hop_ensure_tuned(ctx, g, WD_F64, o.outer_recon, 0, with_x));
+            if (outer_prec_of(o) == WD_DF) WD_TRY(hop_ensure_tuned(ctx, g, WD_DF, o.outer_recon, 0, with_x));
             WD_TRY(hop_ensure_tuned(ctx, g, o.inner_prec, o.inner_recon, 0, with_x));
         }
         WD_TRY(hop_ensure_tuned(ctx, g, WD_F64, o.outer_recon, 1, 1));

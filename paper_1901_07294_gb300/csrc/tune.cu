@@ -117,7 +117,11 @@ int wd_tune_dslash(wd_ctx *ctx, const wd_gauge *g, int prec, int recon, int full
             if (zs > 0 && zs >= A.L[2]) continue;   // same as natural order
             if (v == HOP_RETIRED_VARIANT) continue;
             if ((v == HOP_SP1_VARIANT || v == HOP_SP0_VARIANT) && prec != WD_F16 && prec != WD_BF16) continue;
-            if (v == HOP_F64_1B_VARIANT && prec != WD_F64) continue;
+            if (v == HOP_F64_1B_VARIANT && prec != WD_F64 && prec != WD_DF) continue;
+            // double-word FP32: schedules 0 and 1 one block per SM, and the
+            // three-threads-per-site kernel (its own block shape: timed once)
+            if (prec == WD_DF && v != 0 && v != 1 && v != HOP_F64_1B_VARIANT) continue;
+            if (prec == WD_DF && v == HOP_F64_1B_VARIANT && recon == 18 && ti > 0) continue;
             for (int w = 0; w < 2 && rc == WD_OK; ++w) rc = hop_launch_cfg(A, prec, recon, 0, nrhs, th, v, s);
             const int reps = 10;
             cudaEventRecord(e0, s);

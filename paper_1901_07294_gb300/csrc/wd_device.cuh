@@ -8,7 +8,79 @@
 
 namespace wd {
 
-enum { PREC_F64 = 0, PREC_F32 = 1, PREC_F16 = 2, PREC_BF16 = 3 };
+enum { PREC_F64 = 0, PREC_F32 = 1, PREC_F16 = 2, PREC_BF16 = 3, PREC_DF = 4 };
+
+// ---- double-word FP32 ("double-float") arithmetic ---------------------------
+// A value is the unevaluated sum hi + lo of two FP32 numbers, |lo| <= ulp(hi)
+// after normalisation: 48 significand bits from FP32 instructions, for a part
+// whose FP64 rate is 1/64 of its FP32 rate.  The building blocks are the
+// error-free transformations of Knuth (TwoSum), Dekker (Fast2Sum) and the FMA
+// form of TwoProduct; the operations are the "sloppy" double-word sum and the
+// double-word product of Joldes, Muller and Popescu (ACM TOMS 44, 2017), and
+// fma(x, y, z) = z + x y is one step of the compensated dot product of Ogita,
+// Rump and Oishi (SIAM J. Sci. Comput. 26, 2005): the rounding errors of the
+// running sum and of the products gather in lo, which is left unnormalised
+// between steps.  Every error is of order 2^-48 times the magnitude of the
+// terms involved, which is what a residual b - A x needs.  Intrinsics keep the
+// compiler from contracting or reordering the error terms.
+struct df {
+    float hi, lo;
+    df() = default;
+    __host__ __device__ constexpr df(int v) : hi((float)v), lo(0.0f) {}
+    __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+    __device__ explicit df(float v) : hi(v), lo(0.0f) {}
+    __device__ explicit df(double v)
+    {
+        hi = __double2float_rn(v);
+        lo = __double2float_rn(v - (double)hi);
+    }
+    __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __device__ explicit operator float() const { return __fadd_rn(hi, lo); }
+};
+// s + e = a + b exactly, s = RN(a + b)
+__device__ __forceinline__ df df_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// the same for |a| >= |b| (or a = 0)
+__device__ __forceinline__ df df_fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_normalize(df x) { return df_two_sum(x.hi, x.lo); }
+__device__ __forceinline__ df operator-(df x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ df operator+(df x, df y)
+{
+    const df s = df_two_sum(x.hi, y.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ df operator-(df x, df y) { return x + (-y); }
+__device__ __forceinline__ df operator*(df x, df y)
+{
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return df_fast_two_sum(p, e);
+}
+// sign factors of the projectors (s = +1 or -1 only)
+__device__ __forceinline__ df operator*(int s, df x) { return s < 0 ? -x : x; }
+__device__ __forceinline__ df &operator+=(df &x, df y) { return x = x + y; }
+__device__ __forceinline__ df &operator-=(df &x, df y) { return x = x - y; }
+// z + x y, one compensated dot-product step (result not normalised).  The
+// global float and double fma stay visible beside this overload.
+using ::fma;
+__device__ __forceinline__ df fma(df x, df y, df z)
+{
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    const df s = df_two_sum(z.hi, p);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(e, z.lo))};
+}
 
 // Storage traits.  `real` is the compute type; `per16` reals fit in one 16-byte
 // vector; half types carry a per-site FP32 scale plane for spinors.
@@ -17,6 +89,7 @@ template <> struct Prec<PREC_F64> { using real = double; static constexpr int pe
 template <> struct Prec<PREC_F32> { using real = float;  static constexpr int per16 = 4;  static constexpr int bytes = 4; static constexpr bool scaled = false; };
 template <> struct Prec<PREC_F16> { using real = float;  static constexpr int per16 = 8;  static constexpr int bytes = 2; static constexpr bool scaled = true; };
 template <> struct Prec<PREC_BF16>{ using real = float;  static constexpr int per16 = 8;  static constexpr int bytes = 2; static constexpr bool scaled = true; };
+template <> struct Prec<PREC_DF>  { using real = df;     static constexpr int per16 = 2;  static constexpr int bytes = 8; static constexpr bool scaled = false; };
 
 template <typename T> struct cpx { T re, im; };
 
@@ -159,6 +232,12 @@ template <int P, int HU, int HV, int SIGMA> __device__ __forceinline__ float h16
     else return h16_sub<P, HU>(wu, h16_f32<P, HV>(wv));
 }
 
+template <> __device__ __forceinline__ void unpack16<PREC_DF>(uint4 w, df *r, float)
+{
+    r[0] = {__uint_as_float(w.x), __uint_as_float(w.y)};
+    r[1] = {__uint_as_float(w.z), __uint_as_float(w.w)};
+}
+
 template <int P> __device__ __forceinline__ uint4 pack16(const typename Prec<P>::real *r, float inv_scale);
 template <> __device__ __forceinline__ uint4 pack16<PREC_F64>(const double *r, float)
 {
@@ -170,6 +249,12 @@ template <> __device__ __forceinline__ uint4 pack16<PREC_F64>(const double *r, f
 template <> __device__ __forceinline__ uint4 pack16<PREC_F32>(const float *r, float)
 {
     return make_uint4(__float_as_uint(r[0]), __float_as_uint(r[1]), __float_as_uint(r[2]), __float_as_uint(r[3]));
+}
+// stored normalised: hi = RN(hi + lo)
+template <> __device__ __forceinline__ uint4 pack16<PREC_DF>(const df *r, float)
+{
+    const df a = df_normalize(r[0]), b = df_normalize(r[1]);
+    return make_uint4(__float_as_uint(a.hi), __float_as_uint(a.lo), __float_as_uint(b.hi), __float_as_uint(b.lo));
 }
 template <> __device__ __forceinline__ uint4 pack16<PREC_F16>(const float *r, float is)
 {

@@ -49,7 +49,8 @@ struct Geometry {
 
 // Validates dims (all even, >= 2, Vh < 2^31) and fills g.
 int make_geometry(const int dims[4], Geometry &g);
-bool valid_prec(int prec);
+bool valid_prec(int prec);         // WD_F64 .. WD_BF16 (solver inner precisions, halos)
+bool valid_field_prec(int prec);   // valid_prec or WD_DF (fields, operators, BLAS)
 bool valid_recon(int recon);
 
 // Bytes of one half field (one parity) in a storage precision.
