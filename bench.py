@@ -39,6 +39,7 @@ BYTES_PER_SITE = {  # compulsory bytes per output site
     ("f64", "full", 18): 960, ("f64", "full", 12): 768, ("f64", "eo", 18): 1536, ("f64", "eo", 12): 1152,
     ("f16", "full", 18): 248, ("f16", "full", 12): 200, ("f16", "eo", 18): 392, ("f16", "eo", 12): 296,
     ("bf16", "full", 18): 248, ("bf16", "full", 12): 200, ("bf16", "eo", 18): 392, ("bf16", "eo", 12): 296,
+    ("df", "full", 18): 960, ("df", "full", 12): 768, ("df", "eo", 18): 1536, ("df", "eo", 12): 1152,
 }
 FLOPS_PER_SITE = 1320
 HEADLINE_KERNEL = "hop_kernel<F32, 18, dagger=false, axpy=true>"
@@ -159,11 +160,15 @@ def compose_headline(headline: dict, detail: dict, detail_path) -> dict:
     cg = detail.get("cg") or {}
     runs = cg.get("runs", {})
     for m in ("0.1", "0.05"):
-        r64, r16 = runs.get(f"m{m}/fp64"), runs.get(f"m{m}/fp16")
+        r64, r16, rdf = runs.get(f"m{m}/fp64"), runs.get(f"m{m}/fp16"), runs.get(f"m{m}/fp16_df")
         if r64 and r16:
             sec[f"cg_24x24x24x48_m{m}"] = {"fp64_s": r64["seconds"], "fp16_s": r16["seconds"],
                                             "speedup": round(r64["seconds"] / r16["seconds"], 2),
                                             "fp16_true_rel_resid": r16["true_rel_resid"]}
+            if rdf:   # the same with double-word reliable updates
+                sec[f"cg_24x24x24x48_m{m}"].update({"fp16_df_s": rdf["seconds"],
+                                                    "speedup_df": round(r64["seconds"] / rdf["seconds"], 2),
+                                                    "fp16_df_true_rel_resid": rdf["true_rel_resid"]})
     oc = detail.get("cpu_oracle_cg")
     if oc:
         sec["cpu_oracle_cg_24x24x24x48_m0.1_s"] = oc.get("seconds")
@@ -181,6 +186,8 @@ def compose_headline(headline: dict, detail: dict, detail_path) -> dict:
     if "graph" in bt and "persistent" in bt:
         sec["batch24"] = {"graph_s": bt["graph"]["seconds"], "persistent_s": bt["persistent"]["seconds"],
                           "sequential_s": bt.get("sequential", {}).get("seconds")}
+        if "fp16_graph_df" in bt:
+            sec["batch24"]["fp16_graph_df_s"] = bt["fp16_graph_df"]["seconds"]
     if sec:
         line["secondary"] = sec
     line["detail"] = detail_path
@@ -653,7 +660,7 @@ def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, fp64_tf
         v = synth.volume(dims)
         g = wd.Gauge(ctx, dims, U)
         aos = torch.from_numpy(psi.view(np.float64).reshape(-1).copy()).cuda()
-        for prec in (wd.F32, wd.F64, wd.F16, wd.BF16):
+        for prec in (wd.F32, wd.F64, wd.F16, wd.BF16, wd.DF):
             pn = wd.PREC_NAMES[prec]
             full_in = wd.alloc_field(dims, wd.SITES_FULL, prec)
             wd.pack(ctx, dims, wd.SITES_FULL, prec, aos, full_in, stream=stream)
@@ -690,6 +697,10 @@ def _variants(wd, torch, ctx, base_dims, U_base, psi_base, stream, peak, fp64_tf
                         # FP64 is bounded by the FP64 units: the useful 1320 flops/site
                         # against the measured FP64 FMA rate
                         out[key]["frac_fp64_alu"] = round(out[key]["gflops"] / 1e3 / fp64_tflops, 4)
+                    if pn == "df":   # double-word FP32 replaces FP64 where 48 bits suffice
+                        k64 = key.replace("/df/", "/f64/")
+                        if k64 in out:
+                            out[key]["speedup_vs_f64"] = round(out[k64]["ms"] / ms, 2)
         g.close()
     return out
 
@@ -938,7 +949,7 @@ def _batch_section(wd, torch, ctx, peak):
     t0 = time.perf_counter()
     for p in probs[:1] + probs[8:9] + probs[16:17]:
         for with_x in (False, True):
-            for prec in (wd.F32, wd.F16, wd.F64):
+            for prec in (wd.F32, wd.F16, wd.F64, wd.DF):
                 wd.tune_dslash(ctx, p["gauge"], prec, 18, full=False, with_x=with_x)
     tune_s = time.perf_counter() - t0
     out = {"solves": 24, "lattices": [list(d) for d in lattices], "tol": 1e-10, "inner": "fp32 reliable-update, delta 0.01",
@@ -948,9 +959,12 @@ def _batch_section(wd, torch, ctx, peak):
     runs += [(name, mode, wd.F16) for name, mode in (("fp16_sequential", wd.BATCH_SEQUENTIAL),
                                                      ("fp16_graph", wd.BATCH_GRAPH),
                                                      ("fp16_persistent", wd.BATCH_PERSISTENT))]
+    # double-word reliable updates (the persistent kernel recomputes in FP64 only)
+    runs += [("fp16_sequential_df", wd.BATCH_SEQUENTIAL, wd.F16), ("fp16_graph_df", wd.BATCH_GRAPH, wd.F16)]
     for name, mode, inner in runs:
         for p in probs:
             p["inner_prec"] = inner
+            p["outer_prec"] = wd.DF if name.endswith("_df") else wd.F64
         wd.cg_solve_batch(ctx, probs, mode=mode)   # warm
         best = None
         for _ in range(2):
@@ -1001,10 +1015,11 @@ def _serving_section(wd, torch, ctx, peak, n_main=2000, n_sweep=150, warm=100):
         for with_x in (False, True):
             wd.tune_dslash(ctx, gauges[dims], wd.F16, 18, full=False, with_x=with_x)
             wd.tune_dslash(ctx, gauges[dims], wd.F64, 18, full=False, with_x=with_x)
+            wd.tune_dslash(ctx, gauges[dims], wd.DF, 18, full=False, with_x=with_x)
     torch.cuda.synchronize()
     pools = {d: [] for d in vols}   # free output buffers per volume
 
-    def run(rate, n, seed):
+    def run(rate, n, seed, outer):
         rng = np.random.default_rng(seed)
         q = wd.Queue(ctx, hbm_budget_bytes=48 << 30, max_slots=32)
         waits = pyqueue.Queue()
@@ -1032,7 +1047,7 @@ def _serving_section(wd, torch, ctx, peak, n_main=2000, n_sweep=150, warm=100):
                 time.sleep(max(0.0, min(0.0005, t_next - time.perf_counter())))
             x = pools[dims].pop() if pools[dims] else wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
             t = q.submit(dict(gauge=gauges[dims], mass=mass, tol=tol, b=srcs[dims][i % 2], x=x,
-                              inner_prec=wd.F16, delta=0.01))
+                              inner_prec=wd.F16, delta=0.01, outer_prec=outer))
             waits.put((t, dims, x, tol))
         waits.put(None)
         wt.join()
@@ -1059,15 +1074,20 @@ def _serving_section(wd, torch, ctx, peak, n_main=2000, n_sweep=150, warm=100):
                 "iter_model_gbs": round(it_bytes / span / 1e9, 1), "frac_hbm": round(it_bytes / span / 1e9 / peak, 4),
                 "max_true_resid_over_tol": round(max(r["cg_true_rel_resid"] / t for t, r in zip(tols, res)), 4)}
 
-    out = {"volumes": [list(v) for v in vols], "inner": "fp16 storage, fp32 compute, fp64 reliable updates",
+    out = {"volumes": [list(v) for v in vols],
+           "inner": "fp16 storage, fp32 compute; reliable updates recompute the true residual with the "
+                    "double-word FP32 operator, convergence confirmed with the FP64 one (rate_200_fp64_updates: "
+                    "every update in FP64)",
            "queue": {"hbm_budget_gb": 48, "max_slots": 32, "max_iterations_per_group_launch": 16,
                      "scheduling": "requests grouped by gauge: one shared-link hop launch per hop for a "
-                                   "group's ready members; FP64 reliable updates on the members' own streams"}}
-    results, st = run(200.0, n_main + warm, 5001)
+                                   "group's ready members; reliable updates on the members' own streams"}}
+    results, st = run(200.0, n_main + warm, 5001, wd.DF)
     out["rate_200"] = summarise(results, st, 200.0, warm)
+    results, st = run(200.0, n_main + warm, 5001, wd.F64)
+    out["rate_200_fp64_updates"] = summarise(results, st, 200.0, warm)
     out["sweep"] = []
     for rate in (10.0, 25.0, 50.0, 100.0):
-        results, st = run(rate, n_sweep, 5002 + int(rate))
+        results, st = run(rate, n_sweep, 5002 + int(rate), wd.DF)
         out["sweep"].append(summarise(results, st, rate, 10))
     for g in gauges.values():
         g.close()
@@ -1125,7 +1145,11 @@ def _solve_section(wd, torch, ctx, peak):
             ("bicgstab_fp32", wd.SOLVER_BICGSTAB, dict(inner_prec=wd.F32, reliable=True, delta=0.01)),
             ("cgne_fp64", wd.SOLVER_CGNE, dict(inner_prec=wd.F64)),
             ("cgne_fp16", wd.SOLVER_CGNE, dict(inner_prec=wd.F16, reliable=True, delta=0.01)),
-            ("cgne_fp16_graph", wd.SOLVER_CGNE, dict(inner_prec=wd.F16, reliable=True, delta=0.01, use_graph=True))]
+            ("cgne_fp16_graph", wd.SOLVER_CGNE, dict(inner_prec=wd.F16, reliable=True, delta=0.01, use_graph=True)),
+            ("bicgstab_fp16_df", wd.SOLVER_BICGSTAB, dict(inner_prec=wd.F16, reliable=True, delta=0.01,
+                                                          outer_prec=wd.DF)),
+            ("cgne_fp16_graph_df", wd.SOLVER_CGNE, dict(inner_prec=wd.F16, reliable=True, delta=0.01, use_graph=True,
+                                                        outer_prec=wd.DF))]
     for name, solver, kw in runs:
         wd.wilson_solve(ctx, g, 0.1, fx, fb, tol=1e-10, solver=solver, autotune=True, **kw)
         best = None
@@ -1153,7 +1177,9 @@ def _solve_section(wd, torch, ctx, peak):
 
 
 def _cg_section(wd, torch, ctx, peak: float):
-    """Mixed-precision vs FP64 CG on the even-odd normal equations, 24^3x48, tol 1e-10."""
+    """Mixed-precision vs FP64 CG on the even-odd normal equations, 24^3x48, tol 1e-10.  Runs named
+    *_df recompute the true residual at reliable updates with the double-word FP32 operator
+    (outer_prec = DF), confirming convergence with the FP64 one."""
     import numpy as np
 
     import synth
@@ -1171,6 +1197,10 @@ def _cg_section(wd, torch, ctx, peak: float):
             ("bf16", dict(inner_prec=wd.BF16, reliable=True, delta=0.01)),
             ("fp16_r12", dict(inner_prec=wd.F16, inner_recon=12, reliable=True, delta=0.01)),
             ("fp16_graph", dict(inner_prec=wd.F16, reliable=True, delta=0.01, use_graph=True)),
+            ("fp16_df", dict(inner_prec=wd.F16, reliable=True, delta=0.01, outer_prec=wd.DF)),
+            ("fp16_graph_df", dict(inner_prec=wd.F16, reliable=True, delta=0.01, use_graph=True, outer_prec=wd.DF)),
+            ("fp32_df", dict(inner_prec=wd.F32, reliable=True, delta=0.01, outer_prec=wd.DF)),
+            ("bf16_df", dict(inner_prec=wd.BF16, reliable=True, delta=0.01, outer_prec=wd.DF)),
             ("fp16_delta0.1", dict(inner_prec=wd.F16, reliable=True, delta=0.1)),
             ("fp16_delta0.001", dict(inner_prec=wd.F16, reliable=True, delta=0.001)),
             ("fp16_refine", dict(inner_prec=wd.F16, reliable=False, delta=1e-3))]
@@ -1204,6 +1234,8 @@ def _cg_section(wd, torch, ctx, peak: float):
         out[f"speedup_fp16_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/fp16"]["seconds"], 2)
         out[f"speedup_fp16_graph_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/fp16_graph"]["seconds"], 2)
         out[f"speedup_bf16_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/bf16"]["seconds"], 2)
+        out[f"speedup_fp16_df_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/fp16_df"]["seconds"], 2)
+        out[f"speedup_fp16_graph_df_vs_fp64_m{mass}"] = round(t64 / out["runs"][f"m{mass}/fp16_graph_df"]["seconds"], 2)
     g.close()
     return out
 
@@ -1217,13 +1249,15 @@ def run_case(argv) -> int:
         python bench.py --case --op dd --nsub 4 --halo f16 --launches 3
         python bench.py --case --op solve --prec f16 --dims 24,24,24,48 --launches 1
         python bench.py --case --op batch --prec f16 --dims 24,24,24,48 --nrhs 8 --launches 1
+        python bench.py --case --op eo --prec df --dims 24,24,24,48 --launches 3
 
     Inputs are the seeded synthetic gauge field and source of the benchmark.  With
     --threads/--variant the launch shape is pinned; otherwise the library default
     is used (no tuning, so few launches precede the profiled ones).  --op cg runs
     `launches` mixed-precision CG solves (inner precision --prec, reliable updates,
     delta 0.01, tol 1e-10, mass 0.1) on an even Gaussian source; --graph drives
-    them with CUDA graphs.  --op stream runs `launches` element-wise products of
+    them with CUDA graphs; --outer df recomputes the true residual at the reliable
+    updates (cg, solve, batch) with the double-word operator.  --op stream runs `launches` element-wise products of
     kind --kind on --n elements of N(0,1) arrays.  --op dd applies the operator
     `launches` times to the lattice split into --nsub slabs (field precision
     --prec, halos --halo).  --op solve runs `launches` full-system solves
@@ -1236,7 +1270,9 @@ def run_case(argv) -> int:
     ap.add_argument("--halo", choices=["f64", "f32", "f16"], default="f32")
     ap.add_argument("--kind", type=int, default=1)
     ap.add_argument("--n", type=int, default=1 << 24)
-    ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--prec", choices=["f64", "f32", "f16", "bf16", "df"], default="f32")
+    ap.add_argument("--outer", choices=["f64", "df"], default="f64",
+                    help="cg/solve/batch: arithmetic of the reliable updates' operator")
     ap.add_argument("--recon", type=int, default=18)
     ap.add_argument("--dims", default="32,32,32,32")
     ap.add_argument("--nrhs", type=int, default=1)
@@ -1251,7 +1287,8 @@ def run_case(argv) -> int:
     import paper_1901_07294_gb300 as wd
     import synth
 
-    prec = {"f64": wd.F64, "f32": wd.F32, "f16": wd.F16, "bf16": wd.BF16}[a.prec]
+    prec = {"f64": wd.F64, "f32": wd.F32, "f16": wd.F16, "bf16": wd.BF16, "df": wd.DF}[a.prec]
+    outer = wd.DF if a.outer == "df" else wd.F64
     dims = tuple(int(t) for t in a.dims.split(","))
     ctx = wd.Context(0)
     if a.op == "stream":
@@ -1288,7 +1325,7 @@ def run_case(argv) -> int:
             wd.pack(ctx, dims, wd.SITES_EVEN, wd.F64,
                     torch.from_numpy(b.view(np.float64).reshape(-1).copy()).cuda(), fb)
             probs.append(dict(gauge=g, mass=0.1 + 0.05 * k, tol=1e-10, b=fb, x=wd.alloc_field(dims, wd.SITES_EVEN, wd.F64),
-                              inner_prec=prec, delta=0.01))
+                              inner_prec=prec, delta=0.01, outer_prec=outer))
         for _ in range(a.launches):
             st = wd.cg_solve_batch(ctx, probs, mode=wd.BATCH_GRAPH)
         torch.cuda.synchronize()
@@ -1301,7 +1338,7 @@ def run_case(argv) -> int:
         fx = wd.alloc_field(dims, wd.SITES_FULL, wd.F64)
         for _ in range(a.launches):
             st = wd.wilson_solve(ctx, g, 0.1, fx, fb, tol=1e-10, solver=wd.SOLVER_BICGSTAB, inner_prec=prec,
-                                 inner_recon=a.recon, reliable=True, delta=0.01)
+                                 inner_recon=a.recon, reliable=True, delta=0.01, outer_prec=outer)
         torch.cuda.synchronize()
         print(f"case: solve bicgstab {a.prec} {a.dims} solves={a.launches} iters={st['iters']} "
               f"updates={st['reliable_updates']} seconds={st['seconds']:.4f} ok")
@@ -1313,7 +1350,7 @@ def run_case(argv) -> int:
         fx = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
         for _ in range(a.launches):
             st = wd.cg_solve(ctx, g, 0.1, fx, fb, tol=1e-10, inner_prec=prec, inner_recon=a.recon, reliable=True,
-                             delta=0.01, use_graph=a.graph)
+                             delta=0.01, use_graph=a.graph, outer_prec=outer)
         torch.cuda.synchronize()
         print(f"case: cg {a.prec} r{a.recon} {a.dims} solves={a.launches} iters={st['iters']} "
               f"updates={st['reliable_updates']} seconds={st['seconds']:.4f} ok")

@@ -412,13 +412,15 @@ typedef struct {
                           ignored for inner_prec = WD_F64).  x, b, the residual and all
                           inner products stay FP64.  WD_DF applies A in double-word FP32
                           (errors of order 2^-48 |A| |x|), about 3 times faster than FP64
-                          on a part whose FP64 rate is 1/64 of its FP32 rate; it suits
-                          tolerances down to about 1e-12 (|x| / |b| <= 10^2). */
+                          on a part whose FP64 rate is 1/64 of its FP32 rate.  A
+                          double-word residual that meets the target is recomputed with
+                          the FP64 operator, and only that value ends the solve (and is
+                          reported), so convergence means the same with either setting. */
 } wd_cg_opts;
 
 typedef struct {
     int iters;             /* inner iterations */
-    int reliable_updates;  /* FP64 true-residual recomputations */
+    int reliable_updates;  /* true-residual recomputations (FP64 or double-word) */
     int status;            /* wd_status of the solve */
     double true_rel_resid; /* final |b - A x| / |b|, FP64 */
     double seconds;        /* host wall time of the call */

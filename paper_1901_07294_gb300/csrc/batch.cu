@@ -592,7 +592,9 @@ extern "C" int cg_solve_batch(wd_ctx *ctx, int n, const wd_solve_desc *descs, in
     DeviceGuard dg(ctx->device);
     for (int k = 0; k < n; ++k) {
         const wd_solve_desc &d = descs[k];
-        WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(d.gauge), outer_prec_of(d.opts), d.opts.outer_recon));
+        WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(d.gauge), WD_F64, d.opts.outer_recon));
+        if (outer_prec_of(d.opts) == WD_DF)
+            WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(d.gauge), WD_DF, d.opts.outer_recon));
         WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(d.gauge), d.opts.inner_prec, d.opts.inner_recon));
         if (d.opts.autotune && mode == WD_BATCH_GRAPH)
             for (int with_x = 0; with_x < 2; ++with_x) {

@@ -10,8 +10,9 @@
 // search direction and operator run in a low storage precision (FP32, FP16
 // or BF16 storage, FP32 arithmetic), while FP64 holds the solution, the true
 // residual b - A x (recomputed at every reliable update with the FP64
-// operator, or with the double-word FP32 one when outer_prec = WD_DF) and
-// every global inner product.  An update is triggered when the
+// operator, or with the double-word FP32 one when outer_prec = WD_DF; a
+// double-word residual that meets the target is confirmed with the FP64
+// operator before the solve ends) and every global inner product.  An update is triggered when the
 // iterated residual has fallen by `delta` since the last one, and always
 // before convergence is declared; it folds the low-precision solution
 // increment into x, recomputes r in FP64, re-seeds the low-precision
@@ -136,6 +137,13 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
             WD_TRY(read_scalars(ctx, 4, 1, s));
             r2_true = h[4];
             ++st.reliable_updates;
+            if (r2_true <= stop2 && outer != WD_F64) {
+                // the double-word residual meets the target: only the FP64 one may end the solve
+                WD_TRY(true_residual(WD_F64, vh, x, b, r, ax, d + 4, mdagm_outer, blas));
+                WD_TRY(read_scalars(ctx, 4, 1, s));
+                r2_true = h[4];
+                ++st.reliable_updates;
+            }
             it_update = it;
             if (r2_true <= stop2) {
                 converged = true;
@@ -161,7 +169,7 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
     }
     if (!converged && status == WD_OK) {
         WD_TRY(run_blas(ctx, OpAxpby<PX, PREC_F64>{FX(xs), F64(x), 1.0, 1.0}, vh, s));
-        WD_TRY(true_residual(outer, vh, x, b, r, ax, d + 4, mdagm_outer, blas));
+        WD_TRY(true_residual(WD_F64, vh, x, b, r, ax, d + 4, mdagm_outer, blas));
         WD_TRY(read_scalars(ctx, 4, 1, s));
         r2_true = h[4];
         status = set_error(WD_ENOCONV, "CG did not converge in %d iterations (relative residual %.3e)", it,
@@ -250,11 +258,13 @@ int cg_solve(wd_ctx *ctx, const wd_gauge *g, double mass, void *x_e, const void 
     DeviceGuard dg(ctx->device);
     // build the gauge layouts up front so that no allocation happens mid-solve
     const int outer = outer_prec_of(*opts);
-    WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), outer, opts->outer_recon));
+    WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), WD_F64, opts->outer_recon));
+    if (outer == WD_DF) WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), WD_DF, opts->outer_recon));
     WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), opts->inner_prec, opts->inner_recon));
     if (opts->autotune) {
         for (int with_x = 0; with_x < 2; ++with_x) {
-            WD_TRY(hop_ensure_tuned(ctx, g, outer, opts->outer_recon, 0, with_x));
+            WD_TRY(hop_ensure_tuned(ctx, g, WD_F64, opts->outer_recon, 0, with_x));
+            if (outer == WD_DF) WD_TRY(hop_ensure_tuned(ctx, g, WD_DF, opts->outer_recon, 0, with_x));
             WD_TRY(hop_ensure_tuned(ctx, g, opts->inner_prec, opts->inner_recon, 0, with_x));
         }
     }

@@ -82,6 +82,9 @@ struct GSolve {
     int iters = 0, updates = 0, status = WD_OK, iters_at_update = 0;
     bool active = true;
     bool broke = false;   // the last launch stopped on a breakdown (set by gs_after_begin)
+    // an FP64 recomputation of the true residual is in flight: the double-word
+    // one said converged, and convergence is declared only on the FP64 value
+    bool confirming = false;
     double rel = 1.0;
 };
 
@@ -129,25 +132,31 @@ template <int PS> int iteration(const wd_ctx *ctx, GSolve &q)
     return WD_OK;
 }
 
-// x += x_lo; r = b - A x (FP64, A applied in FP64 or double-word FP32); r_lo = r;
-// |r|^2 -> h[7] (asynchronous).
+// r = b - A x (FP64; A applied in precision op, FP64 or double-word FP32);
+// r_lo = r; |r|^2 -> h[7] (asynchronous).
+template <int PS> int residual_reseed(const wd_ctx *ctx, GSolve &q, int op)
+{
+    const int vh = q.vh;
+    auto apply = [&](int prec, const char *in, char *out) {
+        return mdagm(q.gauge, prec, q.opts.outer_recon, q.mass, in, out, q.t_o, q.t_e, q.s);
+    };
+    auto blas = [&](const auto &o) { return launch(ctx, o, vh, q.red, q.s); };
+    WD_TRY(true_residual(op, vh, (const char *)q.x, (const char *)q.b, q.r, q.ax, q.scal + 3, apply, blas));
+    WD_TRY(launch(ctx, OpConvert<PS, PREC_F64>{field_ref<PS>(q.rs, vh), field_ref<PREC_F64>(q.r, vh)}, vh, q.red,
+                  q.s));
+    WD_CUDA_TRY(cudaMemcpyAsync(q.h + 7, q.scal + 3, sizeof(double), cudaMemcpyDeviceToHost, q.s));
+    return WD_OK;
+}
+
+// x += x_lo, then residual_reseed in the solve's outer precision.
 template <int PS> int reliable_update(const wd_ctx *ctx, GSolve &q)
 {
     const int vh = q.vh;
     auto F64 = [&](const void *p) { return field_ref<PREC_F64>(p, vh); };
-    auto FS = [&](const void *p) { return field_ref<PS>(p, vh); };
     auto FX = [&](const void *p) { return field_ref<PREC_F32>(p, vh); };
     WD_TRY(launch(ctx, OpAxpby<PREC_F32, PREC_F64>{FX(q.xs), F64(q.x), 1.0, 1.0}, vh, q.red, q.s));
     WD_CUDA_TRY(cudaMemsetAsync(q.xs, 0, half_field_bytes(vh, WD_F32), q.s));
-    auto apply = [&](int prec, const char *in, char *out) {
-        return mdagm(q.gauge, prec, q.opts.outer_recon, q.mass, in, out, q.t_o, q.t_e, q.s);
-    };
-    auto blas = [&](const auto &op) { return launch(ctx, op, vh, q.red, q.s); };
-    WD_TRY(true_residual(outer_prec_of(q.opts), vh, (const char *)q.x, (const char *)q.b, q.r, q.ax, q.scal + 3,
-                         apply, blas));
-    WD_TRY(launch(ctx, OpConvert<PS, PREC_F64>{FS(q.rs), F64(q.r)}, vh, q.red, q.s));
-    WD_CUDA_TRY(cudaMemcpyAsync(q.h + 7, q.scal + 3, sizeof(double), cudaMemcpyDeviceToHost, q.s));
-    return WD_OK;
+    return residual_reseed<PS>(ctx, q, outer_prec_of(q.opts));
 }
 
 template <int PS> int init(const wd_ctx *ctx, GSolve &q, bool with_graph)
@@ -333,12 +342,28 @@ inline int gs_after_begin(const wd_ctx *ctx, GSolve &q, bool &pending)
 // ends the solve or enqueues the restart scalars on the stream.  It does not
 // wait for them: the next launch on the same stream runs after them, and the
 // host writes the scalar buffer again only after that launch has finished.
-inline int gs_after_update(GSolve &q)
+// When a double-word residual meets the target, an FP64 recomputation is
+// enqueued instead and q.confirming set: the caller waits for the stream again
+// and calls this once more, and only the FP64 value can end the solve.
+inline int gs_after_update(const wd_ctx *ctx, GSolve &q)
 {
     const double r2t = q.h[7];
+    const bool fp64 = q.confirming || outer_prec_of(q.opts) == WD_F64;
+    q.confirming = false;
     q.updates++;
     q.rel = std::sqrt(r2t / q.b2);
     if (r2t <= q.stop2) {
+        if (!fp64) {
+            int rc;
+            switch (q.prec) {
+            case WD_F16: rc = gs_detail::residual_reseed<PREC_F16>(ctx, q, WD_F64); break;
+            case WD_BF16: rc = gs_detail::residual_reseed<PREC_BF16>(ctx, q, WD_F64); break;
+            default: rc = gs_detail::residual_reseed<PREC_F32>(ctx, q, WD_F64); break;
+            }
+            if (rc) return rc;
+            q.confirming = true;
+            return WD_OK;
+        }
         q.active = false;
         return WD_OK;
     }
@@ -370,8 +395,10 @@ inline int gs_after(const wd_ctx *ctx, GSolve &q)
     bool pending = false;
     WD_TRY(gs_after_begin(ctx, q, pending));
     if (!pending) return WD_OK;
-    WD_CUDA_TRY(cudaStreamSynchronize(q.s));
-    WD_TRY(gs_after_update(q));
+    do {
+        WD_CUDA_TRY(cudaStreamSynchronize(q.s));
+        WD_TRY(gs_after_update(ctx, q));
+    } while (q.confirming);
     WD_CUDA_TRY(cudaStreamSynchronize(q.s));
     return WD_OK;
 }

@@ -247,11 +247,12 @@ bool advance_own(rq_queue *q, Req *r)
         return true;
     }
     if (r->state == R_UPDATING) {
-        const int rc = gs_after_update(r->gs);
+        const int rc = gs_after_update(q->ctx, r->gs);
         if (rc != WD_OK || !r->gs.active || r->gs.status != WD_OK) {
             retire(q, r, rc);
             return false;
         }
+        if (r->gs.confirming) return true;   // an FP64 recomputation is in flight on its stream
         // the restart scalars are still being copied on its stream: the group's
         // next launch waits for them
         if (!r->ev && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -511,7 +512,8 @@ int rq_submit(rq_queue *q, const wd_solve_desc *d, uint64_t *ticket)
     WD_TRY(check_request(d));
     const wd_gauge *g = d->gauge;
     // layouts are built here, on the caller's thread, so that the scheduler never allocates them
-    WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), outer_prec_of(d->opts), d->opts.outer_recon));
+    WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), WD_F64, d->opts.outer_recon));
+    if (outer_prec_of(d->opts) == WD_DF) WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), WD_DF, d->opts.outer_recon));
     WD_TRY(wd_gauge_prepare(const_cast<wd_gauge *>(g), d->opts.inner_prec, d->opts.inner_recon));
     Req *r = new (std::nothrow) Req();
     if (!r) return set_error(WD_ENOMEM, "host allocation failed");

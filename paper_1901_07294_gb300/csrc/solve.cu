@@ -142,6 +142,13 @@ int bicg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b
         WD_TRY(read_scal(ctx, 4, 1, s));
         r2_true = h[4];
         ++st.reliable_updates;
+        if (r2_true <= stop2 && outer != WD_F64) {
+            // the double-word residual meets the target: only the FP64 one may end the solve
+            WD_TRY(true_residual(WD_F64, vh, x, b, r, ax, d + 4, mhat_outer, blas));
+            WD_TRY(read_scal(ctx, 4, 1, s));
+            r2_true = h[4];
+            ++st.reliable_updates;
+        }
         it_update = it;
         if (r2_true <= stop2) {
             converged = true;
@@ -162,7 +169,7 @@ int bicg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b
     }
     if (!converged && status == WD_OK) {
         WD_TRY(run_blas(ctx, OpAxpby<PX, PREC_F64>{FX(xs), F64(x), 1.0, 1.0}, vh, s));
-        WD_TRY(true_residual(outer, vh, x, b, r, ax, d + 4, mhat_outer, blas));
+        WD_TRY(true_residual(WD_F64, vh, x, b, r, ax, d + 4, mhat_outer, blas));
         WD_TRY(read_scal(ctx, 4, 1, s));
         r2_true = h[4];
         status = set_error(WD_ENOCONV, "BiCGStab did not converge in %d iterations (relative residual %.3e)", it,
