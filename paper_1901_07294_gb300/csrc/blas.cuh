@@ -144,10 +144,10 @@ template <int PA, int PB> struct OpDot {
         T re = 0, im = 0;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            re = fma(u[2 * k], (T)w[2 * k], re);
-            re = fma(u[2 * k + 1], (T)w[2 * k + 1], re);
-            im = fma(u[2 * k], (T)w[2 * k + 1], im);
-            im = fma(-u[2 * k + 1], (T)w[2 * k], im);
+            re = fma(u[2 * k], to_real<T>(w[2 * k]), re);
+            re = fma(u[2 * k + 1], to_real<T>(w[2 * k + 1]), re);
+            im = fma(u[2 * k], to_real<T>(w[2 * k + 1]), im);
+            im = fma(-u[2 * k + 1], to_real<T>(w[2 * k]), im);
         }
         acc[0] += (double)re;
         acc[1] += (double)im;
@@ -207,7 +207,7 @@ template <int PX, int PR> struct OpCgUpdate {
         x.load(j, xv);
         const TX ax = (TX)al;
 #pragma unroll
-        for (int k = 0; k < 24; ++k) xv[k] = fma(ax, (TX)pv[k], xv[k]);
+        for (int k = 0; k < 24; ++k) xv[k] = fma(ax, to_real<TX>(pv[k]), xv[k]);
         x.store(j, xv);
         acc[0] += (double)s;
     }
@@ -232,7 +232,7 @@ template <int P, int PY = P> struct OpXmyNorm {
         T s = 0;
 #pragma unroll
         for (int k = 0; k < 24; ++k) {
-            bv[k] -= (T)yv[k];
+            bv[k] -= to_real<T>(yv[k]);
             s = fma(bv[k], bv[k], s);
         }
         r.store(j, bv);
@@ -243,7 +243,8 @@ template <int P, int PY = P> struct OpXmyNorm {
 
 // ---- CG steps whose scalars live in device memory (replayable in a graph) ----
 // Scalar slots: s[0] = |r|^2 now, s[1] = pAp, s[2] = alpha, s[4] = |r|^2 of
-// the previous step, s[6] = breakdown flag.
+// the previous step, s[5] = beta for the next direction update, s[6] =
+// breakdown flag.
 
 // pAp = Re<p, Ap>;  alpha = s[0] / pAp  (alpha = 0 and the flag set on breakdown)
 template <int P> struct OpDotAlphaDev {
@@ -282,7 +283,8 @@ template <int PX, int PR> struct OpCgUpdateDev {
     }
 };
 
-// p = r + beta p with beta = s[0] / s[4]
+// p = r + beta p with beta = s[5] (= s[0] / s[4], set once per iteration by the
+// solve's control step, or by the host after a reliable update)
 template <int P> struct OpXpayDev {
     static constexpr int NR = 0;
     FieldRef<P> r, p;
@@ -290,8 +292,7 @@ template <int P> struct OpXpayDev {
     __device__ __forceinline__ void site(int j, double (&)[1]) const
     {
         using T = typename Prec<P>::real;
-        const double d = s[4];
-        const T beta = (T)(d > 0.0 ? s[0] / d : 0.0);
+        const T beta = (T)s[5];
         T rv[24], pv[24];
         r.load(j, rv);
         p.load(j, pv);
@@ -316,8 +317,13 @@ template <int PX, int PY> struct OpAxpby {
         x.load(j, xv);
         y.load(j, yv);
         const T ta = (T)a, tb = (T)b;
+        if (b == 1.0) {   // y += a x (a reliable update's x += x_lo): one operation a real
 #pragma unroll
-        for (int k = 0; k < 24; ++k) yv[k] = fma(ta, (T)xv[k], tb * yv[k]);
+            for (int k = 0; k < 24; ++k) yv[k] = fma(ta, to_real<T>(xv[k]), yv[k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 24; ++k) yv[k] = fma(ta, to_real<T>(xv[k]), tb * yv[k]);
+        }
         y.store(j, yv);
     }
     __device__ __forceinline__ void finish(const double (&)[1]) const {}
@@ -334,7 +340,7 @@ template <int PD, int PS> struct OpConvert {
         typename Prec<PD>::real dv[24];
         src.load(j, sv);
 #pragma unroll
-        for (int k = 0; k < 24; ++k) dv[k] = (typename Prec<PD>::real)sv[k];
+        for (int k = 0; k < 24; ++k) dv[k] = to_real<typename Prec<PD>::real>(sv[k]);
         dst.store(j, dv);
     }
     __device__ __forceinline__ void finish(const double (&)[1]) const {}

@@ -26,7 +26,7 @@ constexpr int GS_LAUNCH_CAP = 32;   // iterations at most per graph launch
 
 // Device scalar slots of a graph-driven solve (see also OpDotAlphaDev):
 // s[0] |r|^2, s[1] pAp, s[2] alpha, s[3] true |r|^2, s[4] previous |r|^2,
-// s[6] breakdown flag, s[8] max |r| since the last update, s[9] iterations in
+// s[5] beta = s[0] / s[4] for the next direction update, s[6] breakdown flag, s[8] max |r| since the last update, s[9] iterations in
 // this launch, s[10] iterations since the last update, s[11] iterations in
 // total, s[12] tol^2 |b|^2, s[13] delta, s[14] maxiter, s[15] GS_LAUNCH_CAP.
 constexpr int GS_NSCAL = 16;
@@ -47,6 +47,7 @@ __device__ __forceinline__ bool gs_member_step(double *s)
     s[10] = n_gap;
     s[11] = n_total;
     const bool finite = r2 == r2 && r2 < 1e300;
+    s[5] = s[4] > 0.0 ? r2 / s[4] : 0.0;   // once here, not per site in OpXpayDev
     return s[6] != 0.0 || !finite || rn < s[13] * maxr || r2 <= s[12] || n_total >= s[14] ||
            n_gap >= (double)RELIABLE_MAX_GAP || n_launch >= s[15];
 }
@@ -114,7 +115,7 @@ template <typename Op> inline int launch(const wd_ctx *ctx, const Op &op, int ns
 }
 
 // One iteration, starting with the direction update p = r + beta p
-// (beta = s[0]/s[4]; s[4] = +inf gives p = r).  A launch therefore ends right
+// (beta = s[5] = s[0]/s[4]; s[4] = +inf, s[5] = 0 give p = r).  A launch therefore ends right
 // after a residual update, and a host-side reliable update that replaces r
 // and s[0] between launches is picked up by the next direction update, as in
 // the sequential solver.
@@ -379,6 +380,10 @@ inline int gs_after_update(const wd_ctx *ctx, GSolve &q)
     if (q.broke) {
         static const double restart[3] = {INFINITY, 0.0, 0.0};   // s[4], s[5], s[6]
         WD_CUDA_TRY(cudaMemcpyAsync(q.scal + 4, restart, sizeof(restart), cudaMemcpyHostToDevice, q.s));
+    } else {
+        // beta = |r_true|^2 / |r_old|^2 (s[4] is unchanged; the same division as on the device)
+        q.h[5] = q.h[4] > 0.0 ? r2t / q.h[4] : 0.0;
+        WD_CUDA_TRY(cudaMemcpyAsync(q.scal + 5, q.h + 5, sizeof(double), cudaMemcpyHostToDevice, q.s));
     }
     q.maxr = std::sqrt(r2t);
     q.h[8] = q.maxr;   // s[8] = max |r| = the true |r|, s[10] = 0 iterations since the update

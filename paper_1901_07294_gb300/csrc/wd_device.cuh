@@ -23,20 +23,77 @@ enum { PREC_F64 = 0, PREC_F32 = 1, PREC_F16 = 2, PREC_BF16 = 3, PREC_DF = 4 };
 // between steps.  Every error is of order 2^-48 times the magnitude of the
 // terms involved, which is what a residual b - A x needs.  Intrinsics keep the
 // compiler from contracting or reordering the error terms.
+// Conversions between FP64 and FP32 issue on the FP64 pipe, so the ones
+// around the double-word arithmetic and in the FP64 BLAS work on the bit
+// patterns instead.  The rare operands they do not cover go to functions kept
+// out of line: a branch, where an inlined fallback would be predicated and
+// cost its FP64 instructions on every element.
+static __device__ __noinline__ double f32_to_f64_rare(float f) { return (double)f; }
+
+// f32_to_f64: exact widening of a float (subnormal, inf, NaN out of line)
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned u = __float_as_uint(f), e = (u >> 23) & 0xffu;
+    if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));   // +-0
+    if (e == 0u || e == 0xffu) return f32_to_f64_rare(f);
+    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e - 127u + 1023u) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
+// the FP64 route of the double -> double-word split, out of line
+static __device__ __noinline__ float2 f64_split_rare(double v)
+{
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+
 struct df {
     float hi, lo;
     df() = default;
     __host__ __device__ constexpr df(int v) : hi((float)v), lo(0.0f) {}
     __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
     __device__ explicit df(float v) : hi(v), lo(0.0f) {}
+    // hi = v rounded to 24 significant bits, to nearest even (an integer add
+    // below bit 29 of the pattern, whose carry moves into the exponent: the
+    // FP32 rounding of v), lo = v - hi, a signed remainder of at most 28 bits
+    // rounded to 24 (|lo| <=
+    // ulp(hi)/2, error <= 2^-24 |lo| <= 2^-48 |v|); integer operations and one
+    // integer-to-float conversion while both parts are normal FP32 numbers
+    // (2^-74 <= |v| < 2^126), and for +-0; otherwise (tiny, huge, inf, NaN)
+    // hi = RN(v), lo = RN(v - hi) in FP64, out of line.
     __device__ explicit df(double v)
     {
-        hi = __double2float_rn(v);
-        lo = __double2float_rn(v - (double)hi);
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+        if ((b << 1) == 0ull) {   // +-0
+            hi = __uint_as_float((unsigned)(b >> 32));
+            lo = 0.0f;
+        } else if (e >= 949u && e <= 1148u) {
+            const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+            const unsigned long long r = (b + 0x0fffffffull + ((b >> 29) & 1ull)) & ~0x1fffffffull;
+            const unsigned er = (unsigned)(r >> 52) & 0x7ffu;
+            hi = __uint_as_float(sign | ((er - 896u) << 23) | ((unsigned)(r >> 29) & 0x7fffffu));
+            // |v| - |hi| in units of 2^(e - 1075), the last significand bit of v
+            const int d = (int)(long long)((b & 0x7fffffffffffffffull) - (r & 0x7fffffffffffffffull));
+            // as a float its exponent field is 127 + log2|d|; adding e - 1075
+            // (>= -126 here) keeps it a normal number
+            lo = d ? __uint_as_float((__float_as_uint(__int2float_rn(d)) + ((e - 1075u) << 23)) ^ sign) : 0.0f;
+        } else {
+            const float2 t = f64_split_rare(v);
+            hi = t.x;
+            lo = t.y;
+        }
     }
-    __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __device__ explicit operator double() const { return f32_to_f64(hi) + f32_to_f64(lo); }
     __device__ explicit operator float() const { return __fadd_rn(hi, lo); }
 };
+// Value conversion between compute types: float -> double by bit pattern,
+// everything else as a cast.
+template <typename To, typename From> __device__ __forceinline__ To to_real(From v) { return (To)v; }
+template <> __device__ __forceinline__ double to_real<double, float>(float v) { return f32_to_f64(v); }
+
 // s + e = a + b exactly, s = RN(a + b)
 __device__ __forceinline__ df df_two_sum(float a, float b)
 {
