@@ -412,10 +412,12 @@ typedef struct {
                           ignored for inner_prec = WD_F64).  x, b, the residual and all
                           inner products stay FP64.  WD_DF applies A in double-word FP32
                           (errors of order 2^-48 |A| |x|), about 3 times faster than FP64
-                          on a part whose FP64 rate is 1/64 of its FP32 rate.  A
-                          double-word residual that meets the target is recomputed with
-                          the FP64 operator, and only that value ends the solve (and is
-                          reported), so convergence means the same with either setting. */
+                          on a part whose FP64 rate is 1/64 of its FP32 rate.  Updates
+                          that check convergence (the iterated residual has met the
+                          target), a double-word residual that meets it, and all updates
+                          after a failed check use the FP64 operator, so only an FP64
+                          residual ends the solve (and is reported): convergence means
+                          the same with either setting. */
 } wd_cg_opts;
 
 typedef struct {

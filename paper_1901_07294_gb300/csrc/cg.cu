@@ -106,6 +106,7 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
     const double delta = PS == PREC_F64 ? 0.0 : o.delta;
     double r2 = b2, maxr = std::sqrt(b2), r2_restart = b2, r2_true = b2;
     bool converged = false;
+    bool fp64_only = false;   // set once an FP64 convergence check has failed
     int status = WD_OK;
     int it = 0, it_update = 0;
     while (it < o.maxiter) {
@@ -133,17 +134,23 @@ int cg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b, 
             // x += x_lo (FP64), then the true residual with the FP64 operator
             WD_TRY(run_blas(ctx, OpAxpby<PX, PREC_F64>{FX(xs), F64(x), 1.0, 1.0}, vh, s));
             WD_CUDA_TRY(cudaMemsetAsync(xs, 0, hx, s));
-            WD_TRY(true_residual(outer, vh, x, b, r, ax, d + 4, mdagm_outer, blas));
+            // an update that the iterated residual's convergence triggered is a
+            // convergence check: FP64 directly, as are all updates after a failed check
+            const bool check = r2_new <= stop2;
+            const int op = (check || fp64_only) ? WD_F64 : outer;
+            WD_TRY(true_residual(op, vh, x, b, r, ax, d + 4, mdagm_outer, blas));
             WD_TRY(read_scalars(ctx, 4, 1, s));
             r2_true = h[4];
             ++st.reliable_updates;
-            if (r2_true <= stop2 && outer != WD_F64) {
+            if (r2_true <= stop2 && op != WD_F64) {
                 // the double-word residual meets the target: only the FP64 one may end the solve
                 WD_TRY(true_residual(WD_F64, vh, x, b, r, ax, d + 4, mdagm_outer, blas));
                 WD_TRY(read_scalars(ctx, 4, 1, s));
                 r2_true = h[4];
                 ++st.reliable_updates;
+                if (r2_true > stop2) fp64_only = true;
             }
+            if (check && outer != WD_F64 && r2_true > stop2) fp64_only = true;
             it_update = it;
             if (r2_true <= stop2) {
                 converged = true;

@@ -86,6 +86,9 @@ struct GSolve {
     // an FP64 recomputation of the true residual is in flight: the double-word
     // one said converged, and convergence is declared only on the FP64 value
     bool confirming = false;
+    bool update_fp64 = false;   // the update in flight uses the FP64 operator
+    bool update_check = false;  // ... and the iterated residual's convergence triggered it
+    bool fp64_only = false;     // an FP64 convergence check failed: all further updates in FP64
     double rel = 1.0;
 };
 
@@ -149,7 +152,7 @@ template <int PS> int residual_reseed(const wd_ctx *ctx, GSolve &q, int op)
     return WD_OK;
 }
 
-// x += x_lo, then residual_reseed in the solve's outer precision.
+// x += x_lo, then residual_reseed in FP64 or the solve's outer precision (q.update_fp64).
 template <int PS> int reliable_update(const wd_ctx *ctx, GSolve &q)
 {
     const int vh = q.vh;
@@ -157,7 +160,7 @@ template <int PS> int reliable_update(const wd_ctx *ctx, GSolve &q)
     auto FX = [&](const void *p) { return field_ref<PREC_F32>(p, vh); };
     WD_TRY(launch(ctx, OpAxpby<PREC_F32, PREC_F64>{FX(q.xs), F64(q.x), 1.0, 1.0}, vh, q.red, q.s));
     WD_CUDA_TRY(cudaMemsetAsync(q.xs, 0, half_field_bytes(vh, WD_F32), q.s));
-    return residual_reseed<PS>(ctx, q, outer_prec_of(q.opts));
+    return residual_reseed<PS>(ctx, q, q.update_fp64 ? WD_F64 : outer_prec_of(q.opts));
 }
 
 template <int PS> int init(const wd_ctx *ctx, GSolve &q, bool with_graph)
@@ -278,6 +281,7 @@ inline int gs_setup(const wd_ctx *ctx, GSolve &q)
 // counts the iterations of a launch).
 inline void gs_start(GSolve &q, double launch_cap = (double)GS_LAUNCH_CAP)
 {
+    q.confirming = q.update_fp64 = q.update_check = q.fp64_only = false;
     q.b2 = q.h[0];
     q.stop2 = SOLVE_TARGET * SOLVE_TARGET * q.tol * q.tol * q.b2;
     q.maxr = std::sqrt(q.b2);
@@ -328,6 +332,10 @@ inline int gs_after_begin(const wd_ctx *ctx, GSolve &q, bool &pending)
           (int)q.h[10] >= RELIABLE_MAX_GAP))
         return WD_OK;
     q.iters_at_update = q.iters;
+    // an update that the iterated residual's convergence (or maxiter) triggered
+    // is a convergence check: FP64 directly, as are all updates after a failed one
+    q.update_check = r2 <= q.stop2 || q.iters >= q.opts.maxiter;
+    q.update_fp64 = q.update_check || q.fp64_only || outer_prec_of(q.opts) == WD_F64;
     int rc;
     switch (q.prec) {
     case WD_F16: rc = gs_detail::reliable_update<PREC_F16>(ctx, q); break;
@@ -349,8 +357,10 @@ inline int gs_after_begin(const wd_ctx *ctx, GSolve &q, bool &pending)
 inline int gs_after_update(const wd_ctx *ctx, GSolve &q)
 {
     const double r2t = q.h[7];
-    const bool fp64 = q.confirming || outer_prec_of(q.opts) == WD_F64;
+    const bool fp64 = q.confirming || q.update_fp64;
+    if (outer_prec_of(q.opts) != WD_F64 && r2t > q.stop2 && (q.confirming || q.update_check)) q.fp64_only = true;
     q.confirming = false;
+    q.update_check = false;
     q.updates++;
     q.rel = std::sqrt(r2t / q.b2);
     if (r2t <= q.stop2) {

@@ -115,6 +115,7 @@ int bicg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b
     bool converged = false;
     int status = WD_OK;
     int it = 0, it_update = 0;
+    bool fp64_only = false;   // set once an FP64 convergence check has failed
     while (it < o.maxiter) {
         WD_TRY(run_blas(ctx, OpBicgP<PS>{FS(rs), FS(ps), FS(vs), d}, vh, s));
         WD_TRY(apply_mhat(g, PS, o.inner_recon, mass, ps, vs, tso, 0, s));
@@ -138,17 +139,23 @@ int bicg_run(wd_ctx *ctx, const wd_gauge *g, double mass, char *x, const char *b
         // x += x_lo (FP64), then the true residual with the FP64 operator
         WD_TRY(run_blas(ctx, OpAxpby<PX, PREC_F64>{FX(xs), F64(x), 1.0, 1.0}, vh, s));
         WD_CUDA_TRY(cudaMemsetAsync(xs, 0, hx, s));
-        WD_TRY(true_residual(outer, vh, x, b, r, ax, d + 4, mhat_outer, blas));
+        // an update that the iterated residual's convergence triggered is a
+        // convergence check: FP64 directly, as are all updates after a failed check
+        const bool check = r2 <= stop2;
+        const int op = (check || fp64_only) ? WD_F64 : outer;
+        WD_TRY(true_residual(op, vh, x, b, r, ax, d + 4, mhat_outer, blas));
         WD_TRY(read_scal(ctx, 4, 1, s));
         r2_true = h[4];
         ++st.reliable_updates;
-        if (r2_true <= stop2 && outer != WD_F64) {
+        if (r2_true <= stop2 && op != WD_F64) {
             // the double-word residual meets the target: only the FP64 one may end the solve
             WD_TRY(true_residual(WD_F64, vh, x, b, r, ax, d + 4, mhat_outer, blas));
             WD_TRY(read_scal(ctx, 4, 1, s));
             r2_true = h[4];
             ++st.reliable_updates;
+            if (r2_true > stop2) fp64_only = true;
         }
+        if (check && outer != WD_F64 && r2_true > stop2) fp64_only = true;
         it_update = it;
         if (r2_true <= stop2) {
             converged = true;

@@ -154,3 +154,17 @@ def test_queue_df_updates_same_alone_as_in_mix(ctx):
         q1.close()
         assert r["status"] == 0
         assert np.array_equal(unpack_field(ctx, dims, wd.SITES_EVEN, wd.F64, alone["x"]), xs[k]), k
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_cg_df_updates_light_mass_tight_tol(ctx, use_graph):
+    """A light mass (m = 0.02, |x| / |b| large) at tol 1e-12: the double-word residual's noise
+    is then within a few orders of the target, and the FP64 convergence checks still end the
+    solve with the oracle's residual <= tol."""
+    dims = (16, 16, 16, 32)
+    U, b, g, fb = _problem(ctx, dims, 1030, 3500)
+    fx = wd.alloc_field(dims, wd.SITES_EVEN, wd.F64)
+    st = wd.cg_solve(ctx, g, 0.02, fx, fb, tol=1e-12, inner_prec=wd.F16, delta=0.01, outer_prec=wd.DF,
+                     use_graph=use_graph, maxiter=40000)
+    rel = _rel(dims, U, 0.02, b, unpack_field(ctx, dims, wd.SITES_EVEN, wd.F64, fx))
+    assert st["status"] == 0 and rel <= 1e-12, (st, rel)
