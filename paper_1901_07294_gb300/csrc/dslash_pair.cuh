@@ -7,15 +7,17 @@
 // 70 % busy, so fewer instructions at unchanged occupancy make them faster.
 // One thread still computes one site; the pairs are the two spin components
 // that the projected form carries through each direction:
-//   (h0, h1)          the projected half spinor, from (psi_0, psi_1) and
-//                     (psi_3, psi_2) or (psi_2, psi_3), which the
-//                     half-to-float conversion writes straight into lanes;
+//   (h0, h1)          the projected half spinor, each lane one sum of two
+//                     stored values with one of them taken as stored
+//                     (project_words);
 //   (U h0, U h1)      the SU(3) product, with each link entry converted once
 //                     and copied into both lanes;
 //   (acc_0, acc_1), (acc_3, acc_2), (acc_2, acc_3)
 //                     accumulators: directions x, y add into the first lower
 //                     pair, z, t into the second (the projector pairs the
-//                     spins crosswise there), summed once at the end.
+//                     spins crosswise there), summed once at the end; each
+//                     term weighted in a paired FMA by the neighbour's scale
+//                     times the hop coefficient.
 // Per direction that is 60 paired operations in place of 120 scalar ones.
 // The FP32 format would need register moves to form the pairs (its loads
 // fill four consecutive registers of one site) and gains nothing; FP64 has no
@@ -46,54 +48,6 @@ template <int SX, int SY> __device__ __forceinline__ f2 p_addss(f2 a, f2 b)
 }
 __device__ __forceinline__ f2 p_bcast(float v) { return make_float2(v, v); }
 
-// ---- 16-bit spinor words to spin pairs ---------------------------------
-// A 16-bit spinor holds complex number 3 s + c (spin s, colour c) as one
-// 32-bit word (re in the low half, im in the high half).
-template <int P> __device__ __forceinline__ float lo16(unsigned w);
-template <int P> __device__ __forceinline__ float hi16(unsigned w);
-template <> __device__ __forceinline__ float lo16<PREC_F16>(unsigned w)
-{
-    return __low2float(*reinterpret_cast<const __half2 *>(&w));
-}
-template <> __device__ __forceinline__ float hi16<PREC_F16>(unsigned w)
-{
-    return __high2float(*reinterpret_cast<const __half2 *>(&w));
-}
-// a bfloat16 is the upper half of the float with the same value
-template <> __device__ __forceinline__ float lo16<PREC_BF16>(unsigned w) { return __uint_as_float(w << 16); }
-template <> __device__ __forceinline__ float hi16<PREC_BF16>(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
-
-// (spin a, spin b) of colour c from the 12 words of a site
-template <int P> __device__ __forceinline__ c2 spin_pair(const unsigned (&w)[12], int sa, int sb, int c)
-{
-    const unsigned a = w[3 * sa + c], b = w[3 * sb + c];
-    return c2{make_float2(lo16<P>(a), lo16<P>(b)), make_float2(hi16<P>(a), hi16<P>(b))};
-}
-
-// (h0, h1) = upper spin components of (1 + S gamma_MU) psi (chiral basis),
-// from the unscaled 16-bit words of psi.
-template <int P, int MU, int S>
-__device__ __forceinline__ void sp_project(const unsigned (&w)[12], c2 (&h)[3])
-{
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const c2 u = spin_pair<P>(w, 0, 1, c);
-        if constexpr (MU == 0) {        // h0 = p0 + S i p3, h1 = p1 + S i p2
-            const c2 l = spin_pair<P>(w, 3, 2, c);
-            h[c] = {p_adds<-S>(u.re, l.im), p_adds<S>(u.im, l.re)};
-        } else if constexpr (MU == 1) { // h0 = p0 - S p3, h1 = p1 + S p2
-            const c2 l = spin_pair<P>(w, 3, 2, c);
-            h[c] = {p_addss<-S, S>(u.re, l.re), p_addss<-S, S>(u.im, l.im)};
-        } else if constexpr (MU == 2) { // h0 = p0 + S i p2, h1 = p1 - S i p3
-            const c2 l = spin_pair<P>(w, 2, 3, c);
-            h[c] = {p_addss<-S, S>(u.re, l.im), p_addss<S, -S>(u.im, l.re)};
-        } else {                        // h0 = p0 + S p2, h1 = p1 + S p3
-            const c2 l = spin_pair<P>(w, 2, 3, c);
-            h[c] = {p_adds<S>(u.re, l.re), p_adds<S>(u.im, l.im)};
-        }
-    }
-}
-
 // (w0, w1)[r] = (U h0, U h1)[r] (FWD) or with U^dagger; U in both lanes.
 template <bool FWD>
 __device__ __forceinline__ void sp_su3(const cpx<float> (&U)[3][3], const c2 (&h)[3], c2 (&w)[3])
@@ -119,6 +73,17 @@ __device__ __forceinline__ void sp_su3(const cpx<float> (&U)[3][3], const c2 (&h
     }
 }
 
+// (h0, h1) paired from project_words: each sum takes one operand as stored
+// (sm_100's FP32 addition with a 16-bit operand), written into its lane.
+template <int P, int MU, int S>
+__device__ __forceinline__ void sp_project_words(const unsigned (&w)[12], c2 (&h)[3])
+{
+    cpx<float> h0[3], h1[3];
+    project_words<P, MU, S>(w, h0, h1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h[c] = {make_float2(h0[c].re, h1[c].re), make_float2(h0[c].im, h1[c].im)};
+}
+
 // Accumulators of the spin-paired kernel.
 struct SpAcc {
     c2 up[3];   // (acc_0, acc_1)
@@ -126,34 +91,40 @@ struct SpAcc {
     c2 l23[3];  // (acc_2, acc_3), from the z and t directions
 };
 
-// acc += (1 + S gamma_MU) applied in the projected form, w = (U h0, U h1).
+// acc += f (1 + S gamma_MU) applied in the projected form, w = (U h0, U h1):
+// the weight f (the neighbour's scale times the hop coefficient) rides on the
+// paired FMAs, lane signs in the weight pair.
+template <int SX, int SY> __device__ __forceinline__ f2 p_w(float f) { return make_float2(SX * f, SY * f); }
+
 template <int MU, int S>
-__device__ __forceinline__ void sp_accumulate(SpAcc &a, const c2 (&w)[3])
+__device__ __forceinline__ void sp_accumulate(SpAcc &a, const c2 (&w)[3], const float f)
 {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        a.up[c].re = p_add(a.up[c].re, w[c].re);
-        a.up[c].im = p_add(a.up[c].im, w[c].im);
+        a.up[c].re = p_fma(p_w<1, 1>(f), w[c].re, a.up[c].re);
+        a.up[c].im = p_fma(p_w<1, 1>(f), w[c].im, a.up[c].im);
         if constexpr (MU == 0) {        // spin3 += -S i w0, spin2 += -S i w1
-            a.l32[c].re = p_adds<S>(a.l32[c].re, w[c].im);
-            a.l32[c].im = p_adds<-S>(a.l32[c].im, w[c].re);
+            a.l32[c].re = p_fma(p_w<S, S>(f), w[c].im, a.l32[c].re);
+            a.l32[c].im = p_fma(p_w<-S, -S>(f), w[c].re, a.l32[c].im);
         } else if constexpr (MU == 1) { // spin3 += -S w0, spin2 += S w1
-            a.l32[c].re = p_addss<-S, S>(a.l32[c].re, w[c].re);
-            a.l32[c].im = p_addss<-S, S>(a.l32[c].im, w[c].im);
+            a.l32[c].re = p_fma(p_w<-S, S>(f), w[c].re, a.l32[c].re);
+            a.l32[c].im = p_fma(p_w<-S, S>(f), w[c].im, a.l32[c].im);
         } else if constexpr (MU == 2) { // spin2 += -S i w0, spin3 += S i w1
-            a.l23[c].re = p_addss<S, -S>(a.l23[c].re, w[c].im);
-            a.l23[c].im = p_addss<-S, S>(a.l23[c].im, w[c].re);
+            a.l23[c].re = p_fma(p_w<S, -S>(f), w[c].im, a.l23[c].re);
+            a.l23[c].im = p_fma(p_w<-S, S>(f), w[c].re, a.l23[c].im);
         } else {                        // spin2 += S w0, spin3 += S w1
-            a.l23[c].re = p_adds<S>(a.l23[c].re, w[c].re);
-            a.l23[c].im = p_adds<S>(a.l23[c].im, w[c].im);
+            a.l23[c].re = p_fma(p_w<S, S>(f), w[c].re, a.l23[c].re);
+            a.l23[c].im = p_fma(p_w<S, S>(f), w[c].im, a.l23[c].im);
         }
     }
 }
 
 // One direction: neighbour nb, link of site li; neg: the hop crosses an
-// antiperiodic boundary.  The neighbour's 16-bit scale multiplies U h.
+// antiperiodic boundary.  The neighbour's 16-bit scale times wt (the hop
+// coefficient) weights the accumulated terms.
 template <int P, int RECON, int MU, int S, bool FWD, bool LNA>
-__device__ __forceinline__ void sp_dir(const char *in, const char *lblk, int vh, int nb, int li, bool neg, SpAcc &acc)
+__device__ __forceinline__ void sp_dir(const char *in, const char *lblk, int vh, int nb, int li, bool neg, SpAcc &acc,
+                                       const float wt)
 {
     constexpr int NP = Spinor<P>::nplane;
     unsigned w[12];
@@ -164,18 +135,12 @@ __device__ __forceinline__ void sp_dir(const char *in, const char *lblk, int vh,
     }
     const float sc = __ldg(reinterpret_cast<const float *>(in + (size_t)NP * vh * 16) + nb);
     c2 h[3];
-    sp_project<P, MU, S>(w, h);
+    sp_project_words<P, MU, S>(w, h);
     cpx<float> U[3][3];
     Link<link_prec(P), RECON>::template load<LNA>(lblk, vh, li, U);
     c2 r[3];
     sp_su3<FWD>(U, h, r);
-    const f2 f = p_bcast(neg ? -sc : sc);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        r[c].re = p_mul(r[c].re, f);
-        r[c].im = p_mul(r[c].im, f);
-    }
-    sp_accumulate<MU, S>(acc, r);
+    sp_accumulate<MU, S>(acc, r, (neg ? -sc : sc) * wt);
 }
 
 // One output site with the spin-paired arithmetic.  PF 1: memory schedule 1
@@ -213,57 +178,47 @@ __device__ __forceinline__ void sp_site(const HopArgs &A, const int p, const int
     constexpr int SB = -SF;
     const size_t lb = A.link_blk;
 
+    const float wt = (float)A.b;   // the hop coefficient weights the accumulated terms
     SpAcc acc;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         acc.up[c] = acc.l32[c] = acc.l23[c] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     }
     if constexpr (PF == 0) {
-        sp_dir<P, RECON, 0, SF, true, LNA>(in, gf + 0 * lb, vh, xf, i, false, acc);
-        sp_dir<P, RECON, 0, SB, false, LNA>(in, gb + 0 * lb, vh, xb, xb, false, acc);
-        sp_dir<P, RECON, 1, SF, true, LNA>(in, gf + 1 * lb, vh, yf, i, false, acc);
-        sp_dir<P, RECON, 1, SB, false, LNA>(in, gb + 1 * lb, vh, yb, yb, false, acc);
-        sp_dir<P, RECON, 2, SF, true, LNA>(in, gf + 2 * lb, vh, zf, i, false, acc);
-        sp_dir<P, RECON, 2, SB, false, LNA>(in, gb + 2 * lb, vh, zb, zb, false, acc);
-        sp_dir<P, RECON, 3, SF, true, LNA>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
-        sp_dir<P, RECON, 3, SB, false, LNA>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
+        sp_dir<P, RECON, 0, SF, true, LNA>(in, gf + 0 * lb, vh, xf, i, false, acc, wt);
+        sp_dir<P, RECON, 0, SB, false, LNA>(in, gb + 0 * lb, vh, xb, xb, false, acc, wt);
+        sp_dir<P, RECON, 1, SF, true, LNA>(in, gf + 1 * lb, vh, yf, i, false, acc, wt);
+        sp_dir<P, RECON, 1, SB, false, LNA>(in, gb + 1 * lb, vh, yb, yb, false, acc, wt);
+        sp_dir<P, RECON, 2, SF, true, LNA>(in, gf + 2 * lb, vh, zf, i, false, acc, wt);
+        sp_dir<P, RECON, 2, SB, false, LNA>(in, gb + 2 * lb, vh, zb, zb, false, acc, wt);
+        sp_dir<P, RECON, 3, SF, true, LNA>(in, gf + 3 * lb, vh, tf, i, ntf, acc, wt);
+        sp_dir<P, RECON, 3, SB, false, LNA>(in, gb + 3 * lb, vh, tb, tb, ntb, acc, wt);
     } else {
         using LK = Link<link_prec(P), RECON>;
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) LK::prefetch(gf + mu * lb, vh, i);
         Spinor<P>::prefetch(in, vh, tf);
-        sp_dir<P, RECON, 0, SB, false, LNA>(in, gb + 0 * lb, vh, xb, xb, false, acc);
-        sp_dir<P, RECON, 1, SB, false, LNA>(in, gb + 1 * lb, vh, yb, yb, false, acc);
-        sp_dir<P, RECON, 2, SB, false, LNA>(in, gb + 2 * lb, vh, zb, zb, false, acc);
-        sp_dir<P, RECON, 3, SB, false, LNA>(in, gb + 3 * lb, vh, tb, tb, ntb, acc);
-        sp_dir<P, RECON, 0, SF, true, LNA>(in, gf + 0 * lb, vh, xf, i, false, acc);
-        sp_dir<P, RECON, 1, SF, true, LNA>(in, gf + 1 * lb, vh, yf, i, false, acc);
-        sp_dir<P, RECON, 2, SF, true, LNA>(in, gf + 2 * lb, vh, zf, i, false, acc);
-        sp_dir<P, RECON, 3, SF, true, LNA>(in, gf + 3 * lb, vh, tf, i, ntf, acc);
+        sp_dir<P, RECON, 0, SB, false, LNA>(in, gb + 0 * lb, vh, xb, xb, false, acc, wt);
+        sp_dir<P, RECON, 1, SB, false, LNA>(in, gb + 1 * lb, vh, yb, yb, false, acc, wt);
+        sp_dir<P, RECON, 2, SB, false, LNA>(in, gb + 2 * lb, vh, zb, zb, false, acc, wt);
+        sp_dir<P, RECON, 3, SB, false, LNA>(in, gb + 3 * lb, vh, tb, tb, ntb, acc, wt);
+        sp_dir<P, RECON, 0, SF, true, LNA>(in, gf + 0 * lb, vh, xf, i, false, acc, wt);
+        sp_dir<P, RECON, 1, SF, true, LNA>(in, gf + 1 * lb, vh, yf, i, false, acc, wt);
+        sp_dir<P, RECON, 2, SF, true, LNA>(in, gf + 2 * lb, vh, zf, i, false, acc, wt);
+        sp_dir<P, RECON, 3, SF, true, LNA>(in, gf + 3 * lb, vh, tf, i, ntf, acc, wt);
     }
 
     // the four spins: 0, 1 from the upper pair, 2 and 3 from both lower pairs
-    const float a = (float)A.a, b = (float)A.b;
-    float o[24];
-    if constexpr (HAS_X) Spinor<P>::load((p ? A.x[1] : A.x[0]) + roff, vh, i, o);
+    cpx<float> v[4][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float sre[4] = {acc.up[c].re.x, acc.up[c].re.y, acc.l23[c].re.x + acc.l32[c].re.y,
-                              acc.l23[c].re.y + acc.l32[c].re.x};
-        const float sim[4] = {acc.up[c].im.x, acc.up[c].im.y, acc.l23[c].im.x + acc.l32[c].im.y,
-                              acc.l23[c].im.y + acc.l32[c].im.x};
-#pragma unroll
-        for (int sp = 0; sp < 4; ++sp) {
-            if constexpr (HAS_X) {
-                o[6 * sp + 2 * c] = fmaf(b, sre[sp], a * o[6 * sp + 2 * c]);
-                o[6 * sp + 2 * c + 1] = fmaf(b, sim[sp], a * o[6 * sp + 2 * c + 1]);
-            } else {
-                o[6 * sp + 2 * c] = b * sre[sp];
-                o[6 * sp + 2 * c + 1] = b * sim[sp];
-            }
-        }
+        v[0][c] = {acc.up[c].re.x, acc.up[c].im.x};
+        v[1][c] = {acc.up[c].re.y, acc.up[c].im.y};
+        v[2][c] = {acc.l23[c].re.x + acc.l32[c].re.y, acc.l23[c].im.x + acc.l32[c].im.y};
+        v[3][c] = {acc.l23[c].re.y + acc.l32[c].re.x, acc.l23[c].im.y + acc.l32[c].im.x};
     }
-    Spinor<P>::store((p ? A.out[1] : A.out[0]) + roff, vh, i, o);
+    store_weighted<P, HAS_X>(HAS_X ? (p ? A.x[1] : A.x[0]) + roff : nullptr, (p ? A.out[1] : A.out[0]) + roff, vh, i,
+                             (float)A.a, v);
 }
 
 template <int P, int RECON, bool DAG, bool HAS_X, int PF, bool LNA>
