@@ -52,3 +52,41 @@ def test_bad_precision_and_nrhs_rejected():
         with pytest.raises(wd.WdError) as e:
             wd.field_bytes((4, 4, 4, 4), wd.SITES_FULL, prec, nrhs)
         assert e.value.status == wd.WD_EINVAL
+
+
+_MIRRORS = [("wd_tune_entry", "TuneEntry"), ("wd_cg_opts", "CgOpts"), ("wd_cg_stats", "CgStats"),
+            ("wd_solve_desc", "SolveDesc"), ("wd_solve_result", "SolveResult"), ("rq_counters", "RqCounters"),
+            ("wd_device_props", "DeviceProps")]
+
+
+def test_struct_mirrors_match_the_header(tmp_path):
+    """Every ctypes mirror of a C-ABI struct has the header's size and field offsets (a C
+    program compiled against include/wdirac.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "wdirac.h"', "int main(void) {"]
+    for cname, pyname in _MIRRORS:
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in getattr(wd, pyname)._fields_:
+            lines.append(f'    printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(p[0], p[1]): int(p[2]) for p in (l.split() for l in out) if len(p) == 3}
+    for cname, pyname in _MIRRORS:
+        cls = getattr(wd, pyname)
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for field, _ in cls._fields_:
+            assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
+
+
+def test_double_word_field_sizes():
+    """A double-word field holds each real as two FP32 numbers: the FP64 byte count."""
+    for sites in (wd.SITES_FULL, wd.SITES_EVEN):
+        assert wd.field_bytes((4, 6, 8, 10), sites, wd.DF) == wd.field_bytes((4, 6, 8, 10), sites, wd.F64)
