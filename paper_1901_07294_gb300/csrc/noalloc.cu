@@ -122,6 +122,7 @@ extern "C" int wd_norm2_noalloc(const int dims[4], int sites, int prec, const vo
     case WD_F32: return noalloc_norm2<PREC_F32>(x, g.Vh, (int)nsite, result, s);
     case WD_F16: return noalloc_norm2<PREC_F16>(x, g.Vh, (int)nsite, result, s);
     case WD_BF16: return noalloc_norm2<PREC_BF16>(x, g.Vh, (int)nsite, result, s);
+    case WD_DF: return noalloc_norm2<PREC_DF>(x, g.Vh, (int)nsite, result, s);
     default: return set_error(WD_EINVAL, "bad precision %d", prec);
     }
 }

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 RTOL = 1e-12   # the two entry points differ only in the FP64 summation order
 
 
-@pytest.mark.parametrize("prec", [wd.F64, wd.F32, wd.F16, wd.BF16])
+@pytest.mark.parametrize("prec", [wd.F64, wd.F32, wd.F16, wd.BF16, wd.DF])
 @pytest.mark.parametrize("dims,sites", [((8, 8, 8, 8), wd.SITES_FULL), ((4, 6, 8, 10), wd.SITES_EVEN),
                                         ((32, 32, 32, 32), wd.SITES_FULL)])
 def test_noalloc_norm_matches_context_norm_twice(prec, dims, sites):
