@@ -6,8 +6,8 @@
 // over the warps of the block, per-block partials in scratch memory, and the
 // last block to finish (atomic ticket) sums the partials the same way (thread
 // t takes partials t, t+256, ...), so the order is fixed.  The
-// grid size depends only on the field size and the SM count, so repeated calls
-// give bitwise identical results.
+// grid size depends only on the field size, the SM count and the kernel, so
+// repeated calls give bitwise identical results.
 #pragma once
 
 #include "wd_device.cuh"
@@ -50,7 +50,15 @@ template <typename Op> __device__ __forceinline__ void blas_body(const Op &op, c
     double acc[NR > 0 ? NR : 1];
 #pragma unroll
     for (int k = 0; k < (NR > 0 ? NR : 1); ++k) acc[k] = 0.0;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nsite; j += gridDim.x * blockDim.x) op.site(j, acc);
+    // two sites per pass where the loop runs twice or more: the second site's
+    // loads can then be in flight with the first's
+    const int stride = gridDim.x * blockDim.x;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    for (; j + stride < nsite; j += 2 * stride) {
+        op.site(j, acc);
+        op.site(j + stride, acc);
+    }
+    if (j < nsite) op.site(j, acc);
     if constexpr (NR > 0) {
         __shared__ double sm[BLAS_THREADS / 32][NR];
         __shared__ bool last;

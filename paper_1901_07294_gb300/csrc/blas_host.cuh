@@ -28,10 +28,41 @@ inline int blas_grid(const wd_ctx *ctx, int nsite)
     return want < cap ? (want > 0 ? want : 1) : cap;
 }
 
+// Blocks of blas_kernel<Op> that fit on one SM at once (queried once per
+// operation type).
+template <typename Op> inline int blas_resident_blocks()
+{
+    static const int n = [] {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, blas_kernel<Op>, BLAS_THREADS, 0) != cudaSuccess || b < 1) {
+            cudaGetLastError();
+            b = 1;
+        }
+        return b;
+    }();
+    return n;
+}
+
+// Grid of blas_kernel<Op>.  A reduction runs as a single wave: one site per
+// thread up to the blocks that fit on the device at once, longer fields
+// looping within it (a partial second wave, as with a fixed 8 blocks per SM
+// for a kernel that fits 6, leaves the last blocks' partial sums, and so the
+// final sum, waiting on its stragglers).  Operations without a reduction keep
+// blas_grid.  Fixed by the field size, the SM count and the kernel, so the
+// reduction order is too.
+template <typename Op> inline int blas_grid_for(const wd_ctx *ctx, int nsite)
+{
+    if constexpr (Op::NR == 0) return blas_grid(ctx, nsite);
+    const int want = (nsite + BLAS_THREADS - 1) / BLAS_THREADS;
+    int cap = blas_resident_blocks<Op>() * (ctx->num_sms > 0 ? ctx->num_sms : 132);
+    if (cap > MAX_RED_BLOCKS) cap = MAX_RED_BLOCKS;
+    return want < cap ? (want > 0 ? want : 1) : cap;
+}
+
 template <typename Op> int run_blas(const wd_ctx *ctx, const Op &op, int nsite, cudaStream_t s)
 {
     RedScratch rs{ctx->d_partials, ctx->d_ticket};
-    cudaError_t e = wd_launch(blas_kernel<Op>, dim3(blas_grid(ctx, nsite)), dim3(BLAS_THREADS), 0, s, op, nsite, rs);
+    cudaError_t e = wd_launch(blas_kernel<Op>, dim3(blas_grid_for<Op>(ctx, nsite)), dim3(BLAS_THREADS), 0, s, op, nsite, rs);
     if (e != cudaSuccess) return set_error(WD_ECUDA, "BLAS kernel launch failed: %s", cudaGetErrorString(e));
     return WD_OK;
 }

@@ -113,7 +113,7 @@ inline int mdagm(const wd_gauge *g, int prec, int recon, double mass, const char
 
 template <typename Op> inline int launch(const wd_ctx *ctx, const Op &op, int nsite, RedScratch rs, cudaStream_t s)
 {
-    cudaError_t e = wd_launch(blas_kernel<Op>, dim3(blas_grid(ctx, nsite)), dim3(BLAS_THREADS), 0, s, op, nsite, rs);
+    cudaError_t e = wd_launch(blas_kernel<Op>, dim3(blas_grid_for<Op>(ctx, nsite)), dim3(BLAS_THREADS), 0, s, op, nsite, rs);
     return e == cudaSuccess ? WD_OK : set_error(WD_ECUDA, "BLAS launch failed: %s", cudaGetErrorString(e));
 }
 
