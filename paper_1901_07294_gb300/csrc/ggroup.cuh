@@ -149,35 +149,46 @@ __global__ void __launch_bounds__(128, P == PREC_F64 ? 1 : 6)
     }
 }
 
-// ---- per-member BLAS steps (blockIdx.y = position in the active list) ---------
+// ---- per-member BLAS steps --------------------------------------------------
+// Row y of the grid takes the active members y, y + GG_BLAS_ROWS, ...: a
+// member's reduction runs over the gridDim.x blocks of its row whatever the
+// group's size, and a small group launches no rows of blocks with nothing to do.
+constexpr int GG_BLAS_ROWS = 8;
+
 template <int PS> __global__ void __launch_bounds__(BLAS_THREADS) gg_xpay_kernel(const GTable *__restrict__ T, int vh)
 {
-    if ((int)blockIdx.y >= T->n) return;
-    const GMember &m = T->m[T->idx[blockIdx.y]];
     const size_t hs = half_bytes_p<PS>(vh);
-    blas_body(OpXpayDev<PS>{FieldRef<PS>{m.f[GF_RS], hs, vh}, FieldRef<PS>{m.f[GF_PS], hs, vh}, m.scal}, vh, m.red);
+    for (int t = blockIdx.y; t < T->n; t += gridDim.y) {
+        const GMember &m = T->m[T->idx[t]];
+        blas_body(OpXpayDev<PS>{FieldRef<PS>{m.f[GF_RS], hs, vh}, FieldRef<PS>{m.f[GF_PS], hs, vh}, m.scal}, vh, m.red);
+        __syncthreads();   // the next member reuses blas_body's shared memory
+    }
 }
 
 template <int PS> __global__ void __launch_bounds__(BLAS_THREADS) gg_dot_kernel(const GTable *__restrict__ T, int vh)
 {
-    if ((int)blockIdx.y >= T->n) return;
-    const GMember &m = T->m[T->idx[blockIdx.y]];
     const size_t hs = half_bytes_p<PS>(vh);
-    blas_body(OpDotAlphaDev<PS>{FieldRef<PS>{m.f[GF_PS], hs, vh}, FieldRef<PS>{m.f[GF_APS], hs, vh}, m.scal}, vh,
-              m.red);
+    for (int t = blockIdx.y; t < T->n; t += gridDim.y) {
+        const GMember &m = T->m[T->idx[t]];
+        blas_body(OpDotAlphaDev<PS>{FieldRef<PS>{m.f[GF_PS], hs, vh}, FieldRef<PS>{m.f[GF_APS], hs, vh}, m.scal}, vh,
+                  m.red);
+        __syncthreads();   // the next member reuses blas_body's shared memory
+    }
 }
 
 template <int PS> __global__ void __launch_bounds__(BLAS_THREADS) gg_update_kernel(const GTable *__restrict__ T, int vh)
 {
-    if ((int)blockIdx.y >= T->n) return;
-    const GMember &m = T->m[T->idx[blockIdx.y]];
     const size_t hs = half_bytes_p<PS>(vh), h32 = half_bytes_p<PREC_F32>(vh);
-    OpCgUpdateDev<PREC_F32, PS> up{OpCgUpdate<PREC_F32, PS>{FieldRef<PREC_F32>{m.xs, h32, vh},
-                                                           FieldRef<PS>{m.f[GF_RS], hs, vh},
-                                                           FieldRef<PS>{m.f[GF_PS], hs, vh},
-                                                           FieldRef<PS>{m.f[GF_APS], hs, vh}, m.scal + 2, nullptr},
-                                   m.scal};
-    blas_body(up, vh, m.red);
+    for (int t = blockIdx.y; t < T->n; t += gridDim.y) {
+        const GMember &m = T->m[T->idx[t]];
+        OpCgUpdateDev<PREC_F32, PS> up{OpCgUpdate<PREC_F32, PS>{FieldRef<PREC_F32>{m.xs, h32, vh},
+                                                               FieldRef<PS>{m.f[GF_RS], hs, vh},
+                                                               FieldRef<PS>{m.f[GF_PS], hs, vh},
+                                                               FieldRef<PS>{m.f[GF_APS], hs, vh}, m.scal + 2, nullptr},
+                                       m.scal};
+        blas_body(up, vh, m.red);
+        __syncthreads();   // the next member reuses blas_body's shared memory
+    }
 }
 
 // The loop condition: each active member's bookkeeping as in gs_control_kernel
@@ -239,7 +250,7 @@ template <int PS> int build(const wd_ctx *ctx, GGroup &g)
     GraphSink sink;
     sink.graph = cp.conditional.phGraph_out[0];
     graph_sink() = &sink;
-    const dim3 bgrid((unsigned)blas_grid(ctx, vh), (unsigned)GG_MAX), bblk(BLAS_THREADS);
+    const dim3 bgrid((unsigned)blas_grid(ctx, vh), (unsigned)GG_BLAS_ROWS), bblk(BLAS_THREADS);
     const dim3 hgrid((unsigned)((vh + 31) / 32)), hblk(32, 4);
     const GTable *T = g.d_table;
     HopArgs Ao = A, Ae = A;
