@@ -89,6 +89,7 @@ template <> struct Canon<float> { using CT2 = float2; static constexpr int NC = 
 template <int P, typename CT>
 __global__ void pack_spinor_kernel(const CT *__restrict__ aos, char *__restrict__ field, SiteMap m)
 {
+    grid_dependency_enter();
     using CT2 = typename Canon<CT>::CT2;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (int64_t)m.np * m.vh) return;
@@ -109,6 +110,7 @@ __global__ void pack_spinor_kernel(const CT *__restrict__ aos, char *__restrict_
 template <int P, typename CT>
 __global__ void unpack_spinor_kernel(const char *__restrict__ field, CT *__restrict__ aos, SiteMap m)
 {
+    grid_dependency_enter();
     using CT2 = typename Canon<CT>::CT2;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (int64_t)m.np * m.vh) return;
@@ -148,6 +150,7 @@ template <int P, typename CT>
 __global__ void __launch_bounds__(LEX_TILE) pack_lex_kernel(const CT *__restrict__ aos, char *__restrict__ field,
                                                             SiteMap m, int64_t V)
 {
+    grid_dependency_enter();
     constexpr int NC = Canon<CT>::NC, PAD = NC + 1;
     __shared__ uint4 sh[LEX_TILE * PAD];
     const int64_t s0 = (int64_t)blockIdx.x * LEX_TILE;
@@ -169,6 +172,7 @@ template <int P, typename CT>
 __global__ void __launch_bounds__(LEX_TILE) unpack_lex_kernel(const char *__restrict__ field, CT *__restrict__ aos,
                                                               SiteMap m, int64_t V)
 {
+    grid_dependency_enter();
     constexpr int NC = Canon<CT>::NC, PAD = NC + 1;
     __shared__ uint4 sh[LEX_TILE * PAD];
     const int64_t s0 = (int64_t)blockIdx.x * LEX_TILE;
@@ -517,11 +521,11 @@ static int pack_impl(wd_ctx *ctx, const int dims[4], int sites, int prec, const 
         const int64_t V = 2 * (int64_t)m.vh;
         const int blocks = (int)((V + LEX_TILE - 1) / LEX_TILE);
         switch (prec) {
-        case WD_F64: pack_lex_kernel<PREC_F64, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
-        case WD_F32: pack_lex_kernel<PREC_F32, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
-        case WD_F16: pack_lex_kernel<PREC_F16, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
-        case WD_BF16: pack_lex_kernel<PREC_BF16, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
-        case WD_DF: pack_lex_kernel<PREC_DF, CT><<<blocks, LEX_TILE, 0, s>>>(aos, f, m, V); break;
+        case WD_F64: wd_launch(pack_lex_kernel<PREC_F64, CT>, dim3(blocks), dim3(LEX_TILE), 0, s, aos, f, m, V); break;
+        case WD_F32: wd_launch(pack_lex_kernel<PREC_F32, CT>, dim3(blocks), dim3(LEX_TILE), 0, s, aos, f, m, V); break;
+        case WD_F16: wd_launch(pack_lex_kernel<PREC_F16, CT>, dim3(blocks), dim3(LEX_TILE), 0, s, aos, f, m, V); break;
+        case WD_BF16: wd_launch(pack_lex_kernel<PREC_BF16, CT>, dim3(blocks), dim3(LEX_TILE), 0, s, aos, f, m, V); break;
+        case WD_DF: wd_launch(pack_lex_kernel<PREC_DF, CT>, dim3(blocks), dim3(LEX_TILE), 0, s, aos, f, m, V); break;
         }
         WD_CUDA_TRY(cudaGetLastError());
         return WD_OK;
@@ -529,11 +533,11 @@ static int pack_impl(wd_ctx *ctx, const int dims[4], int sites, int prec, const 
     const int threads = 256;
     const int blocks = (int)(((int64_t)m.np * m.vh + threads - 1) / threads);
     switch (prec) {
-    case WD_F64: pack_spinor_kernel<PREC_F64, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
-    case WD_F32: pack_spinor_kernel<PREC_F32, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
-    case WD_F16: pack_spinor_kernel<PREC_F16, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
-    case WD_BF16: pack_spinor_kernel<PREC_BF16, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
-    case WD_DF: pack_spinor_kernel<PREC_DF, CT><<<blocks, threads, 0, s>>>(aos, f, m); break;
+    case WD_F64: wd_launch(pack_spinor_kernel<PREC_F64, CT>, dim3(blocks), dim3(threads), 0, s, aos, f, m); break;
+    case WD_F32: wd_launch(pack_spinor_kernel<PREC_F32, CT>, dim3(blocks), dim3(threads), 0, s, aos, f, m); break;
+    case WD_F16: wd_launch(pack_spinor_kernel<PREC_F16, CT>, dim3(blocks), dim3(threads), 0, s, aos, f, m); break;
+    case WD_BF16: wd_launch(pack_spinor_kernel<PREC_BF16, CT>, dim3(blocks), dim3(threads), 0, s, aos, f, m); break;
+    case WD_DF: wd_launch(pack_spinor_kernel<PREC_DF, CT>, dim3(blocks), dim3(threads), 0, s, aos, f, m); break;
     }
     WD_CUDA_TRY(cudaGetLastError());
     return WD_OK;
@@ -554,11 +558,11 @@ static int unpack_impl(wd_ctx *ctx, const int dims[4], int sites, int prec, cons
         const int64_t V = 2 * (int64_t)m.vh;
         const int blocks = (int)((V + LEX_TILE - 1) / LEX_TILE);
         switch (prec) {
-        case WD_F64: unpack_lex_kernel<PREC_F64, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
-        case WD_F32: unpack_lex_kernel<PREC_F32, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
-        case WD_F16: unpack_lex_kernel<PREC_F16, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
-        case WD_BF16: unpack_lex_kernel<PREC_BF16, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
-        case WD_DF: unpack_lex_kernel<PREC_DF, CT><<<blocks, LEX_TILE, 0, s>>>(f, aos, m, V); break;
+        case WD_F64: wd_launch(unpack_lex_kernel<PREC_F64, CT>, dim3(blocks), dim3(LEX_TILE), 0, s, f, aos, m, V); break;
+        case WD_F32: wd_launch(unpack_lex_kernel<PREC_F32, CT>, dim3(blocks), dim3(LEX_TILE), 0, s, f, aos, m, V); break;
+        case WD_F16: wd_launch(unpack_lex_kernel<PREC_F16, CT>, dim3(blocks), dim3(LEX_TILE), 0, s, f, aos, m, V); break;
+        case WD_BF16: wd_launch(unpack_lex_kernel<PREC_BF16, CT>, dim3(blocks), dim3(LEX_TILE), 0, s, f, aos, m, V); break;
+        case WD_DF: wd_launch(unpack_lex_kernel<PREC_DF, CT>, dim3(blocks), dim3(LEX_TILE), 0, s, f, aos, m, V); break;
         }
         WD_CUDA_TRY(cudaGetLastError());
         return WD_OK;
@@ -566,11 +570,11 @@ static int unpack_impl(wd_ctx *ctx, const int dims[4], int sites, int prec, cons
     const int threads = 256;
     const int blocks = (int)(((int64_t)m.np * m.vh + threads - 1) / threads);
     switch (prec) {
-    case WD_F64: unpack_spinor_kernel<PREC_F64, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
-    case WD_F32: unpack_spinor_kernel<PREC_F32, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
-    case WD_F16: unpack_spinor_kernel<PREC_F16, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
-    case WD_BF16: unpack_spinor_kernel<PREC_BF16, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
-    case WD_DF: unpack_spinor_kernel<PREC_DF, CT><<<blocks, threads, 0, s>>>(f, aos, m); break;
+    case WD_F64: wd_launch(unpack_spinor_kernel<PREC_F64, CT>, dim3(blocks), dim3(threads), 0, s, f, aos, m); break;
+    case WD_F32: wd_launch(unpack_spinor_kernel<PREC_F32, CT>, dim3(blocks), dim3(threads), 0, s, f, aos, m); break;
+    case WD_F16: wd_launch(unpack_spinor_kernel<PREC_F16, CT>, dim3(blocks), dim3(threads), 0, s, f, aos, m); break;
+    case WD_BF16: wd_launch(unpack_spinor_kernel<PREC_BF16, CT>, dim3(blocks), dim3(threads), 0, s, f, aos, m); break;
+    case WD_DF: wd_launch(unpack_spinor_kernel<PREC_DF, CT>, dim3(blocks), dim3(threads), 0, s, f, aos, m); break;
     }
     WD_CUDA_TRY(cudaGetLastError());
     return WD_OK;

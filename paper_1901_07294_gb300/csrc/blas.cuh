@@ -115,6 +115,7 @@ template <typename Op> __device__ __forceinline__ void blas_body(const Op &op, c
 template <typename Op>
 __global__ void __launch_bounds__(BLAS_THREADS) blas_kernel(const Op op, const int nsite, const RedScratch rs)
 {
+    grid_dependency_enter();
     blas_body(op, nsite, rs);
 }
 

@@ -171,6 +171,7 @@ template <typename T> __device__ __forceinline__ void from12(const T (&v)[12], c
 template <int P, int HP, int RECON>
 __global__ void __launch_bounds__(128) dd_gather_kernel(const FaceArgs A)
 {
+    grid_dependency_enter();
     using T = typename Prec<P>::real;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= 2 * A.nf) return;
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(128) dd_gather_kernel(const FaceArgs A)
 template <int P, int HP, int RECON>
 __global__ void __launch_bounds__(128) dd_boundary_kernel(const FaceArgs A)
 {
+    grid_dependency_enter();
     using T = typename Prec<P>::real;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= 2 * A.nf) return;
@@ -269,11 +271,11 @@ cudaError_t launch_faces(bool gather, int recon, const FaceArgs &A, cudaStream_t
     const int threads = 128;
     const int blocks = (2 * A.nf + threads - 1) / threads;
     if (gather) {
-        if (recon == 12) dd_gather_kernel<P, HP, 12><<<blocks, threads, 0, s>>>(A);
-        else dd_gather_kernel<P, HP, 18><<<blocks, threads, 0, s>>>(A);
+        if (recon == 12) wd_launch(dd_gather_kernel<P, HP, 12>, dim3(blocks), dim3(threads), 0, s, A);
+        else wd_launch(dd_gather_kernel<P, HP, 18>, dim3(blocks), dim3(threads), 0, s, A);
     } else {
-        if (recon == 12) dd_boundary_kernel<P, HP, 12><<<blocks, threads, 0, s>>>(A);
-        else dd_boundary_kernel<P, HP, 18><<<blocks, threads, 0, s>>>(A);
+        if (recon == 12) wd_launch(dd_boundary_kernel<P, HP, 12>, dim3(blocks), dim3(threads), 0, s, A);
+        else wd_launch(dd_boundary_kernel<P, HP, 18>, dim3(blocks), dim3(threads), 0, s, A);
     }
     return cudaGetLastError();
 }

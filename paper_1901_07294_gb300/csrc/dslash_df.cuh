@@ -155,6 +155,7 @@ __device__ __forceinline__ void df_row_dir(const char *in, const char *lblk, int
 template <bool DAG, bool HAS_X>
 __global__ void __launch_bounds__(DF_ROW_THREADS, DF_ROW_BLOCKS) hop_df_row_kernel(const HopArgs A)
 {
+    grid_dependency_enter();
     __shared__ DfHalfTile tile[2];
     int p, blk;
     if (A.nparity == 2) { p = blockIdx.x & 1; blk = blockIdx.x >> 1; }

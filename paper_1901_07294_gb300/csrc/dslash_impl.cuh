@@ -419,6 +419,7 @@ __device__ __forceinline__ void hop_site(const HopArgs &A, const int p, const in
 template <int P, int RECON, bool DAG, bool HAS_X, int PF, bool TOPEN = false, bool LNA = false>
 __global__ void __launch_bounds__(256, PF == 4 ? 3 : (PF == 5 || PF == 6) ? 1 : 2) hop_kernel(const HopArgs A)
 {
+    grid_dependency_enter();
     int p, blk;
     if (A.nparity == 2) { p = blockIdx.x & 1; blk = blockIdx.x >> 1; }
     else { p = A.parity0; blk = blockIdx.x; }

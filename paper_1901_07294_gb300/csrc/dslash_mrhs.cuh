@@ -183,6 +183,7 @@ __device__ __forceinline__ int mrhs_site(const HopArgs &A, int j, int zs)
 template <int P, int RECON, bool DAG, bool HAS_X>
 __global__ void __launch_bounds__(256, P == PREC_F64 ? 1 : 3) hop_mrhs_kernel(const HopArgs A, const int nrhs, const int zs)
 {
+    grid_dependency_enter();
     using T = typename Prec<P>::real;
     using LT = LinkTile<T>;
     __shared__ typename LT::V lk[8][LT::NV][32];

@@ -224,6 +224,7 @@ __device__ __forceinline__ void sp_site(const HopArgs &A, const int p, const int
 template <int P, int RECON, bool DAG, bool HAS_X, int PF, bool LNA>
 __global__ void __launch_bounds__(256, 2) hop_sp_kernel(const HopArgs A)
 {
+    grid_dependency_enter();
     int p, blk;
     if (A.nparity == 2) { p = blockIdx.x & 1; blk = blockIdx.x >> 1; }
     else { p = A.parity0; blk = blockIdx.x; }

@@ -84,6 +84,7 @@ template <int P> __host__ __device__ constexpr size_t window_bytes(int threads, 
 template <int P, int RECON, bool DAG, bool HAS_X>
 __global__ void __launch_bounds__(256, 2) hop_window_kernel(const HopArgs A)
 {
+    grid_dependency_enter();
     using T = typename Prec<P>::real;
     extern __shared__ uint4 window_mem[];
     int p, blk;
@@ -196,6 +197,7 @@ bool launch_hop_window(const HopArgs &A, dim3 grid, int threads, cudaStream_t s,
 template <int P, int RECON, bool DAG, bool HAS_X>
 __global__ void __launch_bounds__(256, 2) hop_2site_kernel(const HopArgs A)
 {
+    grid_dependency_enter();
     int p, blk;
     if (A.nparity == 2) { p = blockIdx.x & 1; blk = blockIdx.x >> 1; }
     else { p = A.parity0; blk = blockIdx.x; }

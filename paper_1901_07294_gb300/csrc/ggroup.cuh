@@ -60,6 +60,7 @@ template <int P, int RECON, bool DAG, bool HAS_X>
 __global__ void __launch_bounds__(128, P == PREC_F64 ? 1 : 6)
     hop_group_kernel(const HopArgs A, const GTable *__restrict__ T, const int fi, const int fx, const int fo)
 {
+    grid_dependency_enter();
     using T_ = typename Prec<P>::real;
     using LT = LinkTile<T_>;
     __shared__ typename LT::V lk[8][LT::NV][32];
@@ -157,6 +158,7 @@ constexpr int GG_BLAS_ROWS = 8;
 
 template <int PS> __global__ void __launch_bounds__(BLAS_THREADS) gg_xpay_kernel(const GTable *__restrict__ T, int vh)
 {
+    grid_dependency_enter();
     const size_t hs = half_bytes_p<PS>(vh);
     for (int t = blockIdx.y; t < T->n; t += gridDim.y) {
         const GMember &m = T->m[T->idx[t]];
@@ -167,6 +169,7 @@ template <int PS> __global__ void __launch_bounds__(BLAS_THREADS) gg_xpay_kernel
 
 template <int PS> __global__ void __launch_bounds__(BLAS_THREADS) gg_dot_kernel(const GTable *__restrict__ T, int vh)
 {
+    grid_dependency_enter();
     const size_t hs = half_bytes_p<PS>(vh);
     for (int t = blockIdx.y; t < T->n; t += gridDim.y) {
         const GMember &m = T->m[T->idx[t]];
@@ -178,6 +181,7 @@ template <int PS> __global__ void __launch_bounds__(BLAS_THREADS) gg_dot_kernel(
 
 template <int PS> __global__ void __launch_bounds__(BLAS_THREADS) gg_update_kernel(const GTable *__restrict__ T, int vh)
 {
+    grid_dependency_enter();
     const size_t hs = half_bytes_p<PS>(vh), h32 = half_bytes_p<PREC_F32>(vh);
     for (int t = blockIdx.y; t < T->n; t += gridDim.y) {
         const GMember &m = T->m[T->idx[t]];
@@ -198,6 +202,7 @@ template <int PS> __global__ void __launch_bounds__(BLAS_THREADS) gg_update_kern
 // host to read after the launch.
 __global__ void gg_control_kernel(GTable *T, double *hs, cudaGraphConditionalHandle cond)
 {
+    grid_dependency_enter();
     const int t = threadIdx.x;
     const int n = T->n;
     bool stop = false;

@@ -56,6 +56,7 @@ __device__ __forceinline__ bool gs_member_step(double *s)
 template <int UNUSED = 0>
 __global__ void gs_control_kernel(double *s, cudaGraphConditionalHandle cond)
 {
+    grid_dependency_enter();
     if (threadIdx.x != 0) return;
     cudaGraphSetConditional(cond, gs_member_step(s) ? 0u : 1u);
 }

@@ -10,6 +10,21 @@ namespace wd {
 
 enum { PREC_F64 = 0, PREC_F32 = 1, PREC_F16 = 2, PREC_BF16 = 3, PREC_DF = 4 };
 
+// First statement of every kernel launched through wd_launch, which launches
+// with programmatic dependent launch.  The wait returns once all grids this
+// one depends on programmatically have completed and their memory operations
+// are visible (at once for a kernel launched without such a dependency); no
+// access to global memory may precede it, so an early start can neither read
+// a result before it is written nor overwrite an input its predecessor still
+// reads.  The trigger then lets the next kernel be dispatched as soon as every
+// block of this one has passed it: at most two grids of a chain are resident,
+// the running one and its waiting successor.
+__device__ __forceinline__ void grid_dependency_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---- double-word FP32 ("double-float") arithmetic ---------------------------
 // A value is the unevaluated sum hi + lo of two FP32 numbers, |lo| <= ulp(hi)
 // after normalisation: 48 significand bits from FP32 instructions, for a part
