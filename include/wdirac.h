@@ -46,7 +46,12 @@
  *
  * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).
  * Operator calls are asynchronous on that stream; launch errors are reported
- * at once, asynchronous faults at the next synchronising call.
+ * at once, asynchronous faults at the next synchronising call.  Kernels are
+ * launched with programmatic dependent launch: one may be dispatched while
+ * the kernel before it on the stream is finishing, and it waits for that
+ * kernel's completion before it reads or writes memory, so stream order holds
+ * as for plain launches.  WD_PDL=0 in the environment (read once per process)
+ * launches them serialised instead.
  */
 #ifndef WDIRAC_H
 #define WDIRAC_H
