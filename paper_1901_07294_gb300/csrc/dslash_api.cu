@@ -33,7 +33,7 @@ std::string hop_key(const wd_ctx *ctx, const HopArgs &A, int prec, int recon, in
 // (FP64-ALU bound) with 128 threads, schedule 0.
 static std::pair<int, int> hop_default(int prec, int nrhs, int nparity)
 {
-    if (prec == WD_DF) return {96, HOP_F64_1B_VARIANT};   // double-word: three threads per site (18-real links)
+    if (prec == WD_DF) return {96, HOP_F64_1B_VARIANT};   // double-word: three threads per site
     if (nrhs > 1) return {128, HOP_MRHS_VARIANT};   // shared-link kernel, 4 fields at a time
     if (prec == WD_F64) return {128, 0};
     if (nparity == 1 && (prec == WD_F16 || prec == WD_BF16)) return {64, HOP_SP0_VARIANT};

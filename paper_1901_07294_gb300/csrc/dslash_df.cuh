@@ -9,7 +9,8 @@
 // exchanges the projected half spinors through shared memory, and each thread
 // multiplies them by row r of U (column r for U^dagger) and accumulates the four
 // spin components of colour r.  That is about a third of the per-site state,
-// so more warps fit.
+// so more warps fit.  With 12-real links each warp also rebuilds one entry of
+// the link's third row and shares it through the same tile.
 #pragma once
 
 #include "dslash_impl.cuh"
@@ -93,19 +94,44 @@ __device__ __forceinline__ void df_accumulate(cpx<df> (&acc)[4], const cpx<df> &
 
 // The projected half spinors of the block's 32 sites for one direction:
 // warp c writes colour c, every warp then reads all three.  [colour][h0 re,
-// h0 im, h1 re, h1 im as (hi, lo) pairs: two float4][site]
-struct DfHalfTile {
+// h0 im, h1 re, h1 im as (hi, lo) pairs: two float4][site].  With 12-real
+// links, rec[c] holds entry (2, c) of the direction's link, rebuilt by warp c.
+template <int RECON> struct DfHalfTile {
     float4 v[3][2][32];
+    float4 rec[RECON == 12 ? 3 : 1][32];
 };
+
+// Entry (2, C) of a 12-real link from its stored rows 0 and 1:
+// conj(U0a U1b - U0b U1a) with a = C+1, b = C+2 (mod 3), one four-term
+// compensated chain per part as in Link::load, normalised for use as a
+// product operand.
+template <int C>
+__device__ __forceinline__ cpx<df> df_row3_entry(const cpx<df> (&e0)[3], const cpx<df> (&e1)[3])
+{
+    constexpr int a = (C + 1) % 3, b = (C + 2) % 3;
+    const cpx<df> x = e0[a], y = e1[b], z = e0[b], w = e1[a];
+    df re = x.re * y.re;
+    re = fma(-x.im, y.im, re);
+    re = fma(-z.re, w.re, re);
+    re = fma(z.im, w.im, re);
+    df im = -(x.re * y.im);
+    im = fma(-x.im, y.re, im);
+    im = fma(z.re, w.im, im);
+    im = fma(z.im, w.re, im);
+    return {df_normalize(re), df_normalize(im)};
+}
 
 // One direction for colour row r: acc[s] += the (s, r) component of
 // (1 + S gamma_MU) U psi (FWD) or (1 + S gamma_MU) U^dagger psi.  Warp r loads
 // the neighbour's colour-r spin components only and projects them; the block
 // exchanges the projections through `tile` (one barrier; the tile of a
 // direction is rewritten two directions later, after the next barrier).
-template <int MU, int S, bool FWD, bool FIRST = false>
+// With 12-real links every warp loads the two stored rows and rebuilds entry
+// (2, r); a forward hop's row 2 is then the three warps' entries, read from
+// the tile after the same barrier.
+template <int MU, int S, bool FWD, int RECON, bool FIRST = false>
 __device__ __forceinline__ void df_row_dir(const char *in, const char *lblk, int vh, int nb, int li, bool neg, int r,
-                                           int lane, DfHalfTile &tile, cpx<df> (&acc)[4])
+                                           int lane, DfHalfTile<RECON> &tile, cpx<df> (&acc)[4])
 {
     cpx<df> p[4];
 #pragma unroll
@@ -115,18 +141,44 @@ __device__ __forceinline__ void df_row_dir(const char *in, const char *lblk, int
         p[sp] = {v[0], v[1]};
     }
     cpx<df> u[3];   // U[r][c] (FWD) or U[c][r]
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int k = FWD ? 3 * r + c : 3 * c + r;   // plane of the entry (one complex number per plane)
+    auto entry = [&](int k) {   // plane k = 3 row + column holds one complex number
         df v[2];
         unpack16<PREC_DF>(ldg16(lblk + ((size_t)k * vh + li) * 16), v, 1.0f);
-        u[c] = {v[0], v[1]};
+        return cpx<df>{v[0], v[1]};
+    };
+    if constexpr (RECON == 18) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[c] = entry(FWD ? 3 * r + c : 3 * c + r);
+    } else {
+        cpx<df> e0[3], e1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            e0[c] = entry(c);
+            e1[c] = entry(3 + c);
+        }
+        const cpx<df> rec = r == 0 ? df_row3_entry<0>(e0, e1) : r == 1 ? df_row3_entry<1>(e0, e1)
+                                                                       : df_row3_entry<2>(e0, e1);
+        tile.rec[r][lane] = make_float4(rec.re.hi, rec.re.lo, rec.im.hi, rec.im.lo);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if constexpr (FWD) u[c] = r == 0 ? e0[c] : e1[c];   // row 2: from the tile below
+            else u[c] = c == 2 ? rec : (r == 0 ? (c == 0 ? e0[0] : e1[0]) : r == 1 ? (c == 0 ? e0[1] : e1[1])
+                                                                             : (c == 0 ? e0[2] : e1[2]));
+        }
     }
     cpx<df> g0, g1;
     project_colour<MU, S>(p, g0, g1);
     tile.v[r][0][lane] = make_float4(g0.re.hi, g0.re.lo, g0.im.hi, g0.im.lo);
     tile.v[r][1][lane] = make_float4(g1.re.hi, g1.re.lo, g1.im.hi, g1.im.lo);
     __syncthreads();
+    if constexpr (RECON == 12 && FWD) {
+        if (r == 2)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float4 q = tile.rec[c][lane];
+                u[c] = {df(q.x, q.y), df(q.z, q.w)};
+            }
+    }
     cpx<df> h0[3], h1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -149,14 +201,14 @@ __device__ __forceinline__ void df_row_dir(const char *in, const char *lblk, int
     df_accumulate<MU, S, FIRST>(acc, w0, w1);
 }
 
-// 18-real links; blocks alternate parity for the full operator as in
+// 18- or 12-real links; blocks alternate parity for the full operator as in
 // hop_kernel; out = a x + b acc.  Every thread of a block takes part in the
 // barriers: threads past the last site compute the last site and store nothing.
-template <bool DAG, bool HAS_X>
+template <int RECON, bool DAG, bool HAS_X>
 __global__ void __launch_bounds__(DF_ROW_THREADS, DF_ROW_BLOCKS) hop_df_row_kernel(const HopArgs A)
 {
     grid_dependency_enter();
-    __shared__ DfHalfTile tile[2];
+    __shared__ DfHalfTile<RECON> tile[2];
     int p, blk;
     if (A.nparity == 2) { p = blockIdx.x & 1; blk = blockIdx.x >> 1; }
     else { p = A.parity0; blk = blockIdx.x; }
@@ -177,14 +229,14 @@ __global__ void __launch_bounds__(DF_ROW_THREADS, DF_ROW_BLOCKS) hop_df_row_kern
     constexpr int SF = DAG ? +1 : -1;
     constexpr int SB = -SF;
     cpx<df> acc[4];
-    df_row_dir<0, SB, false, true>(in, gb + 0 * lb, vh, nb[4], nb[4], false, r, lane, tile[0], acc);
-    df_row_dir<1, SB, false>(in, gb + 1 * lb, vh, nb[5], nb[5], false, r, lane, tile[1], acc);
-    df_row_dir<2, SB, false>(in, gb + 2 * lb, vh, nb[6], nb[6], false, r, lane, tile[0], acc);
-    df_row_dir<3, SB, false>(in, gb + 3 * lb, vh, nb[7], nb[7], ntb, r, lane, tile[1], acc);
-    df_row_dir<0, SF, true>(in, gf + 0 * lb, vh, nb[0], i, false, r, lane, tile[0], acc);
-    df_row_dir<1, SF, true>(in, gf + 1 * lb, vh, nb[1], i, false, r, lane, tile[1], acc);
-    df_row_dir<2, SF, true>(in, gf + 2 * lb, vh, nb[2], i, false, r, lane, tile[0], acc);
-    df_row_dir<3, SF, true>(in, gf + 3 * lb, vh, nb[3], i, ntf, r, lane, tile[1], acc);
+    df_row_dir<0, SB, false, RECON, true>(in, gb + 0 * lb, vh, nb[4], nb[4], false, r, lane, tile[0], acc);
+    df_row_dir<1, SB, false, RECON>(in, gb + 1 * lb, vh, nb[5], nb[5], false, r, lane, tile[1], acc);
+    df_row_dir<2, SB, false, RECON>(in, gb + 2 * lb, vh, nb[6], nb[6], false, r, lane, tile[0], acc);
+    df_row_dir<3, SB, false, RECON>(in, gb + 3 * lb, vh, nb[7], nb[7], ntb, r, lane, tile[1], acc);
+    df_row_dir<0, SF, true, RECON>(in, gf + 0 * lb, vh, nb[0], i, false, r, lane, tile[0], acc);
+    df_row_dir<1, SF, true, RECON>(in, gf + 1 * lb, vh, nb[1], i, false, r, lane, tile[1], acc);
+    df_row_dir<2, SF, true, RECON>(in, gf + 2 * lb, vh, nb[2], i, false, r, lane, tile[0], acc);
+    df_row_dir<3, SF, true, RECON>(in, gf + 3 * lb, vh, nb[3], i, ntf, r, lane, tile[1], acc);
     if (!active) return;
 
     const df a = (df)A.a, b = (df)A.b;
@@ -211,11 +263,11 @@ __global__ void __launch_bounds__(DF_ROW_THREADS, DF_ROW_BLOCKS) hop_df_row_kern
     }
 }
 
-template <bool DAG, bool HX>
+template <int RECON, bool DAG, bool HX>
 cudaError_t launch_hop_df_row(const HopArgs &A, int nrhs, cudaStream_t s)
 {
     const int per = (A.vh + 31) / 32;
-    return wd_launch(hop_df_row_kernel<DAG, HX>, dim3((unsigned)(per * A.nparity), (unsigned)nrhs),
+    return wd_launch(hop_df_row_kernel<RECON, DAG, HX>, dim3((unsigned)(per * A.nparity), (unsigned)nrhs),
                      dim3(DF_ROW_THREADS), 0, s, A);
 }
 

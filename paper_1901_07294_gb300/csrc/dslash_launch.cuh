@@ -131,17 +131,21 @@ cudaError_t launch_hop(const HopArgs &A, int recon, int dagger, int nrhs, int th
     const bool hx = A.x[0] != nullptr || A.x[1] != nullptr;
     const int key = (recon == 12 ? 4 : 0) + (dagger ? 2 : 0) + (hx ? 1 : 0);
     if constexpr (P == PREC_DF) {
-        // double-word FP32: with 18-real links, variant HOP_F64_1B_VARIANT is
-        // the three-threads-per-site kernel (dslash_df.cuh); otherwise one site
+        // double-word FP32: variant HOP_F64_1B_VARIANT is the
+        // three-threads-per-site kernel (dslash_df.cuh); otherwise one site
         // per thread, one block of 256 per SM, schedule 1 for variants 1 and 12
         // and schedule 0 for the rest
         if (A.topen) return cudaErrorInvalidValue;
-        if (recon == 18 && pf == HOP_F64_1B_VARIANT) {
+        if (pf == HOP_F64_1B_VARIANT) {
             switch (key) {
-            case 0: return launch_hop_df_row<false, false>(A, nrhs, s);
-            case 1: return launch_hop_df_row<false, true>(A, nrhs, s);
-            case 2: return launch_hop_df_row<true, false>(A, nrhs, s);
-            default: return launch_hop_df_row<true, true>(A, nrhs, s);
+            case 0: return launch_hop_df_row<18, false, false>(A, nrhs, s);
+            case 1: return launch_hop_df_row<18, false, true>(A, nrhs, s);
+            case 2: return launch_hop_df_row<18, true, false>(A, nrhs, s);
+            case 3: return launch_hop_df_row<18, true, true>(A, nrhs, s);
+            case 4: return launch_hop_df_row<12, false, false>(A, nrhs, s);
+            case 5: return launch_hop_df_row<12, false, true>(A, nrhs, s);
+            case 6: return launch_hop_df_row<12, true, false>(A, nrhs, s);
+            default: return launch_hop_df_row<12, true, true>(A, nrhs, s);
             }
         }
         const int per = (A.vh + threads - 1) / threads;

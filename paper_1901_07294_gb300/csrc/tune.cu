@@ -121,7 +121,7 @@ int wd_tune_dslash(wd_ctx *ctx, const wd_gauge *g, int prec, int recon, int full
             // double-word FP32: schedules 0 and 1 one block per SM, and the
             // three-threads-per-site kernel (its own block shape: timed once)
             if (prec == WD_DF && v != 0 && v != 1 && v != HOP_F64_1B_VARIANT) continue;
-            if (prec == WD_DF && v == HOP_F64_1B_VARIANT && recon == 18 && ti > 0) continue;
+            if (prec == WD_DF && v == HOP_F64_1B_VARIANT && ti > 0) continue;
             for (int w = 0; w < 2 && rc == WD_OK; ++w) rc = hop_launch_cfg(A, prec, recon, 0, nrhs, th, v, s);
             const int reps = 10;
             cudaEventRecord(e0, s);
