@@ -27,17 +27,18 @@ std::string hop_key(const wd_ctx *ctx, const HopArgs &A, int prec, int recon, in
 
 // Untuned defaults, from tuning runs on GB300 (32^4, 24^3x48, 16^3x32): the
 // FP32/FP16/BF16 kernels are fastest with 64-thread blocks and memory
-// schedule 1, even-odd hops (each link read once) with the links loaded
-// without L1 allocation, and the 16-bit even-odd hops with the spin-paired
-// kernel (schedule 0, links without L1 allocation); the FP64 kernel
-// (FP64-ALU bound) with 128 threads, schedule 0.
+// schedule 1; even-odd hops (each link read once) load the links without L1
+// allocation, FP32 ones with schedule 0 (24^3x48: 40.1 against 43.3 us for
+// schedule 1; 32^4: 62.6 against 63.8 us) and the 16-bit ones with the
+// spin-paired kernel (schedule 0); the FP64 kernel (FP64-ALU bound) with 128
+// threads, schedule 0.
 static std::pair<int, int> hop_default(int prec, int nrhs, int nparity)
 {
     if (prec == WD_DF) return {96, HOP_F64_1B_VARIANT};   // double-word: three threads per site
     if (nrhs > 1) return {128, HOP_MRHS_VARIANT};   // shared-link kernel, 4 fields at a time
     if (prec == WD_F64) return {128, 0};
     if (nparity == 1 && (prec == WD_F16 || prec == WD_BF16)) return {64, HOP_SP0_VARIANT};
-    return {64, nparity == 1 ? HOP_NA1_VARIANT : 1};
+    return {64, nparity == 1 ? HOP_NA0_VARIANT : 1};
 }
 
 int hop_launch_cfg(const HopArgs &A, int prec, int recon, int dagger, int nrhs, int threads, int variant,
