@@ -40,6 +40,11 @@ struct Req {
     wd_solve_desc d{};
     size_t foot = 0;
     bool cancel = false, done = false;
+    // ownership (under rq_queue::mu): `listed` while the request is in the
+    // scheduler's running list, which the scheduler reads without the lock
+    // during a pass; a result taken while listed marks it `taken`, and the
+    // scheduler frees it when it drops it from the list
+    bool listed = false, taken = false;
     int state = R_INIT;      // scheduler thread only
     int group = -1, slot = -1;
     cudaEvent_t ev = nullptr;   // recorded on its stream when it rejoins after an update
@@ -379,6 +384,7 @@ void scheduler(rq_queue *q)
             r->state = R_INIT;
             std::lock_guard<std::mutex> lk(q->mu);
             q->running.push_back(r);
+            r->listed = true;
         }
         std::vector<Req *> running;
         {
@@ -439,8 +445,14 @@ void scheduler(rq_queue *q)
         {
             std::lock_guard<std::mutex> lk(q->mu);
             std::vector<Req *> keep;
-            for (Req *r : q->running)
-                if (!r->done) keep.push_back(r);
+            for (Req *r : q->running) {
+                if (!r->done) {
+                    keep.push_back(r);
+                    continue;
+                }
+                r->listed = false;
+                if (r->taken) delete r;   // its result was taken during this pass
+            }
             q->running.swap(keep);
         }
         // nothing finished: wait briefly, or until a new request arrives
@@ -546,12 +558,15 @@ int rq_submit(rq_queue *q, const wd_solve_desc *d, uint64_t *ticket)
     return WD_OK;
 }
 
+// Called with q->mu held, for a finished request.  A request the scheduler
+// still lists is freed by the scheduler instead (it may be reading it).
 static int take_result(rq_queue *q, std::unordered_map<uint64_t, Req *>::iterator it, wd_solve_result *out)
 {
     Req *r = it->second;
     if (out) *out = r->res;
     q->all.erase(it);
-    delete r;
+    if (r->listed) r->taken = true;
+    else delete r;
     return WD_OK;
 }
 
