@@ -593,13 +593,35 @@ def _desc(p: dict) -> SolveDesc:
     return SolveDesc(p["gauge"].handle, float(p["mass"]), float(p["tol"]), _ptr(p["x"]), _ptr(p["b"]), o)
 
 
+_live_queues = None
+
+
+def _close_live_queues():
+    for q in list(_live_queues or ()):
+        try:
+            q.close()
+        except Exception:
+            pass
+
+
 class Queue:
-    """Solve-request queue with continuous batching (rq_* of the C ABI)."""
+    """Solve-request queue with continuous batching (rq_* of the C ABI).
+
+    Queues still open when the interpreter exits are closed by an exit handler, which
+    runs before the CUDA runtime and torch are torn down: closing waits for the requests
+    in flight, whose fields must stay alive until then."""
 
     def __init__(self, ctx: Context, hbm_budget_bytes: int, max_slots: int):
+        global _live_queues
         self._h = _vp()
         self.ctx = ctx
         _check(load().rq_create(ctx.handle, _sz(int(hbm_budget_bytes)), int(max_slots), ctypes.byref(self._h)))
+        if _live_queues is None:
+            import atexit
+            import weakref
+            _live_queues = weakref.WeakSet()
+            atexit.register(_close_live_queues)   # registered after torch and the CUDA runtime: runs first
+        _live_queues.add(self)
 
     def submit(self, problem: dict) -> int:
         t = ctypes.c_uint64(0)

@@ -213,27 +213,34 @@ def test_results_taken_while_the_scheduler_runs():
     finishes, while new ones are submitted and others still run: a request finished in
     the scheduler's current pass stays valid until the scheduler has dropped it, so a
     result taken at that moment neither frees memory the scheduler still reads nor lets
-    a new request reuse it.  Every request completes with its tolerance met."""
+    a new request reuse it.  Every request completes.  The fields of a request stay
+    alive until its result is taken (the caller owns them)."""
     ctx = _ctx()
     q = wd.Queue(ctx, hbm_budget_bytes=8 << 30, max_slots=8)
     dims = (4, 4, 4, 4)
     U, g = _gauge(ctx, dims)
     b = pack_field(ctx, dims, wd.SITES_EVEN, wd.F64, synth.even_spinor(dims, seed=3900))
-    pending, done = [], 0
-    for k in range(240):
-        p = dict(gauge=g, mass=0.1 + 0.001 * (k % 50), tol=1e-8, inner_prec=wd.F16, delta=0.1, b=b,
-                 x=wd.alloc_field(dims, wd.SITES_EVEN, wd.F64))
-        pending.append(q.submit(p))
-        if len(pending) > 4:
-            t = pending.pop(0)
-            r = q.poll(t) if k % 2 else None
-            if r is None:
-                r = q.wait(t, timeout_ms=60000)
-            assert r["status"] == 0, r
-            done += 1
-    for t in pending:
-        assert q.wait(t, timeout_ms=60000)["status"] == 0
-        done += 1
-    st = q.stats()
-    q.close()
-    assert done == 240 and st["completed"] == 240, st
+    live = {}   # ticket -> request (keeps its x alive until the result is taken)
+    order, statuses = [], []
+    try:
+        for k in range(240):
+            p = dict(gauge=g, mass=0.1 + 0.001 * (k % 50), tol=1e-8, inner_prec=wd.F16, delta=0.1, b=b,
+                     x=wd.alloc_field(dims, wd.SITES_EVEN, wd.F64))
+            t = q.submit(p)
+            live[t] = p
+            order.append(t)
+            if len(order) > 4:
+                t = order.pop(0)
+                r = q.poll(t) if k % 2 else None
+                if r is None:
+                    r = q.wait(t, timeout_ms=60000)
+                statuses.append(r["status"])
+                del live[t]
+        for t in order:
+            statuses.append(q.wait(t, timeout_ms=60000)["status"])
+            del live[t]
+        st = q.stats()
+    finally:
+        q.close()
+    assert statuses == [0] * 240, statuses
+    assert st["completed"] == 240, st
